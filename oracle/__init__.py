@@ -1,0 +1,308 @@
+"""ctypes wrapper of the plain C oracle (``lopc_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may use it; the library's product path never does.
+The oracle shares no code with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+SRC = HERE / "lopc_oracle.c"
+LIB = HERE / "_liboracle.so"
+
+OK, INVALID_ARG, NONFINITE, RANGE, CAPACITY, CORRUPT = 0, -1, -2, -3, -4, -5
+
+
+def build(force: bool = False, openmp: bool = False) -> Path:
+    """Compiles the oracle with gcc (IEEE binary64 on SSE2, no FMA contraction)."""
+    if LIB.exists() and not force and LIB.stat().st_mtime >= max(SRC.stat().st_mtime,
+                                                               (HERE / "lopc_oracle.h").stat().st_mtime):
+        return LIB
+    tmp = LIB.with_suffix(f".{os.getpid()}.tmp")
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+           str(SRC), "-o", str(tmp), "-lquadmath", "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+class Desc(C.Structure):
+    _fields_ = [("dtype", C.c_int32), ("ndim", C.c_int32), ("dims", C.c_int64 * 3),
+                ("mode", C.c_int32), ("pad_", C.c_int32), ("eb", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(str(LIB))
+        P = C.c_void_p
+        L.orc_resolve_eps.argtypes = [C.POINTER(Desc), P, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        L.orc_quantize.argtypes = [C.c_int, P, C.c_int64, C.c_double, P]
+        L.orc_q1.argtypes = [C.c_int, C.c_double, C.c_double]
+        L.orc_q1.restype = C.c_int64
+        L.orc_lowest_in_bin.argtypes = [C.c_int, C.c_int64, C.c_double, C.POINTER(C.c_double)]
+        L.orc_succ_k.argtypes = [C.c_int, C.c_double, C.c_uint64]
+        L.orc_succ_k.restype = C.c_double
+        L.orc_constraint_masks.argtypes = [C.POINTER(Desc), P, P, P]
+        L.orc_repair_lfp.argtypes = [C.POINTER(Desc), P, P, P]
+        L.orc_repair_alg2.argtypes = [C.POINTER(Desc), P, P, P]
+        L.orc_repair_alg2.restype = C.c_int64
+        L.orc_reconstruct.argtypes = [C.c_int, C.c_int64, P, P, C.c_double, P]
+        L.orc_diffnb.argtypes = [C.c_int, P, C.c_int64, P]
+        L.orc_diffnb.restype = C.c_size_t
+        L.orc_undiffnb.argtypes = [C.c_int, P, C.c_int64, P]
+        L.orc_bit.argtypes = [C.c_int, P, C.c_int64, P]
+        L.orc_bit.restype = C.c_size_t
+        L.orc_unbit.argtypes = [C.c_int, P, C.c_int64, P]
+        L.orc_rze.argtypes = [C.c_int, P, C.c_size_t, P]
+        L.orc_rze.restype = C.c_size_t
+        L.orc_unrze.argtypes = [C.c_int, P, C.c_size_t, C.c_size_t, P]
+        L.orc_compress_bound.argtypes = [C.POINTER(Desc)]
+        L.orc_compress_bound.restype = C.c_size_t
+        L.orc_compress.argtypes = [C.POINTER(Desc), P, P, C.c_size_t, C.POINTER(C.c_size_t)]
+        L.orc_peek.argtypes = [P, C.c_size_t, C.POINTER(Desc)]
+        L.orc_decompress.argtypes = [P, C.c_size_t, P, C.c_size_t]
+        L.orc_order_violations.argtypes = [C.POINTER(Desc), P, P]
+        L.orc_order_violations.restype = C.c_int64
+        L.orc_critical_types.argtypes = [C.POINTER(Desc), P, P, P]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def dtype_code(x: np.ndarray) -> int:
+    if x.dtype == np.float32:
+        return 0
+    if x.dtype == np.float64:
+        return 1
+    raise TypeError(x.dtype)
+
+
+def make_desc(shape, dtype_c: int, mode: int = 1, eb: float = 1e-3) -> Desc:
+    d = Desc()
+    d.dtype = dtype_c
+    d.ndim = len(shape)
+    for k, n in enumerate(shape):
+        d.dims[k] = int(n)
+    d.mode = mode
+    d.eb = float(eb)
+    return d
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: status {code}")
+        self.code = code
+
+
+def _c(x: np.ndarray) -> np.ndarray:
+    return np.ascontiguousarray(x)
+
+
+def resolve_eps(x: np.ndarray, mode: int, eb: float):
+    x = _c(x)
+    d = make_desc(x.shape, dtype_code(x), mode, eb)
+    e, eq, iv, cv = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    const = C.c_int()
+    rc = lib().orc_resolve_eps(C.byref(d), _ptr(x), C.byref(e), C.byref(eq), C.byref(iv), C.byref(const),
+                               C.byref(cv))
+    if rc:
+        raise OracleError(rc, "resolve_eps")
+    return dict(eps=e.value, eps_q=eq.value, inv=iv.value, constant=bool(const.value), const_value=cv.value)
+
+
+def quantize(x: np.ndarray, inv: float) -> np.ndarray:
+    x = _c(x)
+    b = np.empty(x.shape, np.int64)
+    rc = lib().orc_quantize(dtype_code(x), _ptr(x), x.size, inv, _ptr(b))
+    if rc:
+        raise OracleError(rc, "quantize")
+    return b
+
+
+def q1(dtype_c: int, v: float, inv: float) -> int:
+    return lib().orc_q1(dtype_c, v, inv)
+
+
+def lowest_in_bin(dtype_c: int, b: int, inv: float) -> float:
+    v = C.c_double()
+    rc = lib().orc_lowest_in_bin(dtype_c, int(b), inv, C.byref(v))
+    if rc:
+        raise OracleError(rc, "lowest_in_bin")
+    return v.value
+
+
+def succ_k(dtype_c: int, v: float, k: int) -> float:
+    return lib().orc_succ_k(dtype_c, v, int(k))
+
+
+def constraint_masks(x: np.ndarray, b: np.ndarray) -> np.ndarray:
+    x = _c(x)
+    b = _c(b.astype(np.int64))
+    m = np.empty(x.shape, np.uint16)
+    d = make_desc(x.shape, dtype_code(x))
+    lib().orc_constraint_masks(C.byref(d), _ptr(x), _ptr(b), _ptr(m))
+    return m
+
+
+def repair_lfp(x: np.ndarray, b: np.ndarray) -> np.ndarray:
+    x = _c(x)
+    b = _c(b.astype(np.int64))
+    s = np.zeros(x.shape, np.uint64)
+    d = make_desc(x.shape, dtype_code(x))
+    rc = lib().orc_repair_lfp(C.byref(d), _ptr(x), _ptr(b), _ptr(s))
+    if rc:
+        raise OracleError(rc, "repair_lfp")
+    return s
+
+
+def repair_alg2(x: np.ndarray, b: np.ndarray):
+    x = _c(x)
+    b = _c(b.astype(np.int64))
+    s = np.zeros(x.shape, np.uint64)
+    d = make_desc(x.shape, dtype_code(x))
+    it = lib().orc_repair_alg2(C.byref(d), _ptr(x), _ptr(b), _ptr(s))
+    return s, int(it)
+
+
+def reconstruct(dtype_c: int, b: np.ndarray, s: np.ndarray, inv: float) -> np.ndarray:
+    b = _c(b.astype(np.int64))
+    s = _c(s.astype(np.uint64))
+    out = np.empty(b.shape, np.float32 if dtype_c == 0 else np.float64)
+    rc = lib().orc_reconstruct(dtype_c, b.size, _ptr(b), _ptr(s), inv, _ptr(out))
+    if rc:
+        raise OracleError(rc, "reconstruct")
+    return out
+
+
+# codec stages ----------------------------------------------------------------
+
+def diffnb(w: int, v: np.ndarray) -> bytes:
+    v = _c(v.astype(np.int64))
+    out = np.zeros(v.size * w, np.uint8)
+    lib().orc_diffnb(w, _ptr(v), v.size, _ptr(out))
+    return out.tobytes()
+
+
+def undiffnb(w: int, data: bytes, n: int) -> np.ndarray:
+    a = np.frombuffer(data, np.uint8).copy()
+    v = np.empty(n, np.int64)
+    lib().orc_undiffnb(w, _ptr(a), n, _ptr(v))
+    return v
+
+
+def bit(w: int, words: bytes, n: int) -> bytes:
+    a = np.frombuffer(words, np.uint8).copy()
+    n32 = (n + 31) // 32 * 32
+    out = np.zeros(n32 * w, np.uint8)
+    L = lib().orc_bit(w, _ptr(a), n, _ptr(out))
+    return out[:L].tobytes()
+
+
+def unbit(w: int, data: bytes, n32: int) -> bytes:
+    a = np.frombuffer(data, np.uint8).copy()
+    out = np.zeros(n32 * w, np.uint8)
+    lib().orc_unbit(w, _ptr(a), n32, _ptr(out))
+    return out.tobytes()
+
+
+def rze(g: int, data: bytes) -> bytes:
+    a = np.frombuffer(data, np.uint8).copy() if len(data) else np.zeros(1, np.uint8)
+    out = np.zeros(2 * len(data) + 64, np.uint8)
+    n = lib().orc_rze(g, _ptr(a), len(data), _ptr(out))
+    return out[:n].tobytes()
+
+
+def unrze(g: int, data: bytes, L: int) -> bytes:
+    a = np.frombuffer(data, np.uint8).copy() if len(data) else np.zeros(1, np.uint8)
+    out = np.zeros(max(L, 1), np.uint8)
+    rc = lib().orc_unrze(g, _ptr(a), len(data), L, _ptr(out))
+    if rc:
+        raise OracleError(rc, "unrze")
+    return out[:L].tobytes()
+
+
+# whole stream ------------------------------------------------------------------
+
+def compress(x: np.ndarray, mode: int = 1, eb: float = 1e-3) -> bytes:
+    x = _c(x)
+    d = make_desc(x.shape, dtype_code(x), mode, eb)
+    cap = lib().orc_compress_bound(C.byref(d))
+    if cap == 0:
+        raise OracleError(INVALID_ARG, "compress_bound")
+    out = np.zeros(cap, np.uint8)
+    sz = C.c_size_t()
+    rc = lib().orc_compress(C.byref(d), _ptr(x), _ptr(out), cap, C.byref(sz))
+    if rc:
+        raise OracleError(rc, "compress")
+    return out[:sz.value].tobytes()
+
+
+def compress_status(x: np.ndarray, mode: int, eb: float, cap: int | None = None) -> int:
+    x = _c(x)
+    d = make_desc(x.shape, dtype_code(x), mode, eb)
+    bound = lib().orc_compress_bound(C.byref(d))
+    if cap is None:
+        cap = bound
+    out = np.zeros(max(cap, 1), np.uint8)
+    sz = C.c_size_t()
+    return lib().orc_compress(C.byref(d), _ptr(x), _ptr(out), cap, C.byref(sz))
+
+
+def peek(stream: bytes) -> Desc:
+    a = np.frombuffer(stream, np.uint8).copy()
+    d = Desc()
+    rc = lib().orc_peek(_ptr(a), a.size, C.byref(d))
+    if rc:
+        raise OracleError(rc, "peek")
+    return d
+
+
+def decompress(stream: bytes) -> np.ndarray:
+    a = np.frombuffer(stream, np.uint8).copy()
+    d = peek(stream)
+    shape = tuple(int(d.dims[k]) for k in range(d.ndim))
+    out = np.empty(shape, np.float32 if d.dtype == 0 else np.float64)
+    rc = lib().orc_decompress(_ptr(a), a.size, _ptr(out), out.nbytes)
+    if rc:
+        raise OracleError(rc, "decompress")
+    return out
+
+
+def decompress_status(stream: bytes, shape, dtype) -> int:
+    a = np.frombuffer(stream, np.uint8).copy() if len(stream) else np.zeros(1, np.uint8)
+    out = np.empty(shape, dtype)
+    return lib().orc_decompress(_ptr(a), len(stream), _ptr(out), out.nbytes)
+
+
+# checkers ------------------------------------------------------------------------
+
+def order_violations(x: np.ndarray, y: np.ndarray) -> int:
+    x, y = _c(x), _c(y)
+    assert x.dtype == y.dtype and x.shape == y.shape
+    d = make_desc(x.shape, dtype_code(x))
+    return int(lib().orc_order_violations(C.byref(d), _ptr(x), _ptr(y)))
+
+
+def critical_types(x: np.ndarray):
+    x = _c(x)
+    d = make_desc(x.shape, dtype_code(x))
+    lo = np.empty(x.shape, np.uint8)
+    up = np.empty(x.shape, np.uint8)
+    lib().orc_critical_types(C.byref(d), _ptr(x), _ptr(lo), _ptr(up))
+    return lo, up
