@@ -1,0 +1,143 @@
+/* lopc.h -- C ABI of the B300 (sm_103a) implementation of the hot path of the
+ * Local-Order-Preserving Compressor (LOPC): error-bounded quantization, local-order
+ * repair (subbins), lossless coding of bins and subbins, and decompression.
+ *
+ * The operations follow "Fast Topology-Aware Lossy Data Compression with Full
+ * Preservation of Critical Points and Local Order":
+ *   - problem statement, ABS and NOA bounds ..................... Sec. III-A
+ *   - half-width quantizer, bins and subbins ..................... Sec. III-A
+ *   - flags and subbin repair (Algorithms 1, 2) .................. Sec. III-B, III-D
+ *   - termination, minimality, resolution ........................ Sec. III-E
+ *   - lossless coding: DIFFNB.BIT.RZE_1 (bins), BIT.RZE_w.RZE_1 (subbins),
+ *     independent 16 KiB chunks ................................... Sec. III-C, II-C
+ *   - decoding (bin, subbin) to a value .......................... Sec. III-D, III-E
+ * Where the paper leaves a choice open (neighbourhood, tie-break direction, exact
+ * quantizer arithmetic, stream layout), the library fixes one reading; the stream
+ * layout is described in the project's design notes.
+ *
+ * Conventions for every entry point:
+ *   - Device pointers ("d_" prefix) point to memory of the current CUDA device;
+ *     host pointers ("h_" prefix, or plain) to host memory.  The caller owns every
+ *     buffer; the library never allocates device memory on these paths.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Work is stream-ordered.  Calls documented as "synchronising" wait for the
+ *     stream once before returning, to report a size or a status.
+ *   - Fields are dense, C order (slowest dimension first): dims[0] x dims[1] for 2D,
+ *     dims[0] x dims[1] x dims[2] for 3D, float32 or float64 values.  The number of
+ *     points must be below 2^32.
+ *   - Every function returns a status (LOPC_OK or a negative LOPC_ERR_*); no C++
+ *     exception crosses the ABI.  After an error the contents of outputs are
+ *     unspecified; the workspace may be reused.
+ */
+#ifndef LOPC_H
+#define LOPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LOPC_API __attribute__((visibility("default")))
+#else
+#define LOPC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LOPC_VERSION 1
+
+/* Status codes. */
+#define LOPC_OK 0
+#define LOPC_ERR_INVALID_ARG (-1)   /* bad descriptor, null pointer, eb <= 0 or not finite */
+#define LOPC_ERR_NONFINITE (-2)     /* NaN or +-Inf in the field */
+#define LOPC_ERR_RANGE (-3)         /* |x|/eps too large for the bin words (2^30 f32, 2^52 f64) */
+#define LOPC_ERR_CAPACITY (-4)      /* output buffer too small */
+#define LOPC_ERR_CORRUPT (-5)       /* stream fails validation */
+#define LOPC_ERR_NOT_CONVERGED (-6) /* repair round cap reached (only with a lowered cap) */
+#define LOPC_ERR_CUDA (-7)          /* a CUDA runtime call failed */
+#define LOPC_ERR_WORKSPACE (-8)     /* workspace missing or smaller than required */
+
+/* Element type and error-bound mode (Sec. III-A). */
+#define LOPC_F32 0
+#define LOPC_F64 1
+#define LOPC_ABS 0 /* |x - x_hat| <= eb */
+#define LOPC_NOA 1 /* |x - x_hat| <= eb * (max(x) - min(x)) */
+
+typedef struct {
+  int32_t dtype;   /* LOPC_F32 or LOPC_F64 */
+  int32_t ndim;    /* 2 or 3 */
+  int64_t dims[3]; /* slowest first; a 2D field uses dims[0..1] and dims[2] = 0 */
+  int32_t mode;    /* LOPC_ABS or LOPC_NOA */
+  int32_t reserved;
+  double eb;       /* error bound, > 0 and finite */
+} lopc_field_desc;
+
+/* Worst-case stream size in bytes for a field (0 for an invalid descriptor). */
+LOPC_API size_t lopc_compress_bound(const lopc_field_desc* desc);
+
+/* Device scratch bytes that lopc_compress needs for this field (0 if invalid). */
+LOPC_API size_t lopc_compress_workspace_size(const lopc_field_desc* desc);
+
+/* Compresses a field (Sec. III): resolves eps (NOA: from the value range), quantizes
+ * every value to a bin of width eps (Sec. III-A), raises subbins to the least values
+ * that keep every neighbour pair's order (Alg. 1-2, Sec. III-E), and encodes bins
+ * and subbins chunk by chunk (Sec. III-C).
+ *   d_x      field values (dtype, dims from desc), device memory, read only
+ *   d_out    stream output, device memory, out_cap bytes (lopc_compress_bound is
+ *            always enough); receives *out_size bytes
+ *   out_size host pointer, receives the stream length
+ *   d_ws     device workspace of ws_size >= lopc_compress_workspace_size bytes
+ * Synchronising (one wait, to read the size and the status).
+ * Errors: INVALID_ARG, NONFINITE, RANGE, CAPACITY, WORKSPACE, NOT_CONVERGED, CUDA. */
+LOPC_API int lopc_compress(const lopc_field_desc* desc, const void* d_x, void* d_out, size_t out_cap,
+                  size_t* out_size, void* d_ws, size_t ws_size, void* stream);
+
+/* Reads the descriptor from the first 128 bytes of a stream held in HOST memory.
+ * Errors: INVALID_ARG (null), CORRUPT (bad header). */
+LOPC_API int lopc_peek(const void* h_stream, size_t n, lopc_field_desc* desc);
+
+/* Device scratch bytes that lopc_decompress needs for streams of this field. */
+LOPC_API size_t lopc_decompress_workspace_size(const lopc_field_desc* desc);
+
+/* Decompresses a stream (Sec. III-D/E): decodes each chunk's bins and subbins and
+ * writes x_hat = the subbin-th representable value above the lowest value of the
+ * bin.  d_in/in_size: the stream in device memory; d_x: output field, x_cap bytes.
+ * Synchronising (reads the 128-byte header to the host, then waits for the status).
+ * Errors: INVALID_ARG, CORRUPT, CAPACITY, WORKSPACE, CUDA. */
+LOPC_API int lopc_decompress(const void* d_in, size_t in_size, void* d_x, size_t x_cap, void* d_ws, size_t ws_size,
+                    void* stream);
+
+/* Runs the quantizer and the repair only and exports their results, for testing
+ * each stage against a reference: d_bins[i] (int64) and d_subbins[i] (uint64), one
+ * per point in C order.  Same workspace as lopc_compress.  Synchronising.
+ * Errors: as lopc_compress (no CAPACITY). */
+LOPC_API int lopc_quantize_repair(const lopc_field_desc* desc, const void* d_x, int64_t* d_bins, uint64_t* d_subbins,
+                         void* d_ws, size_t ws_size, void* stream);
+
+/* Caps the number of global repair rounds of later calls on this thread's library
+ * instance (0 restores the default, which is never reached by a valid field).  A
+ * lowered cap makes lopc_compress return LOPC_ERR_NOT_CONVERGED.  Returns the
+ * previous cap. */
+LOPC_API int64_t lopc_set_round_cap(int64_t cap);
+
+/* Statistics of the last lopc_compress on this thread: repair rounds and tile runs
+ * (first pass plus reruns).  Either pointer may be NULL. */
+LOPC_API void lopc_last_stats(int64_t* rounds, int64_t* tile_runs);
+
+/* Per-kernel timing for measurement: while enabled, every kernel the library
+ * launches is bracketed by CUDA events recorded on the launching stream, and the
+ * elapsed times are added up per kernel when the call returns.  Off by default;
+ * state is per thread.  lopc_profile_read copies up to `cap` entries (kernel name,
+ * launches, total milliseconds) and returns the number of kernels seen. */
+LOPC_API void lopc_profile_enable(int on);
+LOPC_API void lopc_profile_reset(void);
+LOPC_API int lopc_profile_read(const char** names, int64_t* launches, double* total_ms, int cap);
+
+/* Human-readable text of a status code (static storage). */
+LOPC_API const char* lopc_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOPC_H */

@@ -671,6 +671,13 @@ static int dec_subbins(int w, const uint8_t* rec, uint32_t sz, int64_t n, uint64
   return rc;
 }
 
+void orc_encode_chunk(int dtype, const int64_t* b, const uint64_t* s, int64_t n, uint8_t* bin_rec,
+                      uint32_t* bin_size, uint8_t* sub_rec, uint32_t* sub_size) {
+  int w = dtype == 0 ? 4 : 8;
+  *bin_size = enc_bins(w, b, n, bin_rec);
+  *sub_size = enc_subbins(w, s, n, sub_rec);
+}
+
 /* ---------------------------------------------------------------- stream */
 
 #define HDR 128

@@ -69,6 +69,11 @@ void orc_unbit(int w, const uint8_t* in, int64_t n32, uint8_t* words);
 size_t orc_rze(int g, const uint8_t* in, size_t L, uint8_t* out);
 int orc_unrze(int g, const uint8_t* in, size_t in_len, size_t L, uint8_t* out);
 
+/* One chunk's records (Sec. III-C): bins and subbins of its n points in chunk
+ * order; each record buffer needs n*w bytes; sizes carry the raw flag (bit 31). */
+void orc_encode_chunk(int dtype, const int64_t* b, const uint64_t* s, int64_t n, uint8_t* bin_rec,
+                      uint32_t* bin_size, uint8_t* sub_rec, uint32_t* sub_size);
+
 /* Whole stream. */
 size_t orc_compress_bound(const orc_desc* d);
 int orc_compress(const orc_desc* d, const void* x, uint8_t* out, size_t cap, size_t* out_size);

@@ -1,0 +1,229 @@
+"""Python binding of the C ABI in ``include/lopc.h`` (ctypes; marshalling only).
+
+Every step of compression and decompression runs in the CUDA library
+``liblopc.so``; this module passes device pointers of torch tensors, sizes and the
+current CUDA stream.  There is no fallback: if the library is missing, importing
+the binding's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+from typing import Optional, Tuple
+
+import torch
+
+PKG = Path(__file__).resolve().parent
+LIB_PATH = PKG / "liblopc.so"
+
+OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "NONFINITE", -3: "RANGE", -4: "CAPACITY", -5: "CORRUPT",
+          -6: "NOT_CONVERGED", -7: "CUDA", -8: "WORKSPACE"}
+F32, F64 = 0, 1
+ABS, NOA = 0, 1
+
+
+class LopcError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({lib().lopc_strerror(code).decode()})")
+        self.code = code
+
+
+class FieldDesc(C.Structure):
+    _fields_ = [("dtype", C.c_int32), ("ndim", C.c_int32), ("dims", C.c_int64 * 3),
+                ("mode", C.c_int32), ("reserved", C.c_int32), ("eb", C.c_double)]
+
+    @property
+    def shape(self) -> Tuple[int, ...]:
+        return tuple(int(self.dims[k]) for k in range(self.ndim))
+
+    @property
+    def torch_dtype(self):
+        return torch.float32 if self.dtype == F32 else torch.float64
+
+
+_lib = None
+
+
+def lib():
+    """Loads ``liblopc.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2603_26968_b300.build")
+        L = C.CDLL(str(LIB_PATH))
+        P, D = C.c_void_p, C.POINTER(FieldDesc)
+        L.lopc_compress_bound.argtypes = [D]
+        L.lopc_compress_bound.restype = C.c_size_t
+        L.lopc_compress_workspace_size.argtypes = [D]
+        L.lopc_compress_workspace_size.restype = C.c_size_t
+        L.lopc_decompress_workspace_size.argtypes = [D]
+        L.lopc_decompress_workspace_size.restype = C.c_size_t
+        L.lopc_compress.argtypes = [D, P, P, C.c_size_t, C.POINTER(C.c_size_t), P, C.c_size_t, P]
+        L.lopc_peek.argtypes = [P, C.c_size_t, D]
+        L.lopc_decompress.argtypes = [P, C.c_size_t, P, C.c_size_t, P, C.c_size_t, P]
+        L.lopc_quantize_repair.argtypes = [D, P, P, P, P, C.c_size_t, P]
+        L.lopc_set_round_cap.argtypes = [C.c_int64]
+        L.lopc_set_round_cap.restype = C.c_int64
+        L.lopc_last_stats.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.lopc_profile_enable.argtypes = [C.c_int]
+        L.lopc_profile_reset.argtypes = []
+        L.lopc_profile_read.argtypes = [C.POINTER(C.c_char_p), C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int]
+        L.lopc_profile_read.restype = C.c_int
+        L.lopc_strerror.argtypes = [C.c_int]
+        L.lopc_strerror.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def make_desc(shape, dtype, mode: int = NOA, eb: float = 1e-3) -> FieldDesc:
+    d = FieldDesc()
+    if dtype in (torch.float32, F32, "f32"):
+        d.dtype = F32
+    elif dtype in (torch.float64, F64, "f64"):
+        d.dtype = F64
+    else:
+        raise TypeError(dtype)
+    d.ndim = len(shape)
+    for k, n in enumerate(shape):
+        d.dims[k] = int(n)
+    d.mode = int(mode)
+    d.eb = float(eb)
+    return d
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise LopcError(rc, what)
+
+
+def compress_bound(desc: FieldDesc) -> int:
+    return int(lib().lopc_compress_bound(C.byref(desc)))
+
+
+def compress_workspace_size(desc: FieldDesc) -> int:
+    return int(lib().lopc_compress_workspace_size(C.byref(desc)))
+
+
+def decompress_workspace_size(desc: FieldDesc) -> int:
+    return int(lib().lopc_decompress_workspace_size(C.byref(desc)))
+
+
+def _field_desc(x: torch.Tensor, mode: int, eb: float) -> FieldDesc:
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("field must be a contiguous CUDA tensor")
+    return make_desc(tuple(x.shape), x.dtype, mode, eb)
+
+
+def compress(x: torch.Tensor, eb: float, mode: int = NOA, out: Optional[torch.Tensor] = None,
+             workspace: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Compresses a CUDA field; returns the stream as a uint8 CUDA tensor (a view of
+    ``out`` when given)."""
+    d = _field_desc(x, mode, eb)
+    if out is None:
+        out = torch.empty(compress_bound(d), dtype=torch.uint8, device=x.device)
+    if workspace is None:
+        workspace = torch.empty(compress_workspace_size(d), dtype=torch.uint8, device=x.device)
+    size = C.c_size_t()
+    rc = lib().lopc_compress(C.byref(d), C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), out.numel(),
+                             C.byref(size), C.c_void_p(workspace.data_ptr()), workspace.numel(),
+                             C.c_void_p(_stream(stream)))
+    _check(rc, "lopc_compress")
+    return out[: size.value]
+
+
+def peek(stream_bytes) -> FieldDesc:
+    b = bytes(stream_bytes[:128]) if not isinstance(stream_bytes, torch.Tensor) else \
+        bytes(stream_bytes[:128].cpu().numpy().tobytes())
+    buf = C.create_string_buffer(b, len(b))
+    d = FieldDesc()
+    _check(lib().lopc_peek(buf, len(b), C.byref(d)), "lopc_peek")
+    return d
+
+
+def decompress(stream_t: torch.Tensor, out: Optional[torch.Tensor] = None, desc: Optional[FieldDesc] = None,
+               workspace: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Decompresses a stream held in a uint8 CUDA tensor."""
+    if not stream_t.is_cuda:
+        raise ValueError("stream must be a CUDA tensor")
+    if desc is None:
+        desc = peek(stream_t)
+    if out is None:
+        out = torch.empty(desc.shape, dtype=desc.torch_dtype, device=stream_t.device)
+    if workspace is None:
+        workspace = torch.empty(decompress_workspace_size(desc), dtype=torch.uint8, device=stream_t.device)
+    rc = lib().lopc_decompress(C.c_void_p(stream_t.data_ptr()), stream_t.numel(), C.c_void_p(out.data_ptr()),
+                               out.numel() * out.element_size(), C.c_void_p(workspace.data_ptr()),
+                               workspace.numel(), C.c_void_p(_stream(stream)))
+    _check(rc, "lopc_decompress")
+    return out
+
+
+def quantize_repair(x: torch.Tensor, eb: float, mode: int = NOA) -> Tuple[torch.Tensor, torch.Tensor]:
+    """Bins (int64) and subbins (uint64 bits in an int64 tensor) of a CUDA field."""
+    d = _field_desc(x, mode, eb)
+    ws = torch.empty(compress_workspace_size(d), dtype=torch.uint8, device=x.device)
+    b = torch.empty(x.shape, dtype=torch.int64, device=x.device)
+    s = torch.empty(x.shape, dtype=torch.int64, device=x.device)
+    rc = lib().lopc_quantize_repair(C.byref(d), C.c_void_p(x.data_ptr()), C.c_void_p(b.data_ptr()),
+                                    C.c_void_p(s.data_ptr()), C.c_void_p(ws.data_ptr()), ws.numel(),
+                                    C.c_void_p(_stream(None)))
+    _check(rc, "lopc_quantize_repair")
+    return b, s
+
+
+def set_round_cap(cap: int) -> int:
+    return int(lib().lopc_set_round_cap(int(cap)))
+
+
+def last_stats() -> Tuple[int, int]:
+    r, t = C.c_int64(), C.c_int64()
+    lib().lopc_last_stats(C.byref(r), C.byref(t))
+    return r.value, t.value
+
+
+def compress_status(x: torch.Tensor, eb: float, mode: int = NOA, out_cap: Optional[int] = None,
+                    ws_bytes: Optional[int] = None) -> int:
+    """Raw status of lopc_compress (for error-path tests)."""
+    d = _field_desc(x, mode, eb)
+    cap = compress_bound(d) if out_cap is None else out_cap
+    out = torch.empty(max(cap, 1), dtype=torch.uint8, device=x.device)
+    wsz = compress_workspace_size(d) if ws_bytes is None else ws_bytes
+    ws = torch.empty(max(wsz, 1), dtype=torch.uint8, device=x.device)
+    size = C.c_size_t()
+    return lib().lopc_compress(C.byref(d), C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), cap,
+                               C.byref(size), C.c_void_p(ws.data_ptr()), wsz, C.c_void_p(_stream(None)))
+
+
+def decompress_status(stream_t: torch.Tensor, shape, dtype) -> int:
+    out = torch.empty(shape, dtype=dtype, device=stream_t.device)
+    d = make_desc(shape, dtype)
+    ws = torch.empty(decompress_workspace_size(d), dtype=torch.uint8, device=stream_t.device)
+    return lib().lopc_decompress(C.c_void_p(stream_t.data_ptr()), stream_t.numel(), C.c_void_p(out.data_ptr()),
+                                 out.numel() * out.element_size(), C.c_void_p(ws.data_ptr()), ws.numel(),
+                                 C.c_void_p(_stream(None)))
+
+
+def profile_enable(on: bool = True) -> None:
+    """Per-kernel CUDA-event timing inside the library (see include/lopc.h)."""
+    lib().lopc_profile_enable(1 if on else 0)
+
+
+def profile_reset() -> None:
+    lib().lopc_profile_reset()
+
+
+def profile_read() -> dict:
+    """{kernel name: (launches, total milliseconds)} since the last reset."""
+    cap = 64
+    names = (C.c_char_p * cap)()
+    launches = (C.c_int64 * cap)()
+    ms = (C.c_double * cap)()
+    n = lib().lopc_profile_read(names, launches, ms, cap)
+    return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(n, cap))}

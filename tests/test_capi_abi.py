@@ -1,0 +1,73 @@
+"""The C ABI library: it loads without a GPU, exports every function that
+include/lopc.h declares, and its host-only entry points agree with the oracle."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lopc.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2603_26968_b300 import build, lopc
+    build.build()
+    return lopc
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lopc_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert "lopc_compress" in names and "lopc_decompress" in names and len(names) >= 10
+    lib = L.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", str(L.LIB_PATH)], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\s(lopc_\w+)$", out, flags=re.M))
+    assert set(names) <= exported
+    assert all(e in names for e in exported), exported - set(names)
+
+
+def test_strerror_and_invalid_args(L):
+    lib = L.lib()
+    assert lib.lopc_strerror(0) == b"ok"
+    assert lib.lopc_strerror(-5) == b"corrupt stream"
+    bad = L.make_desc((4, 4), "f32", L.NOA, 1e-3)
+    bad.ndim = 4
+    assert lib.lopc_compress_bound(C.byref(bad)) == 0
+    assert lib.lopc_compress_workspace_size(C.byref(bad)) == 0
+    size = C.c_size_t()
+    rc = lib.lopc_compress(C.byref(bad), None, None, 0, C.byref(size), None, 0, None)
+    assert rc == -1
+    good = L.make_desc((4, 4), "f32", L.NOA, 1e-3)
+    good.eb = 0.0
+    assert lib.lopc_compress(C.byref(good), None, None, 0, C.byref(size), None, 0, None) == -1
+    assert lib.lopc_peek(None, 0, C.byref(good)) == -1
+
+
+def test_bounds_cover_the_oracle_streams(L, orc):
+    rng = np.random.default_rng(0)
+    for shape, dt in [((70, 90), np.float32), ((9, 17, 33), np.float64), ((1, 300), np.float32)]:
+        x = np.cumsum(rng.standard_normal(shape), axis=-1).astype(dt)
+        st = orc.compress(x, 1, 1e-4)
+        d = L.make_desc(shape, x.dtype == np.float32 and "f32" or "f64", L.NOA, 1e-4)
+        assert L.compress_bound(d) >= len(st)
+        assert L.compress_workspace_size(d) > 0 and L.decompress_workspace_size(d) > 0
+
+
+def test_peek_reads_oracle_headers(L, orc):
+    x = np.linspace(-1, 1, 5 * 6 * 7).reshape(5, 6, 7)
+    st = orc.compress(x, 0, 1e-3)
+    d = L.peek(st)
+    assert (d.dtype, d.ndim, d.shape, d.mode, d.eb) == (1, 3, (5, 6, 7), 0, 1e-3)
+    with pytest.raises(L.LopcError):
+        L.peek(b"XXXX" + st[4:128])

@@ -1,0 +1,289 @@
+"""GPU parity: the CUDA library's streams and reconstructions are byte-identical to
+the CPU oracle's (the paper's bit-for-bit claim, Sec. I and V), on fields that span
+several tiles with ragged edges, degenerate shapes, heavy ties and deep repair
+chains; plus the error paths.  All calls go through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2603_26968_b300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2603_26968_b300 import build, lopc
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return lopc
+
+
+def gpu_roundtrip(L, x: np.ndarray, mode: int, eb: float):
+    xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    st = L.compress(xt, eb, mode)
+    y = L.decompress(st)
+    torch.cuda.synchronize()
+    return bytes(st.cpu().numpy().tobytes()), y.cpu().numpy()
+
+
+def assert_parity(L, orc, x, mode, eb):
+    st_g, y_g = gpu_roundtrip(L, x, mode, eb)
+    st_o = orc.compress(x, mode, eb)
+    assert len(st_g) == len(st_o), (len(st_g), len(st_o))
+    if st_g != st_o:
+        diff = next(i for i in range(len(st_o)) if st_g[i] != st_o[i])
+        raise AssertionError(f"stream differs at byte {diff} of {len(st_o)}")
+    y_o = orc.decompress(st_o)
+    assert y_g.dtype == y_o.dtype and y_g.shape == y_o.shape
+    assert y_g.tobytes() == y_o.tobytes()
+    # the GPU decoder reads the oracle's stream too (same bytes, so same output)
+    return st_o, y_o
+
+
+def bumps(shape, dtype, seed=1, n=24, noise=1e-4):
+    f = np.zeros(shape, np.float64)
+    S.add_bumps(f, n, max(shape) / 40.0, max(shape) / 5.0, seed)
+    if noise:
+        S.add_uniform_noise(f, noise, seed)
+    return f.astype(dtype)
+
+
+CASES = [
+    ("2d_f32_c1", lambda: S.make_field(S.spec_2d_small()), 1, 1e-3),
+    ("2d_f32_c1_loose", lambda: S.make_field(S.spec_2d_small()), 1, 1e-2),
+    ("2d_f32_c1_tight", lambda: S.make_field(S.spec_2d_small()), 1, 1e-4),
+    ("2d_f32_ragged", lambda: bumps((130, 200), np.float32), 1, 1e-2),
+    ("2d_f64_ragged", lambda: bumps((100, 150), np.float64), 1, 1e-3),
+    ("2d_f64_abs", lambda: bumps((70, 65), np.float64), 0, 2e-3),
+    ("3d_f32_ragged", lambda: S.make_field(S.spec_3d_f32(n=48))[:45, :40, :37].copy(), 1, 1e-3),
+    ("3d_f32_loose", lambda: S.make_field(S.spec_3d_f32(n=48)), 1, 1e-2),
+    ("3d_f32_tight", lambda: S.make_field(S.spec_3d_f32(n=40)), 1, 1e-4),
+    ("3d_f64_ties", lambda: S.make_field(S.spec_3d_f64_ties(shape=(24, 36, 36))), 1, 5e-4),
+    ("3d_f64_ties_ragged", lambda: S.make_field(S.spec_3d_f64_ties(shape=(24, 36, 36)))[:19, :35, :33].copy(), 1, 5e-4),
+    ("3d_f64_abs", lambda: bumps((17, 20, 23), np.float64), 0, 1e-3),
+    ("row_1xN", lambda: bumps((1, 777), np.float32), 1, 1e-2),
+    ("col_Nx1", lambda: bumps((300, 1), np.float64), 1, 1e-2),
+    ("3d_thin_z", lambda: bumps((1, 40, 50), np.float32), 1, 1e-2),
+    ("3d_two_z", lambda: bumps((2, 33, 17), np.float64), 1, 1e-2),
+    ("3d_line", lambda: bumps((70, 1, 1), np.float32), 1, 1e-2),
+    ("tiny_2x2", lambda: np.array([[0.0, 1.0], [1.0, 0.0]], np.float32), 1, 0.6),
+    ("single_point", lambda: np.array([[3.5]], np.float64), 0, 1e-3),
+    ("constant_noa", lambda: np.full((20, 30, 40), -1.25, np.float32), 1, 1e-3),
+    ("integer_plateaus", lambda: np.floor(bumps((40, 40, 40), np.float32, noise=0) * 3), 1, 0.3),
+    ("long_chain_2d", lambda: np.linspace(1.0, 0.0, 2000, dtype=np.float32).reshape(1, 2000), 0, 10.0),
+    ("long_chain_3d", lambda: (-np.arange(30 * 31 * 32, dtype=np.float64)).reshape(30, 31, 32), 0, 1e9),
+    ("neg_zero_mix", lambda: np.array([[0.0, -0.0, 0.0, -0.0], [1e-30, -1e-30, 0.0, -0.0]], np.float32), 0, 0.5),
+    ("denormals", lambda: (np.arange(64, dtype=np.float32).reshape(8, 8) * np.float32(1e-44)), 0, 1e-44),
+]
+
+
+@pytest.mark.parametrize("name,make,mode,eb", CASES, ids=[c[0] for c in CASES])
+def test_stream_and_reconstruction_parity(L, orc, name, make, mode, eb):
+    x = make()
+    assert_parity(L, orc, x, mode, eb)
+
+
+@pytest.mark.parametrize("name,make,mode,eb", CASES[:12], ids=[c[0] for c in CASES[:12]])
+def test_stage_parity_bins_and_subbins(L, orc, name, make, mode, eb):
+    x = make()
+    xt = torch.from_numpy(x).cuda()
+    b_g, s_g = L.quantize_repair(xt, eb, mode)
+    e = orc.resolve_eps(x, mode, eb)
+    b_o = orc.quantize(x, e["inv"])
+    s_o = orc.repair_lfp(x, b_o)
+    assert (b_g.cpu().numpy() == b_o).all()
+    assert (s_g.cpu().numpy().astype(np.uint64) == s_o).all()
+
+
+def test_decoder_reads_oracle_streams_after_gpu_compress(L, orc):
+    x = bumps((90, 110), np.float32, seed=3)
+    st = orc.compress(x, 1, 1e-3)
+    t = torch.frombuffer(bytearray(st), dtype=torch.uint8).cuda()
+    y = L.decompress(t).cpu().numpy()
+    assert y.tobytes() == orc.decompress(st).tobytes()
+
+
+def test_deep_chain_needs_many_rounds(L, orc):
+    x = np.linspace(1.0, 0.0, 2000, dtype=np.float32).reshape(1, 2000)
+    assert_parity(L, orc, x, 0, 10.0)
+    rounds, runs = L.last_stats()  # stats of the last compress (the round trip above)
+    assert rounds >= 10
+
+
+# ------------------------------------------------------------------ error paths
+
+def test_nonfinite(L):
+    x = torch.zeros(40, 50, device="cuda")
+    x[3, 7] = float("nan")
+    assert L.compress_status(x, 1e-3, L.NOA) == -2
+    assert L.compress_status(x, 1e-3, L.ABS) == -2
+    x[3, 7] = float("inf")
+    assert L.compress_status(x.double(), 1e-3, L.ABS) == -2
+
+
+def test_range(L):
+    x = torch.linspace(-1, 1, 4096, device="cuda").reshape(64, 64)
+    assert L.compress_status(x, 1e-12, L.ABS) == -3
+    assert L.compress_status(x.double(), 1e-12, L.ABS) == 0
+
+
+def test_capacity_and_workspace(L, orc):
+    x = bumps((64, 80), np.float32)
+    st = orc.compress(x, 1, 1e-3)
+    xt = torch.from_numpy(x).cuda()
+    assert L.compress_status(xt, 1e-3, L.NOA, out_cap=len(st)) == 0
+    assert L.compress_status(xt, 1e-3, L.NOA, out_cap=len(st) - 1) == -4
+    d = L.make_desc(x.shape, "f32", L.NOA, 1e-3)
+    assert L.compress_status(xt, 1e-3, L.NOA, ws_bytes=L.compress_workspace_size(d) - 1) == -8
+
+
+def test_round_cap_not_converged(L):
+    x = torch.linspace(1.0, 0.0, 2000, device="cuda").reshape(1, 2000)
+    old = L.set_round_cap(2)
+    try:
+        assert L.compress_status(x, 10.0, L.ABS) == -6
+    finally:
+        L.set_round_cap(old)
+    assert L.compress_status(x, 10.0, L.ABS) == 0
+
+
+def test_corrupt_streams_never_fault(L, orc):
+    x = bumps((70, 90), np.float32, seed=9)
+    st = orc.compress(x, 1, 1e-3)
+    rng = np.random.default_rng(0)
+    dev = torch.device("cuda")
+    # truncated
+    for cut in (len(st) - 16, 200, 100):
+        t = torch.frombuffer(bytearray(st[:cut]), dtype=torch.uint8).to(dev)
+        assert L.decompress_status(t, x.shape, torch.float32) == -5
+    # bit flips past the header
+    outcomes = set()
+    for k in range(60):
+        b = bytearray(st)
+        pos = 128 + int(rng.integers(0, len(st) - 128))
+        b[pos] ^= 1 << int(rng.integers(0, 8))
+        t = torch.frombuffer(b, dtype=torch.uint8).to(dev)
+        rc = L.decompress_status(t, x.shape, torch.float32)
+        assert rc in (0, -5)
+        outcomes.add(rc)
+        rc_o = orc.decompress_status(bytes(b), x.shape, x.dtype)
+        if rc_o == orc.CORRUPT:
+            assert rc == -5
+    assert -5 in outcomes
+    torch.cuda.synchronize()
+
+
+# ------------------------------------------------------------ full-size configs
+
+def lfp_local_equality(x: torch.Tensor, b: torch.Tensor, s: torch.Tensor) -> int:
+    """Counts points where s(p) != max(0, max over same-bin lower neighbours n of
+    s(n) + [idx_n > idx_p]).  On the acyclic constraint graph this equation has one
+    solution, the least fixpoint, so zero mismatches pins s exactly."""
+    if x.dim() == 2:
+        x, b, s = x[None], b[None], s[None]
+    need = torch.zeros_like(s)
+    nz, ny, nx = x.shape
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                if dz == dy == dx == 0:
+                    continue
+                for sign in (-1, 1):
+                    oz, oy, ox = sign * dz, sign * dy, sign * dx
+                    zp = slice(max(0, -oz), nz - max(0, oz))
+                    yp = slice(max(0, -oy), ny - max(0, oy))
+                    xp = slice(max(0, -ox), nx - max(0, ox))
+                    zn = slice(max(0, oz), nz - max(0, -oz))
+                    yn = slice(max(0, oy), ny - max(0, -oy))
+                    xn = slice(max(0, ox), nx - max(0, -ox))
+                    xv, nv = x[zp, yp, xp], x[zn, yn, xn]
+                    same = b[zp, yp, xp] == b[zn, yn, xn]
+                    # neighbour index is higher for sign > 0: it precedes only if strictly lower
+                    lower = (nv < xv) if sign > 0 else (nv <= xv)
+                    cand = torch.where(same & lower, s[zn, yn, xn] + (1 if sign > 0 else 0), torch.zeros_like(s[zn, yn, xn]))
+                    torch.maximum(need[zp, yp, xp], cand, out=need[zp, yp, xp])
+    return int((need != s).sum().item())
+
+
+def order_mismatches(x: torch.Tensor, y: torch.Tensor) -> int:
+    if x.dim() == 2:
+        x, y = x[None], y[None]
+    nz, ny, nx = x.shape
+    bad = 0
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                if dz == dy == dx == 0:
+                    continue
+                a = (slice(0, nz - dz), slice(0, ny - dy), slice(0, nx - dx))
+                c = (slice(dz, nz), slice(dy, ny), slice(dx, nx))
+                # the neighbour c has the higher index: it is below a only if strictly lower
+                bad += int(((x[c] < x[a]) != (y[c] < y[a])).sum().item())
+    return bad
+
+
+def split_stream(st: bytes):
+    nch = int.from_bytes(st[80:88], "little")
+    tab = np.frombuffer(st[128:128 + 8 * nch], np.uint32)
+    o = 128 + (8 * nch + 15) // 16 * 16
+    offs = []
+    for v in tab:
+        offs.append(o)
+        o += ((int(v) & 0x7FFFFFFF) + 15) // 16 * 16
+    return tab, offs
+
+
+def tile_points(shape, tile, tid):
+    sh = (1,) + tuple(shape) if len(shape) == 2 else tuple(shape)
+    nt = [-(-sh[k] // tile[k]) for k in range(3)]
+    tz, rem = divmod(tid, nt[1] * nt[2])
+    ty, tx = divmod(rem, nt[2])
+    z0, y0, x0 = tz * tile[0], ty * tile[1], tx * tile[2]
+    z1, y1, x1 = min(z0 + tile[0], sh[0]), min(y0 + tile[1], sh[1]), min(x0 + tile[2], sh[2])
+    zz, yy, xx = np.meshgrid(np.arange(z0, z1), np.arange(y0, y1), np.arange(x0, x1), indexing="ij")
+    return ((zz * sh[1] + yy) * sh[2] + xx).ravel()
+
+
+FULL = [
+    ("c2_f32_512", lambda: S.make_field(S.spec_3d_f32(n=512)), 1, 1e-3, (16, 16, 16)),
+    ("c3_f64_ties", lambda: S.make_field(S.spec_3d_f64_ties()), 1, 5e-4, (8, 16, 16)),
+]
+
+
+@pytest.mark.parametrize("name,make,mode,eb,tile", FULL, ids=[f[0] for f in FULL])
+def test_full_size_sampled_parity(L, orc, name, make, mode, eb, tile):
+    x = make()
+    dc = 0 if x.dtype == np.float32 else 1
+    xt = torch.from_numpy(x).cuda()
+    st_t = L.compress(xt, eb, mode)
+    st = bytes(st_t.cpu().numpy().tobytes())
+    b_t, s_t = L.quantize_repair(xt, eb, mode)
+    e = orc.resolve_eps(x, mode, eb)
+    rng = np.random.default_rng(0)
+    # bins at sampled points against the oracle's exact quantizer
+    idx = rng.integers(0, x.size, 20000)
+    xf = x.ravel()
+    bf = b_t.view(-1)[torch.from_numpy(idx).cuda()].cpu().numpy()
+    assert all(orc.q1(dc, float(xf[i]), e["inv"]) == int(bf[k]) for k, i in enumerate(idx))
+    # subbins: the least-fixpoint equation holds at every point
+    xd = xt.double() if dc == 0 else xt
+    assert lfp_local_equality(xd, b_t, s_t) == 0
+    # sampled chunks: the oracle encodes the same records from these bins/subbins
+    tab, offs = split_stream(st)
+    nch = len(tab) // 2
+    bn, sn = b_t.view(-1).cpu().numpy(), s_t.view(-1).cpu().numpy().astype(np.uint64)
+    for tid in list(rng.integers(0, nch, 40)) + [0, nch - 1]:
+        pts = tile_points(x.shape, tile, int(tid))
+        sb, rb, ss, rs = orc.encode_chunk(dc, bn[pts], sn[pts])
+        assert int(tab[tid]) == sb and st[offs[tid]:offs[tid] + (sb & 0x7FFFFFFF)] == rb
+        assert int(tab[nch + tid]) == ss and st[offs[nch + tid]:offs[nch + tid] + (ss & 0x7FFFFFFF)] == rs
+    # decompression: error bound, x_hat <= x, neighbour order, sampled values
+    y = L.decompress(st_t)
+    yd = y.double()
+    assert bool((yd <= xd).all()) and float((xd - yd).max()) < e["eps"]
+    assert order_mismatches(xd, yd) == 0
+    ys = y.view(-1)[torch.from_numpy(idx[:2000]).cuda()].cpu().numpy()
+    want = orc.reconstruct(dc, bf[:2000], sn[idx[:2000]], e["inv"])
+    assert ys.tobytes() == want.tobytes()
