@@ -108,6 +108,27 @@ LOPC_API size_t lopc_decompress_workspace_size(const lopc_field_desc* desc);
 LOPC_API int lopc_decompress(const void* d_in, size_t in_size, void* d_x, size_t x_cap, void* d_ws, size_t ws_size,
                     void* stream);
 
+/* Decompression that allocates nothing and takes no workspace (the paper has no
+ * counterpart; this is a library convenience).  It is meant for callers that cannot
+ * call cudaMalloc: code running inside a memory allocator's callbacks, under a host
+ * framework that reserves all device memory up front, or on paths that must not
+ * take the driver's allocation locks.  Same arguments and result as
+ * lopc_decompress minus the workspace.
+ *   - Scratch lives in a fixed device array of the library (1 MiB + 256 bytes on
+ *     every GPU that loads it, held until the process exits), so streams of at most
+ *     lopc_noalloc_max_chunks() chunks (65536: 256 Mi float32 or 128 Mi float64
+ *     points) are accepted; larger ones return LOPC_ERR_WORKSPACE before any work.
+ *   - The first call on a device looks up the array's device address (one
+ *     cudaGetSymbolAddress with that device current); make that first call before
+ *     any stream capture.
+ *   - All calls share the array: calls whose work overlaps on the GPU (other streams,
+ *     other host threads) race and must be serialised by the caller.
+ * Synchronising.  Errors: INVALID_ARG, CORRUPT, CAPACITY, WORKSPACE, CUDA. */
+LOPC_API int lopc_decompress_noalloc(const void* d_in, size_t in_size, void* d_x, size_t x_cap, void* stream);
+
+/* Largest chunk count lopc_decompress_noalloc accepts. */
+LOPC_API int64_t lopc_noalloc_max_chunks(void);
+
 /* Runs the quantizer and the repair only and exports their results, for testing
  * each stage against a reference: d_bins[i] (int64) and d_subbins[i] (uint64), one
  * per point in C order.  Same workspace as lopc_compress.  Synchronising.

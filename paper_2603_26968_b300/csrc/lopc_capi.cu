@@ -4,6 +4,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "lopc.h"
 #include "lopc_decompress.cuh"
 
@@ -482,6 +484,73 @@ static int decompress_entry(const void* d_in, size_t in_size, void* d_x, size_t 
   return H.d.ndim == 2 ? decompress_impl<double, 2>(H, in, in_size, d_x, ws, st)
                        : decompress_impl<double, 3>(H, in, in_size, d_x, ws, st);
 }
+
+// ------------------------------------------------- decompression without allocation
+// For callers that cannot allocate device memory: code running where cudaMalloc is
+// off limits (inside a caching allocator's own callbacks, in a process whose memory
+// is reserved up front by a host framework, or on a path that must not take the
+// driver's allocation locks).  The decompressor's scratch, a status word and two
+// 64-bit record offsets per chunk, lives in this fixed device array instead of a
+// caller workspace.  Every GPU that loads the library holds it until the process
+// exits.
+constexpr int64_t kNoAllocMaxChunks = 65536;
+constexpr size_t kNoAllocScratchBytes = 256 + 16 * (size_t)kNoAllocMaxChunks;  // 1 MiB + 256 B
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once per
+// device.  In host code the array's name is only a stand-in, so the address must
+// come from cudaGetSymbolAddress with that device current.
+int noalloc_scratch(uint8_t** out) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return LOPC_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = reinterpret_cast<uint8_t*>(g_noalloc_addr[dev]);
+  return LOPC_OK;
+}
+}  // namespace
+
+int lopc_decompress_noalloc(const void* d_in, size_t in_size, void* d_x, size_t x_cap, void* stream) {
+  if (!d_in || !d_x) return LOPC_ERR_INVALID_ARG;
+  if (in_size < (size_t)kHeaderBytes) return LOPC_ERR_CORRUPT;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint8_t* ws = nullptr;
+  int rc = noalloc_scratch(&ws);
+  if (rc) return rc;
+  uint8_t hb[kHeaderBytes];
+  CK(cudaMemcpyAsync(hb, d_in, kHeaderBytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  Header H;
+  rc = parse_header(hb, in_size, &H);
+  if (rc) return rc;
+  const Geometry g = geometry_of(&H.d);
+  if (g.ntiles > kNoAllocMaxChunks) return LOPC_ERR_WORKSPACE;  // beyond the fixed scratch
+  if (H.total > in_size) return LOPC_ERR_CORRUPT;
+  const size_t need = (size_t)(g.nz * g.ny * g.nx) * word_bytes(H.d.dtype);
+  if (x_cap < need) return LOPC_ERR_CAPACITY;
+  const uint8_t* in = reinterpret_cast<const uint8_t*>(d_in);
+  // decompress_impl zeroes the status word and rewrites every offset it reads
+  if (H.d.dtype == LOPC_F32)
+    rc = H.d.ndim == 2 ? decompress_impl<float, 2>(H, in, in_size, d_x, ws, st)
+                       : decompress_impl<float, 3>(H, in, in_size, d_x, ws, st);
+  else
+    rc = H.d.ndim == 2 ? decompress_impl<double, 2>(H, in, in_size, d_x, ws, st)
+                       : decompress_impl<double, 3>(H, in, in_size, d_x, ws, st);
+  g_prof.resolve();
+  return rc;
+}
+
+int64_t lopc_noalloc_max_chunks(void) { return kNoAllocMaxChunks; }
 
 int64_t lopc_set_round_cap(int64_t cap) {
   const int64_t old = g_round_cap;

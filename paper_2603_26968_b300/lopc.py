@@ -62,6 +62,8 @@ def lib():
         L.lopc_compress.argtypes = [D, P, P, C.c_size_t, C.POINTER(C.c_size_t), P, C.c_size_t, P]
         L.lopc_peek.argtypes = [P, C.c_size_t, D]
         L.lopc_decompress.argtypes = [P, C.c_size_t, P, C.c_size_t, P, C.c_size_t, P]
+        L.lopc_decompress_noalloc.argtypes = [P, C.c_size_t, P, C.c_size_t, P]
+        L.lopc_noalloc_max_chunks.restype = C.c_int64
         L.lopc_quantize_repair.argtypes = [D, P, P, P, P, C.c_size_t, P]
         L.lopc_set_round_cap.argtypes = [C.c_int64]
         L.lopc_set_round_cap.restype = C.c_int64
@@ -163,6 +165,15 @@ def decompress(stream_t: torch.Tensor, out: Optional[torch.Tensor] = None, desc:
                                workspace.numel(), C.c_void_p(_stream(stream)))
     _check(rc, "lopc_decompress")
     return out
+
+
+def decompress_noalloc(stream_t: torch.Tensor, out: torch.Tensor, stream=None) -> int:
+    """Status of lopc_decompress_noalloc: decompression into ``out`` with the
+    library's fixed scratch instead of a workspace (for callers that cannot
+    allocate device memory; see include/lopc.h)."""
+    return lib().lopc_decompress_noalloc(C.c_void_p(stream_t.data_ptr()), stream_t.numel(),
+                                         C.c_void_p(out.data_ptr()), out.numel() * out.element_size(),
+                                         C.c_void_p(_stream(stream)))
 
 
 def quantize_repair(x: torch.Tensor, eb: float, mode: int = NOA) -> Tuple[torch.Tensor, torch.Tensor]:
