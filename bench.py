@@ -221,6 +221,9 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
     rounds, runs = lopc.last_stats()
+    sweeps, sweeps_max = lopc.last_fixpoint_stats()
+    phases = dict(zip(["pass_load", "pass_flags", "pass_fixpoint", "pass_writeback", "pass_bin_record",
+                       "rerun_load", "rerun_fixpoint", "unused"], lopc.last_phase_cycles()))
     hbm, peak_kind = peaks()
     cr = nbytes / ssize
     w = 4
@@ -231,7 +234,10 @@ def main():
 
     # per-kernel table and the dominant kernel's roofline
     npts = nbytes // w
-    algo_bytes = {"range": nbytes, "tile_pass": nbytes, "encode": ssize, "decode": ssize + nbytes,
+    # algorithmic bytes per step of each kernel: what the method must move (range and
+    # tile pass read x; the subbin encoder writes its records; decode reads the stream
+    # and writes x_hat); a rerun must read the subbins and masks of the tiles it reruns
+    algo_bytes = {"range": nbytes, "tile_pass": nbytes, "encode_subbins": ssize, "decode": ssize + nbytes,
                   "pack": 2 * ssize}
     kern = {}
     for name, (launches, total_ms) in prof.items():
@@ -243,8 +249,8 @@ def main():
         if dom in algo_bytes:
             bytes_per_launch = algo_bytes[dom] / per_step_launches
         elif dom == "tile_rerun":
-            # a rerun re-reads the x of the tiles it processes: counted as w per point rerun
-            bytes_per_launch = (runs - npts / 4096) * 4096 * w / max(1, rounds)
+            # a rerun reads the subbins (4 B) and lower masks (2 B) of its tiles' points
+            bytes_per_launch = (runs - npts / 4096) * 4096 * 6 / max(1, rounds)
         else:
             bytes_per_launch = 0
         achieved = bytes_per_launch / (kern[dom]["ms_per_launch"] * 1e-3) / 1e9
@@ -257,7 +263,8 @@ def main():
     for eb in [float(v) for v in args.extra_ebs.split(",") if v]:
         t2, c2, d2, s2, _ = timed(eb, max(1, args.steps // 2), 1)
         r2, n2 = lopc.last_stats()
-        extra[f"{eb:g}"] = {"ms_per_step": float(t2.mean()), "compress_gbs": nbytes / (c2.mean() * 1e-3) / 1e9,
+        f2 = lopc.last_fixpoint_stats()
+        extra[f"{eb:g}"] = {"fixpoint_sweeps": f2[0], "fixpoint_sweeps_max": f2[1], "ms_per_step": float(t2.mean()), "compress_gbs": nbytes / (c2.mean() * 1e-3) / 1e9,
                             "decompress_gbs": nbytes / (d2.mean() * 1e-3) / 1e9, "cr": nbytes / s2,
                             "repair_rounds": r2, "tile_runs": n2}
 
@@ -299,7 +306,8 @@ def main():
                                    f"{args.eb:g}; step = compress + decompress", "field_bytes": nbytes,
                        "parallelism": "replicas" if world > 1 else "single", "l2": "flushed between steps (256 MB write); input 512 MB > L2"},
             "compress": {"gbs": comp_gbs, "ms": float(tc.mean()), "hbm_frac_algorithmic": algo_comp / (tc.mean() * 1e-3) / 1e9 / hbm,
-                         "input_frac": comp_gbs / hbm, "cr": cr, "repair_rounds": rounds, "tile_runs": runs},
+                         "input_frac": comp_gbs / hbm, "cr": cr, "repair_rounds": rounds, "tile_runs": runs,
+                         "fixpoint_sweeps": sweeps, "fixpoint_sweeps_max": sweeps_max, "phase_cycles": phases},
             "decompress": {"gbs": dec_gbs, "ms": float(td.mean()), "hbm_frac_algorithmic": algo_dec / (td.mean() * 1e-3) / 1e9 / hbm},
             "other_bounds": extra,
             "kernels": kern,

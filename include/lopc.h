@@ -146,6 +146,16 @@ LOPC_API int64_t lopc_set_round_cap(int64_t cap);
  * (first pass plus reruns).  Either pointer may be NULL. */
 LOPC_API void lopc_last_stats(int64_t* rounds, int64_t* tile_runs);
 
+/* Statistics of the last compression on this thread: block-wide sweeps of the
+ * tile-local fixpoint summed over all tile runs, and the largest count of one run. */
+LOPC_API void lopc_last_fixpoint_stats(int64_t* sweeps_total, int64_t* sweeps_max);
+
+/* Measurement aid: SM cycles of the last compression on this thread, summed over
+ * blocks, per phase: 0 tile load + quantization, 1 flags, 2 tile fixpoint, 3 state
+ * write-back + marking, 4 bin record, 5 rerun load, 6 rerun fixpoint, 7 unused.
+ * Copies min(n, 8) values and returns 8. */
+LOPC_API int lopc_last_phase_cycles(int64_t* cycles, int n);
+
 /* Per-kernel timing for measurement: while enabled, every kernel the library
  * launches is bracketed by CUDA events recorded on the launching stream, and the
  * elapsed times are added up per kernel when the call returns.  Off by default;

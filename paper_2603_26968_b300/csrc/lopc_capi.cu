@@ -86,7 +86,8 @@ thread_local Profiler g_prof;
     __VA_ARGS__;                    \
     g_prof.after(st);               \
   } while (0)
-thread_local int64_t g_last_rounds = 0, g_last_tile_runs = 0;
+thread_local int64_t g_last_rounds = 0, g_last_tile_runs = 0, g_last_fix_iters = 0, g_last_fix_iters_max = 0;
+thread_local int64_t g_last_phase[8] = {};
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -135,25 +136,26 @@ Geometry geometry_of(const lopc_field_desc* d) {
 }
 
 struct CompressLayout {
-  size_t params, dirty, list, s, b, sizes, offs, slots, total;
+  size_t params, dirty, done, list, s, cm, sizes, offs, slots, total;
 };
 
 CompressLayout compress_layout(const lopc_field_desc* d) {
   const Geometry g = geometry_of(d);
   const size_t n = (size_t)(g.nz * g.ny * g.nx);
-  const size_t W = (size_t)word_bytes(d->dtype);
   CompressLayout L;
   size_t o = 0;
   L.params = o;
   o = align256(o + sizeof(Params));
   L.dirty = o;
   o = align256(o + (size_t)g.ntiles);
+  L.done = o;
+  o = align256(o + (size_t)g.ntiles);
   L.list = o;
   o = align256(o + 4 * (size_t)g.ntiles);
   L.s = o;
   o = align256(o + 4 * n);
-  L.b = o;
-  o = align256(o + W * n);
+  L.cm = o;
+  o = align256(o + 2 * n);
   L.sizes = o;
   o = align256(o + 8 * (size_t)g.ntiles);
   L.offs = o;
@@ -183,26 +185,30 @@ int status_to_code(unsigned int st) {
 
 template <typename T, int ND>
 int run_repair(const lopc_field_desc* d, const Geometry& g, const T* x, uint8_t* ws, const CompressLayout& L,
-               cudaStream_t st) {
+               int64_t* bins_out, cudaStream_t st) {
   using C = TileCfg<T, ND>;
-  using B = typename Traits<T>::Bin;
   Params* P = reinterpret_cast<Params*>(ws + L.params);
   uint8_t* dirty = ws + L.dirty;
   uint32_t* list = reinterpret_cast<uint32_t*>(ws + L.list);
   uint32_t* s = reinterpret_cast<uint32_t*>(ws + L.s);
-  B* b = reinterpret_cast<B*>(ws + L.b);
+  uint16_t* cm = reinterpret_cast<uint16_t*>(ws + L.cm);
+  uint32_t* sizes = reinterpret_cast<uint32_t*>(ws + L.sizes);
   const int64_t n = g.nz * g.ny * g.nx;
 
   LAUNCH("init_params", st, k_init_params<<<1, 1, 0, st>>>(P, d->eb, d->mode));
   if (d->mode == LOPC_NOA) LAUNCH("range", st, k_range<T><<<148 * 8, 256, 0, st>>>(x, n, P));
   LAUNCH("resolve_eps", st, k_resolve_eps<T><<<1, 1, 0, st>>>(P));
   CK(cudaMemsetAsync(dirty, 0, (size_t)g.ntiles, st));
-  const size_t smem = TileSmem<T, ND>::bytes();
-  CK(cudaFuncSetAttribute(k_tile<T, ND, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  CK(cudaFuncSetAttribute(k_tile<T, ND, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  LAUNCH("tile_pass", st, k_tile<T, ND, 0><<<(unsigned)g.ntiles, C::NT, smem, st>>>(x, g, P, s, b, dirty, nullptr));
+  const size_t psmem = PassSmem<T, ND>::bytes(), rsmem = RerunSmem<T, ND>::bytes();
+  CK(cudaFuncSetAttribute(k_pass<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
+  CK(cudaFuncSetAttribute(k_rerun<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem));
+  LAUNCH("tile_pass", st,
+         k_pass<T, ND><<<(unsigned)g.ntiles, C::NT, psmem, st>>>(x, g, P, s, cm, bins_out, ws + L.slots, sizes));
   CK(cudaGetLastError());
-  int64_t runs = g.ntiles, rounds = 0;
+  // round 1 visits every tile: each one tests its own incoming cross-tile constraints
+  LAUNCH("tile_rerun", st, k_rerun<T, ND><<<(unsigned)g.ntiles, C::NT, rsmem, st>>>(g, P, s, cm, dirty, nullptr));
+  CK(cudaGetLastError());
+  int64_t runs = 2 * g.ntiles, rounds = 1;
   const int64_t cap = g_round_cap > 0 ? g_round_cap : n + 16;  // a chain has fewer than n links
   const unsigned cgrid = (unsigned)imin64(ceil_div(g.ntiles, 256), 148 * 16);
   while (true) {
@@ -220,7 +226,7 @@ int run_repair(const lopc_field_desc* d, const Geometry& g, const T* x, uint8_t*
       CK(cudaStreamSynchronize(st));
       break;
     }
-    LAUNCH("tile_rerun", st, k_tile<T, ND, 1><<<cnt, C::NT, smem, st>>>(x, g, P, s, b, dirty, list));
+    LAUNCH("tile_rerun", st, k_rerun<T, ND><<<cnt, C::NT, rsmem, st>>>(g, P, s, cm, dirty, list));
     CK(cudaGetLastError());
     runs += cnt;
     ++rounds;
@@ -239,14 +245,15 @@ int compress_impl(const lopc_field_desc* d, const void* d_x, void* d_out, size_t
   const CompressLayout L = compress_layout(d);
   uint8_t* ws = reinterpret_cast<uint8_t*>(d_ws);
   Params* P = reinterpret_cast<Params*>(ws + L.params);
-  int rc = run_repair<T, ND>(d, g, reinterpret_cast<const T*>(d_x), ws, L, st);
+  int rc = run_repair<T, ND>(d, g, reinterpret_cast<const T*>(d_x), ws, L, nullptr, st);
   if (rc) return rc;
   const size_t esmem = EncSmem<T, ND>::bytes();
-  CK(cudaFuncSetAttribute(k_encode<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esmem));
+  CK(cudaFuncSetAttribute(k_encode_sub<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esmem));
   uint32_t* sizes = reinterpret_cast<uint32_t*>(ws + L.sizes);
   uint64_t* offs = reinterpret_cast<uint64_t*>(ws + L.offs);
-  LAUNCH("encode", st, k_encode<T, ND><<<(unsigned)g.ntiles, C::NT, esmem, st>>>(g, P, reinterpret_cast<const uint32_t*>(ws + L.s),
-                                                            reinterpret_cast<const B*>(ws + L.b), ws + L.slots, sizes));
+  LAUNCH("encode_subbins", st,
+         k_encode_sub<T, ND><<<(unsigned)g.ntiles, C::NT, esmem, st>>>(g, P, reinterpret_cast<const uint32_t*>(ws + L.s),
+                                                                     ws + L.slots, sizes));
   CK(cudaGetLastError());
   const int64_t m = 2 * g.ntiles;
   const uint64_t base = kHeaderBytes + ((uint64_t)m * 4 + 15) / 16 * 16;
@@ -267,6 +274,9 @@ int compress_impl(const lopc_field_desc* d, const void* d_x, void* d_out, size_t
   Params hp;
   CK(cudaMemcpyAsync(&hp, P, sizeof(Params), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  g_last_fix_iters = (int64_t)hp.fix_iters;
+  g_last_fix_iters_max = (int64_t)hp.fix_iters_max;
+  for (int k = 0; k < 8; ++k) g_last_phase[k] = (int64_t)hp.phase[k];
   rc = status_to_code(hp.status);
   if (rc) return rc;
   if (hp.total > out_cap) return LOPC_ERR_CAPACITY;
@@ -277,19 +287,19 @@ int compress_impl(const lopc_field_desc* d, const void* d_x, void* d_out, size_t
 template <typename T, int ND>
 int quantize_repair_impl(const lopc_field_desc* d, const void* d_x, int64_t* bins, uint64_t* subbins, void* d_ws,
                          cudaStream_t st) {
-  using B = typename Traits<T>::Bin;
   const Geometry g = geometry_of(d);
   const CompressLayout L = compress_layout(d);
   uint8_t* ws = reinterpret_cast<uint8_t*>(d_ws);
-  int rc = run_repair<T, ND>(d, g, reinterpret_cast<const T*>(d_x), ws, L, st);
+  int rc = run_repair<T, ND>(d, g, reinterpret_cast<const T*>(d_x), ws, L, bins, st);
   if (rc) return rc;
   const int64_t n = g.nz * g.ny * g.nx;
-  LAUNCH("export", st, k_export<T><<<148 * 8, 256, 0, st>>>(n, reinterpret_cast<const uint32_t*>(ws + L.s),
-                                       reinterpret_cast<const B*>(ws + L.b), bins, subbins));
+  LAUNCH("export", st, k_export_subbins<<<148 * 8, 256, 0, st>>>(n, reinterpret_cast<const uint32_t*>(ws + L.s), subbins));
   CK(cudaGetLastError());
   Params hp;
   CK(cudaMemcpyAsync(&hp, ws + L.params, sizeof(Params), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  g_last_fix_iters = (int64_t)hp.fix_iters;
+  g_last_fix_iters_max = (int64_t)hp.fix_iters_max;
   return status_to_code(hp.status);
 }
 
@@ -561,6 +571,16 @@ int64_t lopc_set_round_cap(int64_t cap) {
 void lopc_last_stats(int64_t* rounds, int64_t* tile_runs) {
   if (rounds) *rounds = g_last_rounds;
   if (tile_runs) *tile_runs = g_last_tile_runs;
+}
+
+void lopc_last_fixpoint_stats(int64_t* sweeps_total, int64_t* sweeps_max) {
+  if (sweeps_total) *sweeps_total = g_last_fix_iters;
+  if (sweeps_max) *sweeps_max = g_last_fix_iters_max;
+}
+
+int lopc_last_phase_cycles(int64_t* cycles, int n) {
+  for (int k = 0; k < n && k < 8; ++k) cycles[k] = g_last_phase[k];
+  return 8;
 }
 
 void lopc_profile_enable(int on) {

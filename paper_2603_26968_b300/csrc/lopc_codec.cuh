@@ -1,0 +1,367 @@
+// lopc_codec.cuh -- block-cooperative lossless stages on shared memory (Sec. III-C):
+// BIT_w bit-plane transposes with warp ballots, and RZE_g (repeated zero
+// elimination with a twice repeat-eliminated bitmap) as word-level encode/decode,
+// plus 16-byte copies between a staged record and global memory.
+#pragma once
+#include "lopc_device.cuh"
+
+namespace lopc {
+
+// ------------------------------------------------------------- BIT_w stage
+
+// 32 x 32 bit-matrix transpose across a warp: lane r holds row r (bit c = column
+// c) on entry and column r on exit.  Five butterfly stages swap the off-diagonal
+// s x s blocks between lanes r and r ^ s.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const uint32_t m = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu : s == 2 ? 0x33333333u : 0x55555555u;
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, s);
+    x = (lane & s) ? ((x & ~m) | ((y & ~m) >> s)) : ((x & m) | ((y & m) << s));
+  }
+  return x;
+}
+
+// Bit-plane transpose of n32 words (a multiple of 32): plane k (k = 0 least
+// significant) is n32/32 u32 words, bit j of word g being bit k of word 32g+j.
+// `word(i)` supplies input word i (zero for padding).  One warp per group of 32.
+template <int NT, int W, typename WordFn>
+__device__ __forceinline__ void bit_transpose(int n32, WordFn word, uint32_t* planes) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int G = n32 >> 5;
+  for (int g = wid; g < G; g += NT / 32) {
+    const uint64_t v = word(32 * g + lane);
+    planes[lane * G + g] = warp_transpose32((uint32_t)v);
+    if (W == 8) planes[(32 + lane) * G + g] = warp_transpose32((uint32_t)(v >> 32));
+  }
+}
+
+// Inverse of bit_transpose: `emit(i, word)` receives word i of the n32.
+template <int NT, int W, typename EmitFn>
+__device__ __forceinline__ void bit_untranspose(int n32, const uint32_t* planes, EmitFn emit) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int G = n32 >> 5;
+  for (int g = wid; g < G; g += NT / 32) {
+    const uint32_t lo = warp_transpose32(planes[lane * G + g]);
+    const uint32_t hi = W == 8 ? warp_transpose32(planes[(32 + lane) * G + g]) : 0u;
+    emit(32 * g + lane, (uint64_t)lo | ((uint64_t)hi << 32));
+  }
+}
+
+// ------------------------------------------------------------- RZE_g stage
+
+// Scratch of one RZE pass over at most Lmax bytes.
+struct RzeWork {
+  uint8_t* m0;    // level-0 bitmap, >= Lmax/8 + 8 bytes
+  uint8_t* m1;    // level-1 bitmap, >= Lmax/64 + 8 bytes
+  uint8_t* m2;    // level-2 bitmap, >= Lmax/512 + 8 bytes
+  uint32_t* pre;  // prefix counts of m1 words, >= Lmax/256 + 8 words
+  uint32_t* tmp;  // scan slots, >= 40 words
+  static constexpr size_t a16(size_t v) { return (v + 15) & ~(size_t)15; }
+  static constexpr size_t bytes(uint32_t Lmax) {
+    return a16(Lmax / 8 + 16) + a16(Lmax / 64 + 16) + a16(Lmax / 512 + 16) + ((size_t)Lmax / 256 + 8) * 4 + 40 * 4;
+  }
+};
+
+// Carves the scratch out of `base` (16-byte aligned); every part is 16-byte aligned.
+__device__ __forceinline__ RzeWork rze_work_at(uint8_t* base, uint32_t Lmax) {
+  RzeWork w;
+  w.m0 = base;
+  w.m1 = w.m0 + RzeWork::a16(Lmax / 8 + 16);
+  w.m2 = w.m1 + RzeWork::a16(Lmax / 64 + 16);
+  w.pre = reinterpret_cast<uint32_t*>(w.m2 + RzeWork::a16(Lmax / 512 + 16));
+  w.tmp = w.pre + Lmax / 256 + 8;
+  return w;
+}
+
+__device__ __forceinline__ uint32_t ceil8(uint32_t n) { return (n + 7u) >> 3; }
+
+// Non-zero flags of the 4 bytes of w as a nibble (bit i = byte i non-zero).
+__device__ __forceinline__ uint32_t nz_nibble(uint32_t w) {
+  const uint32_t h = (((w & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w) & 0x80808080u;
+  return (((h >> 7) * 0x204081u) >> 21) & 0xFu;
+}
+
+// Level-0 bitmap byte j: bit b set when unit 8j+b (of U units of G bytes) is non-zero.
+template <int G>
+__device__ __forceinline__ uint32_t level0_byte(const uint8_t* in, uint32_t U, uint32_t j) {
+  const uint32_t u0 = 8 * j;
+  if (u0 + 8 <= U) {
+    if (G == 1) {
+      const uint2 v = *reinterpret_cast<const uint2*>(in + u0);
+      return nz_nibble(v.x) | (nz_nibble(v.y) << 4);
+    } else if (G == 4) {
+      const uint4 a = *reinterpret_cast<const uint4*>(in + 4 * u0);
+      const uint4 b = *reinterpret_cast<const uint4*>(in + 4 * u0 + 16);
+      return (a.x != 0) | ((a.y != 0) << 1) | ((a.z != 0) << 2) | ((a.w != 0) << 3) | ((b.x != 0) << 4) |
+             ((b.y != 0) << 5) | ((b.z != 0) << 6) | ((b.w != 0) << 7);
+    } else {
+      uint32_t r = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint2 v = *reinterpret_cast<const uint2*>(in + 8 * (u0 + k));
+        r |= (uint32_t)((v.x | v.y) != 0) << k;
+      }
+      return r;
+    }
+  }
+  uint32_t r = 0;
+  for (uint32_t k = 0; k < 8 && u0 + k < U; ++k) {
+    uint32_t nz = 0;
+    for (int b = 0; b < G; ++b) nz |= in[(u0 + k) * G + b];
+    r |= (nz != 0) << k;
+  }
+  return r;
+}
+
+// Warp-level exclusive scan of v; *total gets the warp's sum.
+__device__ __forceinline__ uint32_t warp_exclusive_scan(uint32_t v, uint32_t* total) {
+  const int lane = threadIdx.x & 31;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  *total = __shfl_sync(0xffffffffu, x, 31);
+  return x - v;
+}
+
+// Level-0 bitmap bytes are split into one contiguous range per warp; within a
+// range, lane l takes bytes 32*step + l, so a warp touches consecutive memory.
+template <int NT>
+struct WarpRange {
+  uint32_t a, b;  // bitmap bytes [a, b) of this warp
+  __device__ WarpRange(uint32_t l0) {
+    constexpr int NW = NT / 32;
+    const uint32_t cw = ((l0 + NW - 1) / NW + 31) & ~31u;
+    a = min(l0, (uint32_t)(threadIdx.x >> 5) * cw);
+    b = min(l0, a + cw);
+  }
+};
+
+// RZE_g encode of `in` (L bytes, shared memory, 16-byte aligned) into `out` (shared
+// memory): [level-2 bitmap][level-1 kept][level-0 kept][non-zero units].  Nothing is
+// written when the result would not be shorter than `limit`.  Returns its length.
+// Needs ceil(L/G/512) <= NT (true for the chunk sizes used here).
+template <int NT, int G>
+__device__ uint32_t rze_encode(const uint8_t* in, uint32_t L, uint8_t* out, uint32_t limit, const RzeWork& w) {
+  const uint32_t U = L / G;
+  const uint32_t l0 = ceil8(U), l1 = ceil8(l0), l2 = ceil8(l1);
+  const int t = threadIdx.x, lane = t & 31;
+  const WarpRange<NT> wr(l0);
+  // level 0, warp-strided
+  uint32_t c0 = 0;
+  for (uint32_t j = wr.a + lane; j < wr.b; j += 32) {
+    const uint32_t byte = level0_byte<G>(in, U, j);
+    w.m0[j] = (uint8_t)byte;
+    c0 += __popc(byte);
+  }
+  for (uint32_t j = l0 + t; j < ((l0 + 3) & ~3u); j += NT) w.m0[j] = 0;
+  __syncthreads();
+  // level 1: contiguous level-1 bytes per thread (few)
+  const uint32_t per1 = (l1 + NT - 1) / NT;
+  const uint32_t a1 = min(l1, (uint32_t)t * per1), b1 = min(l1, a1 + per1);
+  uint32_t c1 = 0;
+  for (uint32_t jj = a1; jj < b1; ++jj) {
+    uint32_t byte = 0;
+    for (uint32_t b = 0; b < 8; ++b) {
+      const uint32_t j = 8 * jj + b;
+      if (j >= l0) break;
+      const uint8_t prev = j ? w.m0[j - 1] : 0;
+      if (w.m0[j] != prev) byte |= 1u << b;
+    }
+    w.m1[jj] = (uint8_t)byte;
+    c1 += __popc(byte);
+  }
+  // per-warp payload totals, then the block-wide order of warps
+  uint32_t wtot;
+  warp_exclusive_scan(c0, &wtot);
+  uint32_t np, nk0;
+  const uint32_t wbase = block_exclusive_scan<NT, uint32_t>(lane == 0 ? wtot : 0u, w.tmp, &np);
+  const uint32_t warp_base = __shfl_sync(0xffffffffu, wbase, 0);
+  const uint32_t k0_off = block_exclusive_scan<NT, uint32_t>(c1, w.tmp, &nk0);
+  // level 2: each thread owns one level-2 byte (8 level-1 bytes)
+  uint32_t c2 = 0;
+  if ((uint32_t)t < l2) {
+    uint32_t byte = 0;
+    for (uint32_t b = 0; b < 8; ++b) {
+      const uint32_t j = 8 * t + b;
+      if (j >= l1) break;
+      const uint8_t prev = j ? w.m1[j - 1] : 0;
+      if (w.m1[j] != prev) byte |= 1u << b;
+    }
+    w.m2[t] = (uint8_t)byte;
+    c2 = __popc(byte);
+  }
+  uint32_t nk1;
+  const uint32_t k1_off = block_exclusive_scan<NT, uint32_t>(c2, w.tmp, &nk1);
+  const uint32_t total = l2 + nk1 + nk0 + np * G;
+  if (total >= limit) return total;
+  if ((uint32_t)t < l2) {
+    out[t] = w.m2[t];
+    uint32_t r = 0;
+    for (uint32_t b = 0; b < 8; ++b)
+      if ((w.m2[t] >> b) & 1u) out[l2 + k1_off + r++] = w.m1[8 * t + b];
+  }
+  {
+    uint32_t r = 0;
+    uint8_t* k0 = out + l2 + nk1 + k0_off;
+    for (uint32_t jj = a1; jj < b1; ++jj) {
+      uint32_t bits = w.m1[jj];
+      while (bits) {
+        const uint32_t j = 8 * jj + (__ffs(bits) - 1);
+        bits &= bits - 1;
+        k0[r++] = w.m0[j];
+      }
+    }
+  }
+  {
+    uint8_t* pay = out + l2 + nk1 + nk0;
+    uint32_t run = warp_base;
+    for (uint32_t base = wr.a; base < wr.b; base += 32) {
+      const uint32_t j = base + lane;
+      const uint32_t bits = j < wr.b ? (uint32_t)w.m0[j] : 0u;
+      uint32_t stot;
+      uint32_t r = run + warp_exclusive_scan(__popc(bits), &stot);
+      uint32_t bb = bits;
+      while (bb) {
+        const uint32_t u = 8 * j + (__ffs(bb) - 1);
+        bb &= bb - 1;
+#pragma unroll
+        for (int b = 0; b < G; ++b) pay[r * G + b] = in[u * G + b];
+        ++r;
+      }
+      run += stot;
+    }
+  }
+  __syncthreads();
+  return total;
+}
+
+__device__ __forceinline__ bool tail_clear(const uint8_t* bm, uint32_t nbits) {
+  const uint32_t r = nbits & 7;
+  return !r || (bm[nbits >> 3] >> r) == 0;
+}
+
+// RZE_g decode: `in` (in_len bytes, shared memory) -> `out` (L bytes, shared
+// memory, 16-byte aligned).  Returns false for an inconsistent record.
+template <int NT, int G>
+__device__ bool rze_decode(const uint8_t* in, uint32_t in_len, uint32_t L, uint8_t* out, const RzeWork& w) {
+  const uint32_t U = L / G;
+  const uint32_t l0 = ceil8(U), l1 = ceil8(l0), l2 = ceil8(l1);
+  const int t = threadIdx.x, lane = t & 31;
+  if (in_len < l2) return false;  // uniform
+  const uint8_t* m2 = in;
+  // level-1 bitmap from level 2 (each thread ranks its bytes from scratch: l2 is small)
+  uint32_t nk1 = 0;
+  for (uint32_t i = 0; i < l2; ++i) nk1 += __popc((uint32_t)m2[i]);
+  if (!tail_clear(m2, l1) || l2 + nk1 > in_len) return false;  // uniform
+  for (uint32_t j = t; j < ((l1 + 3) & ~3u); j += NT) {
+    uint8_t v = 0;
+    if (j < l1) {
+      uint32_t r = 0;
+      for (uint32_t i = 0; i < (j >> 3); ++i) r += __popc((uint32_t)m2[i]);
+      r += __popc((uint32_t)m2[j >> 3] & ((2u << (j & 7)) - 1u));
+      v = r ? in[l2 + r - 1] : 0;
+    }
+    w.m1[j] = v;
+  }
+  __syncthreads();
+  // prefix counts of level-1 words (warp 0)
+  const uint32_t nw1 = (l1 + 3) >> 2;
+  const uint32_t* m1w = reinterpret_cast<const uint32_t*>(w.m1);
+  if (t < 32) {
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < nw1; base += 32) {
+      const uint32_t wi = base + t;
+      const uint32_t c = wi < nw1 ? __popc(m1w[wi]) : 0u;
+      uint32_t tot;
+      const uint32_t ex = warp_exclusive_scan(c, &tot);
+      if (wi < nw1) w.pre[wi] = carry + ex;
+      carry += tot;
+    }
+    if (t == 0) w.pre[nw1] = carry;
+  }
+  __syncthreads();
+  const uint32_t nk0 = w.pre[nw1];
+  if (!tail_clear(w.m1, l0) || l2 + nk1 + nk0 > in_len) return false;  // uniform
+  const uint8_t* k0 = in + l2 + nk1;
+  for (uint32_t j = t; j < ((l0 + 3) & ~3u); j += NT) {
+    uint8_t v = 0;
+    if (j < l0) {
+      const uint32_t r = w.pre[j >> 5] + __popc(m1w[j >> 5] << (31 - (j & 31)));
+      v = r ? k0[r - 1] : 0;
+    }
+    w.m0[j] = v;
+  }
+  __syncthreads();
+  if (!tail_clear(w.m0, U)) return false;  // uniform
+  // payload, warp-strided over the level-0 bytes
+  const WarpRange<NT> wr(l0);
+  uint32_t c0 = 0;
+  for (uint32_t j = wr.a + lane; j < wr.b; j += 32) c0 += __popc((uint32_t)w.m0[j]);
+  uint32_t wtot;
+  warp_exclusive_scan(c0, &wtot);
+  uint32_t np;
+  const uint32_t wbase = block_exclusive_scan<NT, uint32_t>(lane == 0 ? wtot : 0u, w.tmp, &np);
+  if ((uint64_t)l2 + nk1 + nk0 + (uint64_t)np * G != in_len) return false;  // uniform
+  const uint8_t* pay = in + l2 + nk1 + nk0;
+  uint32_t run = __shfl_sync(0xffffffffu, wbase, 0);
+  for (uint32_t base = wr.a; base < wr.b; base += 32) {
+    const uint32_t j = base + lane;
+    const uint32_t bits = j < wr.b ? (uint32_t)w.m0[j] : 0u;
+    uint32_t stot;
+    uint32_t r = run + warp_exclusive_scan(__popc(bits), &stot);
+    run += stot;
+    if (j >= wr.b) continue;
+    const uint32_t u0 = 8 * j;
+    if (G == 1 && u0 + 8 <= U) {
+      uint32_t lo = 0, hi = 0;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        uint32_t v = 0;
+        if ((bits >> b) & 1u) v = pay[r++];
+        if (b < 4)
+          lo |= v << (8 * b);
+        else
+          hi |= v << (8 * (b - 4));
+      }
+      *reinterpret_cast<uint2*>(out + u0) = make_uint2(lo, hi);
+    } else {
+      for (uint32_t b = 0; b < 8 && u0 + b < U; ++b) {
+        if ((bits >> b) & 1u) {
+#pragma unroll
+          for (int k = 0; k < G; ++k) out[(u0 + b) * G + k] = pay[r * G + k];
+          ++r;
+        } else {
+#pragma unroll
+          for (int k = 0; k < G; ++k) out[(u0 + b) * G + k] = 0;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// ------------------------------------------------------------- record copies
+
+// Copies n bytes (rounded up to 16) between 16-byte aligned buffers.
+template <int NT>
+__device__ __forceinline__ void copy16(uint8_t* dst, const uint8_t* src, uint32_t n) {
+  const uint32_t n16 = (n + 15) >> 4;
+  const uint4* s = reinterpret_cast<const uint4*>(src);
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  for (uint32_t i = threadIdx.x; i < n16; i += NT) d[i] = s[i];
+}
+
+// Zeroes bytes [n, pad16(n)) of a shared buffer (record padding).
+template <int NT>
+__device__ __forceinline__ void zero_tail16(uint8_t* buf, uint32_t n) {
+  const uint32_t p = (n + 15) & ~15u;
+  for (uint32_t i = n + threadIdx.x; i < p; i += NT) buf[i] = 0;
+}
+
+}  // namespace lopc

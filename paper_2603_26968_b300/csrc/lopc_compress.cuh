@@ -2,7 +2,7 @@
 // resolution, the tile pass (quantize, flags, tile-local least fixpoint), reruns of
 // tiles whose halo changed, the chunk encoder, the size scan and the stream pack.
 #pragma once
-#include "lopc_device.cuh"
+#include "lopc_codec.cuh"
 
 namespace lopc {
 
@@ -11,19 +11,19 @@ template <typename T, int ND>
 struct TileCfg;
 template <>
 struct TileCfg<float, 3> {
-  static constexpr int TZ = 16, TY = 16, TX = 16, HZ = 1, NT = 256;
+  static constexpr int TZ = 16, TY = 16, TX = 16, HZ = 1, NT = 256, MINB = 3, MINB_RERUN = 4;
 };
 template <>
 struct TileCfg<double, 3> {
-  static constexpr int TZ = 8, TY = 16, TX = 16, HZ = 1, NT = 128;
+  static constexpr int TZ = 8, TY = 16, TX = 16, HZ = 1, NT = 128, MINB = 3, MINB_RERUN = 8;
 };
 template <>
 struct TileCfg<float, 2> {
-  static constexpr int TZ = 1, TY = 64, TX = 64, HZ = 0, NT = 256;
+  static constexpr int TZ = 1, TY = 64, TX = 64, HZ = 0, NT = 256, MINB = 3, MINB_RERUN = 4;
 };
 template <>
 struct TileCfg<double, 2> {
-  static constexpr int TZ = 1, TY = 32, TX = 64, HZ = 0, NT = 128;
+  static constexpr int TZ = 1, TY = 32, TX = 64, HZ = 0, NT = 128, MINB = 6, MINB_RERUN = 8;
 };
 
 // Freudenthal neighbourhood (Sec. II): offsets +-d, d in {0,1}^3 \ {0}.  Direction
@@ -58,6 +58,11 @@ __global__ void k_init_params(Params* P, double eb, int mode) {
   P->dirty_count = 0;
   P->total = 0;
   P->rounds = 0;
+  P->fix_iters = 0;
+  P->fix_iters_max = 0;
+  for (int k = 0; k < 8; ++k) P->phase[k] = 0;
+  P->fast_ok = 0;
+  P->inv_f = 0.f;
 }
 
 template <typename T>
@@ -136,187 +141,484 @@ __global__ void k_resolve_eps(Params* P) {
   const int ex = (int)((u >> 52) & 0x7ff);
   P->inv_m = (u & 0xfffffffffffffULL) | (ex ? 0x10000000000000ULL : 0ULL);
   P->inv_e = ex ? ex - 1075 : -1074;
+  const float inv_f = __double2float_rn(inv);
+  P->inv_f = inv_f;
+  P->fast_ok = inv_f >= 1.1754943508222875e-38f && inv_f <= 3.4028234663852886e38f;
 }
 
 // ---------------------------------------------------------------- tile pass
 
+constexpr uint32_t kSlotBytes = 16384;  // a record never exceeds the raw chunk (16 KiB)
+
+// Shared-memory geometry of a tile with its 1-point halo, and the thread mapping:
+// thread t owns the 16 points (lz, 16*sy + j, lx), j = 0..15, of one y-segment, with
+// t = (lz * SEGY + sy) * TX + lx, so the lanes of a warp walk consecutive x.  Rows
+// are padded to an odd pitch and z-planes to a pitch = 16 (mod 32) so that the two
+// x-runs of 16 lanes a warp touches fall in distinct banks.
 template <typename T, int ND>
-struct TileSmem {
+struct TileGeom {
   using C = TileCfg<T, ND>;
-  using K = typename Traits<T>::Key;
-  using B = typename Traits<T>::Bin;
-  static constexpr int BZ = C::TZ + 2 * C::HZ, BY = C::TY + 2, BX = C::TX + 2;
-  static constexpr int E = BZ * BY * BX;
-  static constexpr int NP = C::TZ * C::TY * C::TX;
-  static constexpr size_t bytes() { return (size_t)E * (sizeof(K) + sizeof(B) + 4) + (size_t)NP * 4 + 64; }
+  static constexpr int TZ = C::TZ, TY = C::TY, TX = C::TX, HZ = C::HZ, NT = C::NT;
+  static constexpr int BZ = TZ + 2 * HZ, BY = TY + 2, BX = TX + 2;
+  static constexpr int BXP = (BX % 2) ? BX : BX + 1;
+  static constexpr int PP = HZ ? ((BY * BXP + 15) / 32) * 32 + 16 : BY * BXP;
+  static constexpr int E = BZ * PP;               // shared-memory entries
+  static constexpr int NP = TZ * TY * TX;         // points of a full tile
+  static constexpr int SEGY = TY / kSegment;      // y-segments per column
+  static_assert(TZ * SEGY * TX == NT, "one y-segment per thread");
+  static_assert(TX >= 16, "a half warp spans one x-run");
+  __device__ static constexpr int off(int dz, int dy, int dx) { return dz * PP + dy * BXP + dx; }
+  __device__ static constexpr int entry(int lz, int ly, int lx) { return (lz + HZ) * PP + (ly + 1) * BXP + lx + 1; }
+  // owner thread of a point, and the point's bit in the frontier (thread-major)
+  __device__ static constexpr int owner(int lz, int ly, int lx) { return (lz * SEGY + ly / kSegment) * TX + lx; }
+  __device__ static constexpr int fbit(int lz, int ly, int lx) { return owner(lz, ly, lx) * kSegment + ly % kSegment; }
 };
 
-// Tile pass (mode 0) and rerun (mode 1) of one chunk-tile.
-//   mode 0: halo subbins are taken as 0 (a lower bound); writes all subbins and bins.
-//   mode 1: halo and own subbins come from the global array (current values).
-// Then the tile-local least fixpoint of Alg. 2's update is computed in shared
-// memory (chaotic relaxation; any schedule reaches the same least fixpoint,
-// Sec. III-E), subbins that rose are written back, and every other tile holding a
-// greater same-bin neighbour of a risen point is marked for the next round.
-template <typename T, int ND, int MODE>
-__global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_tile(const T* __restrict__ x, Geometry g, Params* P,
-                                                             uint32_t* __restrict__ s_glob,
-                                                             typename Traits<T>::Bin* __restrict__ b_glob,
-                                                             uint8_t* __restrict__ dirty,
-                                                             const uint32_t* __restrict__ list) {
-  using C = TileCfg<T, ND>;
-  using S = TileSmem<T, ND>;
-  using K = typename Traits<T>::Key;
-  using B = typename Traits<T>::Bin;
-  constexpr int NT = C::NT, BY = S::BY, BX = S::BX, E = S::E;
-  if (P->status & kErrNonfinite) return;
-  if (P->constant) return;
-  extern __shared__ __align__(16) unsigned char smem[];
-  K* key = reinterpret_cast<K*>(smem);
-  B* bin = reinterpret_cast<B*>(key + E);
-  uint32_t* sv = reinterpret_cast<uint32_t*>(bin + E);
-  uint32_t* cm = sv + E;
+struct SegPos {
+  int lz, ly0, lx;  // local coordinates of the thread's first point
+  int e0;           // its shared-memory entry; point j is at e0 + j * BXP
+  int b0;           // its frontier bit; point j is bit b0 + j
+};
 
-  const int64_t tid = MODE == 0 ? (int64_t)blockIdx.x : (int64_t)list[blockIdx.x];
-  const TileBox tb = tile_box(g, tid);
-  const unsigned long long inv_m = P->inv_m;
-  const int inv_e = P->inv_e;
-  const int64_t plane = g.ny * g.nx;
+template <typename G>
+__device__ __forceinline__ SegPos seg_pos() {
+  SegPos s;
+  const int t = threadIdx.x;
+  s.lx = t % G::TX;
+  const int r = t / G::TX;
+  s.lz = r / G::SEGY;
+  s.ly0 = (r % G::SEGY) * kSegment;
+  s.e0 = G::entry(s.lz, s.ly0, s.lx);
+  s.b0 = t * kSegment;
+  return s;
+}
 
-  // load the tile and its halo: keys and bins (absent points get a bin no value has)
-  bool range_bad = false;
-  for (int e = threadIdx.x; e < E; e += NT) {
-    const int lx = e % BX, ly = (e / BX) % BY, lz = e / (BX * BY);
-    const int64_t gz = tb.z0 + lz - C::HZ, gy = tb.y0 + ly - 1, gx = tb.x0 + lx - 1;
-    const bool in = gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx >= 0 && gx < g.nx;
-    B b = Traits<T>::kAbsent;
-    K k = 0;
-    uint32_t s0 = 0;
-    if (in) {
-      const int64_t gi = gz * plane + gy * g.nx + gx;
-      const T v = x[gi];
-      long long q;
-      if (!is_finite_bits<T>(v)) {
-        range_bad = true;  // only reachable in ABS mode; reported as non-finite below
-      } else if (!quantize_exact<T>(v, inv_m, inv_e, q) || q >= Traits<T>::kBinLimit || q <= -Traits<T>::kBinLimit) {
-        range_bad = true;
-      } else {
-        b = (B)q;
-        k = order_key<T>(v);
-      }
-      if (MODE == 1) s0 = s_glob[gi];
-    }
-    key[e] = k;
-    bin[e] = b;
-    sv[e] = s0;
-  }
-  if (range_bad) {
-    // tell the two cases apart once, off the fast path
-    for (int e = threadIdx.x; e < E; e += NT) {
-      const int lx = e % BX, ly = (e / BX) % BY, lz = e / (BX * BY);
-      const int64_t gz = tb.z0 + lz - C::HZ, gy = tb.y0 + ly - 1, gx = tb.x0 + lx - 1;
-      if (gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx >= 0 && gx < g.nx) {
-        const T v = x[gz * plane + gy * g.nx + gx];
-        atomicOr(&P->status, is_finite_bits<T>(v) ? kErrRange : kErrNonfinite);
-      }
-    }
-  }
-  __syncthreads();
+// Direction k (0..13) of the Freudenthal neighbourhood (Sec. II): k < 7 is -D[k]
+// (lower linear index), k >= 7 is +D[k-7]; D[d] has bits (z, y, x) of d + 1.
+__host__ __device__ constexpr int dz_of(int k) { return (k < 7 ? -1 : 1) * ((((k % 7) + 1) >> 2) & 1); }
+__host__ __device__ constexpr int dy_of(int k) { return (k < 7 ? -1 : 1) * ((((k % 7) + 1) >> 1) & 1); }
+__host__ __device__ constexpr int dx_of(int k) { return (k < 7 ? -1 : 1) * (((k % 7) + 1) & 1); }
+constexpr int kPlusY = 8;  // direction +D[1] = (0, 1, 0)
 
-  // flags (Alg. 1): lower same-bin neighbours in bits 0..13, greater ones in 14..27
-  const int p0 = threadIdx.x * kSegment;
-  const int lz = p0 / (C::TX * C::TY), ly = (p0 / C::TX) % C::TY, lx0 = p0 % C::TX;
-  const bool row_in = lz < tb.cz && ly < tb.cy;
-  uint32_t sinit[kSegment];
-#pragma unroll
-  for (int j = 0; j < kSegment; ++j) {
-    const int lx = lx0 + j;
-    const int e = ((lz + C::HZ) * BY + ly + 1) * BX + lx + 1;
-    uint32_t m = 0;
-    if (row_in && lx < tb.cx) {
-      const B bp = bin[e];
-      const K kp = key[e];
+__device__ __forceinline__ uint32_t ld_acquire_u8(const uint8_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u8 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Tile-local least fixpoint of Alg. 2's update, frontier driven: only points whose
+// lower same-bin neighbours rose are recomputed,
+//   s(p) = max(s(p), max over lower same-bin n of s(n) + [n after p]),
+// and a point that rises puts its greater same-bin neighbours of the tile on the
+// next frontier (its +y neighbour in the same segment is taken in the same sweep).
+// Chaotic relaxation from lower bounds reaches the unique least fixpoint (Sec.
+// III-E) whatever the schedule.  `cml[e]` holds the lower-neighbour bits of entry
+// e; `fa` holds the first frontier (thread-major bits), `fb` must be clear.
+// Returns the number of block-wide sweeps; `risen` gets the thread's risen points.
+template <typename G>
+__device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint16_t* cml, uint32_t* fa, uint32_t* fb,
+                                                 const SegPos& sp, int limit, bool& over, uint32_t& risen) {
+  volatile uint32_t* vs = sv;
+  const int wsh = sp.b0 & 31;
+  int iter = 0;
+  while (true) {
+    uint32_t work = (fa[sp.b0 >> 5] >> wsh) & 0xFFFFu;
+    int changed = 0;
+    while (work) {
+      const int j = __ffs(work) - 1;
+      work &= work - 1;
+      const int e = sp.e0 + j * G::BXP;
+      const uint32_t m = cml[e];
+      const uint32_t before = vs[e];
+      uint32_t best = before;
 #pragma unroll
       for (int k = 0; k < 14; ++k) {
-        if (!dir_valid<C::HZ>(k)) continue;
-        int dz, dy, dx;
-        dir3(k, dz, dy, dx);
-        const int e2 = e + (dz * BY + dy) * BX + dx;
-        if (bin[e2] != bp) continue;
-        const K kn = key[e2];
-        const bool lower = kn < kp || (kn == kp && k < 7);
-        m |= lower ? (1u << k) : (1u << (14 + k));
+        if (!G::HZ && dz_of(k) != 0) continue;
+        if (m & (1u << k)) {
+          const uint32_t c = vs[e + G::off(dz_of(k), dy_of(k), dx_of(k))] + (k >= 7 ? 1u : 0u);
+          best = c > best ? c : best;
+        }
       }
-    }
-    cm[p0 + j] = m;
-    sinit[j] = sv[e];
-  }
-  __syncthreads();
-
-  // tile-local least fixpoint: s(p) = max(s(p), max over lower same-bin n of s(n) + [n after p])
-  volatile uint32_t* vs = sv;
-  int iter = 0;
-  bool over = false;
-  while (true) {
-    int changed = 0;
-    const bool fwd = (iter & 1) == 0;
-#pragma unroll 1
-    for (int jj = 0; jj < kSegment; ++jj) {
-      const int j = fwd ? jj : kSegment - 1 - jj;
-      const uint32_t m = cm[p0 + j] & 0x3fffu;
-      if (!m) continue;
-      const int e = ((lz + C::HZ) * BY + ly + 1) * BX + lx0 + j + 1;
-      uint32_t best = vs[e];
-      uint32_t mm = m;
-      while (mm) {
-        const int k = __ffs(mm) - 1;
-        mm &= mm - 1;
-        int dz, dy, dx;
-        dir3(k, dz, dy, dx);
-        const uint32_t c = vs[e + (dz * BY + dy) * BX + dx] + (k >= 7 ? 1u : 0u);
-        best = c > best ? c : best;
-      }
-      if (best > vs[e]) {
-        vs[e] = best;
-        changed = 1;
+      if (best == before) continue;
+      vs[e] = best;
+      changed = 1;
+      risen |= 1u << j;
+      const int ly = sp.ly0 + j;
+#pragma unroll
+      for (int k = 0; k < 14; ++k) {
+        if (!G::HZ && dz_of(k) != 0) continue;
+        const int nz = sp.lz + dz_of(k), ny = ly + dy_of(k), nx = sp.lx + dx_of(k);
+        if (nz < 0 || nz >= G::TZ || ny < 0 || ny >= G::TY || nx < 0 || nx >= G::TX) continue;
+        const int kop = k < 7 ? k + 7 : k - 7;
+        if (!((cml[e + G::off(dz_of(k), dy_of(k), dx_of(k))] >> kop) & 1u)) continue;
+        if (k == kPlusY && j + 1 < kSegment) {
+          work |= 1u << (j + 1);  // +y neighbour, later in this sweep
+        } else {
+          const int q = G::fbit(nz, ny, nx);
+          atomicOr(&fb[q >> 5], 1u << (q & 31));
+        }
       }
     }
     ++iter;
     if (!__syncthreads_or(changed)) break;
-    if (iter > 4 * E + 64) {  // a chain inside the box has fewer than E links
+    if (iter > limit) {
       over = true;
       break;
     }
+    if (wsh == 0) fa[sp.b0 >> 5] = 0;  // one owner per frontier word
+    __syncthreads();
+    uint32_t* t = fa;
+    fa = fb;
+    fb = t;
   }
-  if (over && threadIdx.x == 0) atomicOr(&P->status, kErrNotConverged);
+  return iter;
+}
 
-  // write back, mark tiles that hold greater same-bin neighbours of risen points
+// Bits of the directions that leave the tile box, for a point at local (lz, ly, lx).
+template <typename G>
+__device__ __forceinline__ uint32_t out_of_box_bits(int lz, int ly, int lx) {
+  uint32_t r = 0;
+#pragma unroll
+  for (int k = 0; k < 14; ++k) {
+    if (!G::HZ && dz_of(k) != 0) continue;
+    const int nz = lz + dz_of(k), ny = ly + dy_of(k), nx = lx + dx_of(k);
+    if (nz < 0 || nz >= G::TZ || ny < 0 || ny >= G::TY || nx < 0 || nx >= G::TX) r |= 1u << k;
+  }
+  return r;
+}
+
+template <typename T, int ND>
+struct PassSmem {
+  using G = TileGeom<T, ND>;
+  using K = typename Traits<T>::Key;
+  using B = typename Traits<T>::Bin;
+  static constexpr uint32_t L = (uint32_t)G::NP * Traits<T>::W;  // BIT output of a full tile
+  static constexpr size_t up16(size_t v) { return (v + 15) & ~(size_t)15; }
+  // RA: keys -> subbins -> bit planes + RZE work;  RB: bins -> staged bin record
+  static constexpr size_t RAa = (size_t)G::E * (sizeof(K) > 4 ? sizeof(K) : 4);
+  static constexpr size_t RAb = (size_t)L + RzeWork::bytes(L);
+  static constexpr size_t RA = up16(RAa > RAb ? RAa : RAb);
+  static constexpr size_t RB = up16((size_t)G::E * sizeof(B) > L ? (size_t)G::E * sizeof(B) : L);
+  static constexpr size_t RC = up16((size_t)G::E * 2);                  // lower masks
+  static constexpr size_t RD = up16((size_t)2 * (G::NP / 32) * 4);      // two frontiers
+  static constexpr size_t bytes() { return RA + RB + RC + RD; }
+};
+
+// Tile pass (one block per chunk-tile):
+//   1. load x on the tile and its halo, quantize (Sec. III-A) and take order keys;
+//   2. flags (Alg. 1): the lower same-bin neighbours of every point;
+//   3. tile-local least fixpoint with halo subbins taken as 0 (a lower bound);
+//   4. write subbins and lower masks (what reruns and the boundary check need);
+//   5. encode the tile's bin record (Sec. III-C; bins are final here).
+template <typename T, int ND>
+__global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
+    k_pass(const T* __restrict__ x, Geometry g, Params* P, uint32_t* __restrict__ s_glob,
+           uint16_t* __restrict__ cm_glob, int64_t* __restrict__ bins_out, uint8_t* __restrict__ slots,
+           uint32_t* __restrict__ sizes) {
+  using G = TileGeom<T, ND>;
+  using PS = PassSmem<T, ND>;
+  using K = typename Traits<T>::Key;
+  using B = typename Traits<T>::Bin;
+  using WordT = typename Traits<T>::Bits;
+  constexpr int NT = G::NT, W = Traits<T>::W;
+  if (P->status & kErrNonfinite) return;
+  if (P->constant) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  K* key = reinterpret_cast<K*>(smem);
+  uint32_t* sv = reinterpret_cast<uint32_t*>(smem);
+  B* bin = reinterpret_cast<B*>(smem + PS::RA);
+  uint16_t* cml = reinterpret_cast<uint16_t*>(smem + PS::RA + PS::RB);
+  uint32_t* fa = reinterpret_cast<uint32_t*>(smem + PS::RA + PS::RB + PS::RC);
+  uint32_t* fb = fa + G::NP / 32;
+
+  const int64_t tid = blockIdx.x;
+  const TileBox tb = tile_box(g, tid);
+  const unsigned long long inv_m = P->inv_m;
+  const int inv_e = P->inv_e;
+  const float inv_f = P->inv_f;
+  const int fast_ok = P->fast_ok;
+  const int64_t plane = g.ny * g.nx;
+  long long t0 = clock64();
+
+  // 1. load, quantize, keys (absent points get a bin no value has)
+  bool bad = false;
+  constexpr int NBOX = G::BZ * G::BY * G::BX;
+#pragma unroll 4
+  for (int i = threadIdx.x; i < NBOX; i += NT) {
+    const int lx = i % G::BX, ly = (i / G::BX) % G::BY, lz = i / (G::BX * G::BY);
+    const int e = lz * G::PP + ly * G::BXP + lx;
+    const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1, gx = tb.x0 + lx - 1;
+    B b = Traits<T>::kAbsent;
+    K k = 0;
+    if (gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx >= 0 && gx < g.nx) {
+      const T v = __ldg(&x[gz * plane + gy * g.nx + gx]);
+      long long q;
+      if (is_finite_bits<T>(v) && quantize_fast<T>(v, inv_f, fast_ok, inv_m, inv_e, q) &&
+          q < Traits<T>::kBinLimit && q > -Traits<T>::kBinLimit) {
+        b = (B)q;
+        k = order_key<T>(v);
+      } else {
+        bad = true;
+      }
+    }
+    key[e] = k;
+    bin[e] = b;
+  }
+  for (int i = threadIdx.x; i < G::NP / 16; i += NT) fa[i] = 0;  // both frontiers
+  if (bad) {  // tell non-finite from out-of-range, off the fast path
+    for (int i = threadIdx.x; i < NBOX; i += NT) {
+      const int lx = i % G::BX, ly = (i / G::BX) % G::BY, lz = i / (G::BX * G::BY);
+      const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1, gx = tb.x0 + lx - 1;
+      if (gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx >= 0 && gx < g.nx) {
+        const T v = x[gz * plane + gy * g.nx + gx];
+        long long q;
+        if (!is_finite_bits<T>(v))
+          atomicOr(&P->status, kErrNonfinite);
+        else if (!quantize_exact<T>(v, inv_m, inv_e, q) || q >= Traits<T>::kBinLimit || q <= -Traits<T>::kBinLimit)
+          atomicOr(&P->status, kErrRange);
+      }
+    }
+  }
+  __syncthreads();
+  phase_mark(P, 0, t0);
+
+  // 2. flags of the thread's y-segment; the first frontier is every point with a
+  //    lower same-bin neighbour
+  const SegPos sp = seg_pos<G>();
+  const bool col_in = sp.lz < tb.cz && sp.lx < tb.cx;
+  uint32_t active = 0;
 #pragma unroll 1
   for (int j = 0; j < kSegment; ++j) {
-    const int lx = lx0 + j;
-    if (!(row_in && lx < tb.cx)) continue;
-    const int e = ((lz + C::HZ) * BY + ly + 1) * BX + lx + 1;
-    const int64_t gz = tb.z0 + lz, gy = tb.y0 + ly, gx = tb.x0 + lx;
-    const int64_t gi = gz * plane + gy * g.nx + gx;
-    const uint32_t sf = sv[e];
-    if (MODE == 0) {
-      s_glob[gi] = sf;
-      b_glob[gi] = bin[e];
-    } else if (sf != sinit[j]) {
-      s_glob[gi] = sf;
+    uint32_t lo = 0;
+    const int e = sp.e0 + j * G::BXP;
+    if (col_in && sp.ly0 + j < tb.cy) {
+      const B bp = bin[e];
+      const K kp = key[e];
+#pragma unroll
+      for (int k = 0; k < 14; ++k) {
+        if (!G::HZ && dz_of(k) != 0) continue;
+        const int e2 = e + G::off(dz_of(k), dy_of(k), dx_of(k));
+        if (bin[e2] == bp) {
+          const K kn = key[e2];
+          if (kn < kp || (kn == kp && k < 7)) lo |= 1u << k;
+        }
+      }
     }
-    if (sf == sinit[j]) continue;
-    uint32_t up = cm[p0 + j] >> 14;
-    while (up) {
-      const int k = __ffs(up) - 1;
-      up &= up - 1;
-      int dz, dy, dx;
-      dir3(k, dz, dy, dx);
-      const int nz = lz + dz, ny = ly + dy, nx = lx + dx;
-      if (nz >= 0 && nz < C::TZ && ny >= 0 && ny < C::TY && nx >= 0 && nx < C::TX) continue;
-      const int64_t qz = gz + dz, qy = gy + dy, qx = gx + dx;
-      const int64_t t2 = ((qz / g.tz) * g.nty + qy / g.ty) * g.ntx + qx / g.tx;
-      dirty[t2] = 1;
+    cml[e] = (uint16_t)lo;
+    active |= (lo != 0) << j;
+  }
+  if (active) atomicOr(&fa[sp.b0 >> 5], active << (sp.b0 & 31));
+  __syncthreads();  // keys are dead from here on
+
+  // 3. tile-local least fixpoint, halo subbins 0
+  for (int e = threadIdx.x; e < G::E; e += NT) sv[e] = 0;
+  __syncthreads();
+  phase_mark(P, 1, t0);
+  bool over = false;
+  uint32_t risen = 0;
+  const int iters = frontier_fixpoint<G>(sv, cml, fa, fb, sp, 4 * G::NP + 64, over, risen);
+  if (threadIdx.x == 0) {
+    if (over) atomicOr(&P->status, kErrNotConverged);
+    atomicAdd(&P->fix_iters, (unsigned long long)iters);
+    atomicMax(&P->fix_iters_max, (unsigned long long)iters);
+  }
+  phase_mark(P, 2, t0);
+
+  // 4. write the state reruns need (cross-tile constraints are checked afterwards)
+  const int64_t gz = tb.z0 + sp.lz, gx = tb.x0 + sp.lx;
+  if (col_in) {
+#pragma unroll 4
+    for (int j = 0; j < kSegment; ++j) {
+      if (sp.ly0 + j >= tb.cy) break;
+      const int e = sp.e0 + j * G::BXP;
+      const int64_t gi = gz * plane + (tb.y0 + sp.ly0 + j) * g.nx + gx;
+      s_glob[gi] = sv[e];
+      cm_glob[gi] = cml[e];
+      if (bins_out) bins_out[gi] = (int64_t)bin[e];
+    }
+  }
+  (void)risen;
+  __syncthreads();
+  phase_mark(P, 3, t0);
+
+  // 5. bin record: DIFFNB_w, BIT_w, RZE_1; raw if that is not shorter
+  {
+    const int n = tb.n, n32 = (n + 31) & ~31;
+    const uint32_t raw = (uint32_t)n * W;
+    const bool full = n == G::NP;
+    auto bin_of = [&](int i) -> WordT {
+      int lx2, ly2, lz2;
+      if (full) {
+        lx2 = i % G::TX;
+        ly2 = (i / G::TX) % G::TY;
+        lz2 = i / (G::TX * G::TY);
+      } else {
+        lx2 = i % tb.cx;
+        ly2 = (i / tb.cx) % tb.cy;
+        lz2 = i / (tb.cx * tb.cy);
+      }
+      return (WordT)bin[G::entry(lz2, ly2, lx2)];
+    };
+    uint32_t* planes = reinterpret_cast<uint32_t*>(smem);
+    const RzeWork w = rze_work_at(smem + PS::L, PS::L);
+    constexpr WordT M = (WordT)0xAAAAAAAAAAAAAAAAULL;
+    bit_transpose<NT, W>(n32, [&](int i) -> uint64_t {
+      if (i >= n) return 0;
+      const WordT d = bin_of(i) - (i ? bin_of(i - 1) : (WordT)0);
+      return (uint64_t)((WordT)(d + M) ^ M);
+    }, planes);
+    __syncthreads();
+    uint8_t* slot = slots + (size_t)tid * kSlotBytes;
+    uint8_t* stage = reinterpret_cast<uint8_t*>(bin);  // bins are dead once the record is written
+    const uint32_t len = rze_encode<NT, 1>(reinterpret_cast<const uint8_t*>(planes), W * n32, stage, raw, w);
+    if (len >= raw) {  // nothing was staged: bins are intact
+      for (int i = threadIdx.x; i < n; i += NT) reinterpret_cast<WordT*>(slot)[i] = bin_of(i);
+      if (threadIdx.x == 0) sizes[tid] = raw | kRawFlag;
+    } else {
+      zero_tail16<NT>(stage, len);
+      __syncthreads();
+      copy16<NT>(slot, stage, len);
+      if (threadIdx.x == 0) sizes[tid] = len;
+    }
+  }
+  phase_mark(P, 4, t0);
+}
+
+template <typename T, int ND>
+struct RerunSmem {
+  using G = TileGeom<T, ND>;
+  // boundary points of a tile: an upper bound for the queue of risen boundary points
+  static constexpr int QMAX = 2 * (G::TY * G::TX + (G::HZ ? G::TZ * G::TX + G::TZ * G::TY : G::TX + G::TY));
+  static constexpr size_t bytes() {
+    return (size_t)G::E * 4 + (((size_t)G::E * 2 + 15) & ~(size_t)15) + (size_t)2 * (G::NP / 32) * 4 +
+           (size_t)QMAX * 4 + 32;
+  }
+};
+
+// Rerun of a tile whose halo subbins may have risen: the stored lower-neighbour
+// masks and the current subbins of the tile and its halo are all it needs.  After
+// the pass every tile holds its tile-local least fixpoint with halo subbins 0, so
+// the first round visits every tile (list == nullptr); later rounds visit the tiles
+// marked by the round before.  The first frontier is the boundary points whose
+// constraint from a lower same-bin neighbour in another tile is violated; a tile
+// without one returns at once.  Writes the subbins that rose and marks the tiles
+// whose constraints from risen boundary points are now violated.
+template <typename T, int ND>
+__global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN)
+    k_rerun(Geometry g, Params* P, uint32_t* __restrict__ s_glob, const uint16_t* __restrict__ cm_glob,
+            uint8_t* __restrict__ dirty, const uint32_t* __restrict__ list) {
+  using G = TileGeom<T, ND>;
+  constexpr int NT = G::NT;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* sv = reinterpret_cast<uint32_t*>(smem);
+  uint16_t* cm = reinterpret_cast<uint16_t*>(smem + (size_t)G::E * 4);
+  uint32_t* fa = reinterpret_cast<uint32_t*>(smem + (size_t)G::E * 4 + (((size_t)G::E * 2 + 15) & ~(size_t)15));
+  uint32_t* fb = fa + G::NP / 32;
+  using RS = RerunSmem<T, ND>;
+  uint32_t* queue = fb + G::NP / 32;
+  __shared__ uint32_t qn;
+  if (P->status & kErrNonfinite) return;
+  if (P->constant) return;
+  const int64_t tid = list ? (int64_t)list[blockIdx.x] : (int64_t)blockIdx.x;
+  const TileBox tb = tile_box(g, tid);
+  const int64_t plane = g.ny * g.nx;
+  long long t0 = clock64();
+  constexpr int NBOX = G::BZ * G::BY * G::BX;
+  constexpr int BATCH = 4;
+  for (int i0 = threadIdx.x; i0 < NBOX; i0 += BATCH * NT) {
+    uint32_t sb[BATCH], mb[BATCH];
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {  // issue every load of the batch first
+      const int i = i0 + u * NT;
+      const int lx = i % G::BX, ly = (i / G::BX) % G::BY, lz = i / (G::BX * G::BY);
+      const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1, gx = tb.x0 + lx - 1;
+      sb[u] = 0;
+      mb[u] = 0;
+      if (i < NBOX && gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx >= 0 && gx < g.nx) {
+        const int64_t gi = gz * plane + gy * g.nx + gx;
+        sb[u] = s_glob[gi];
+        mb[u] = __ldg(&cm_glob[gi]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const int i = i0 + u * NT;
+      if (i >= NBOX) break;
+      const int lx = i % G::BX, ly = (i / G::BX) % G::BY, lz = i / (G::BX * G::BY);
+      const int e = lz * G::PP + ly * G::BXP + lx;
+      sv[e] = sb[u];
+      cm[e] = (uint16_t)mb[u];
+    }
+  }
+  for (int i = threadIdx.x; i < G::NP / 16; i += NT) fa[i] = 0;
+  if (threadIdx.x == 0) qn = 0;
+  __syncthreads();
+  const SegPos sp = seg_pos<G>();
+  const bool col_in = sp.lz < tb.cz && sp.lx < tb.cx;
+  // the first frontier: boundary points whose constraint from a lower same-bin
+  // neighbour outside the tile is violated by the current subbins (points outside
+  // a clipped tile are out of the domain: their masks were loaded as 0)
+  uint32_t first = 0;
+  if (col_in) {
+#pragma unroll 1
+    for (int j = 0; j < kSegment; ++j) {
+      const int e = sp.e0 + j * G::BXP;
+      const uint32_t mo = cm[e] & out_of_box_bits<G>(sp.lz, sp.ly0 + j, sp.lx);
+      if (!mo) continue;
+      const uint32_t sp_ = sv[e];
+#pragma unroll
+      for (int k = 0; k < 14; ++k) {
+        if ((mo >> k) & 1u) {
+          if (sv[e + G::off(dz_of(k), dy_of(k), dx_of(k))] + (k >= 7 ? 1u : 0u) > sp_) first |= 1u << j;
+        }
+      }
+    }
+  }
+  if (first) atomicOr(&fa[sp.b0 >> 5], first << (sp.b0 & 31));
+  if (!__syncthreads_or(first != 0)) return;  // every constraint into this tile holds
+  phase_mark(P, 5, t0);
+  bool over = false;
+  uint32_t risen = 0;
+  const int iters = frontier_fixpoint<G>(sv, cm, fa, fb, sp, 4 * G::NP + 64, over, risen);
+  if (threadIdx.x == 0) {
+    if (over) atomicOr(&P->status, kErrNotConverged);
+    atomicAdd(&P->fix_iters, (unsigned long long)iters);
+    atomicMax(&P->fix_iters_max, (unsigned long long)iters);
+  }
+  phase_mark(P, 6, t0);
+  // write the subbins that rose; queue the risen boundary points
+  const int64_t gz = tb.z0 + sp.lz, gx = tb.x0 + sp.lx;
+  if (col_in && risen) {
+#pragma unroll 1
+    for (int j = 0; j < kSegment; ++j) {
+      if (!((risen >> j) & 1u)) continue;
+      const int ly = sp.ly0 + j;
+      s_glob[gz * plane + (tb.y0 + ly) * g.nx + gx] = sv[sp.e0 + j * G::BXP];
+      if (out_of_box_bits<G>(sp.lz, ly, sp.lx)) {
+        const uint32_t slot = atomicAdd(&qn, 1u);
+        if (slot < (uint32_t)RS::QMAX) queue[slot] = ((uint32_t)sp.lz << 20) | ((uint32_t)ly << 10) | (uint32_t)sp.lx;
+      }
+    }
+  }
+  __syncthreads();
+  // mark, in parallel over the queue: tiles whose constraints from risen boundary
+  // points are now violated (the neighbour's mask says whether it is constrained)
+  const uint32_t nq = min(qn, (uint32_t)RS::QMAX);
+  for (uint32_t qi = threadIdx.x; qi < nq; qi += NT) {
+    const uint32_t v = queue[qi];
+    const int lz = (int)(v >> 20), ly = (int)((v >> 10) & 1023u), lx = (int)(v & 1023u);
+    const int e = G::entry(lz, ly, lx);
+    const uint32_t sf = sv[e];
+    const uint32_t ob = out_of_box_bits<G>(lz, ly, lx);
+    const int64_t pz = tb.z0 + lz, py = tb.y0 + ly, px = tb.x0 + lx;
+#pragma unroll
+    for (int k = 0; k < 14; ++k) {
+      if (!((ob >> k) & 1u)) continue;
+      const int kop = k < 7 ? k + 7 : k - 7;
+      if (!((cm[e + G::off(dz_of(k), dy_of(k), dx_of(k))] >> kop) & 1u)) continue;
+      const int64_t qz = pz + dz_of(k), qy = py + dy_of(k), qx = px + dx_of(k);
+      if (*(volatile const uint32_t*)&s_glob[qz * plane + qy * g.nx + qx] >= sf + (k < 7 ? 1u : 0u)) continue;
+      dirty[((qz / g.tz) * g.nty + qy / g.ty) * g.ntx + qx / g.tx] = 1;
     }
   }
 }
@@ -332,116 +634,73 @@ __global__ void k_compact(uint8_t* dirty, int64_t ntiles, uint32_t* list, Params
   }
 }
 
-// ----------------------------------------------------------------- encoder
-
-constexpr uint32_t kSlotBytes = 16384;  // a record never exceeds the raw chunk (16 KiB)
+// ----------------------------------------------------------------- subbin encoder
 
 template <typename T, int ND>
 struct EncSmem {
-  using C = TileCfg<T, ND>;
-  static constexpr int NP = C::TZ * C::TY * C::TX;  // points of a full tile
+  using G = TileGeom<T, ND>;
+  static constexpr int NP = G::NP;
   static constexpr int W = Traits<T>::W;
-  static constexpr uint32_t L = (uint32_t)NP * W;   // BIT output bytes of a full tile
-  static constexpr uint32_t LR = L + L / 8 + L / 64 + L / 512 + 16;  // RZE_w output bound
-  static constexpr size_t bytes() {
-    return (size_t)NP * 8 * 2 /*words*/ + L /*planes*/ + LR /*rze_w out*/ + (LR / 8 + 16) /*m0*/ +
-           (LR / 64 + 16) /*m1*/ + (LR / 512 + 16) /*m2*/ + ((LR / 8 + 16) / 4 + 8) * 4 /*pre*/ + 64 * 4;
-  }
+  static constexpr uint32_t L = (uint32_t)NP * W;                    // BIT output bytes of a full tile
+  static constexpr uint32_t LR = (L + L / 8 + L / 64 + L / 512 + 16 + 15) & ~15u;  // RZE_w output bound
+  // A: words -> staged record; B: planes; C: RZE_w output; work
+  static constexpr size_t bytes() { return (size_t)L + L + LR + RzeWork::bytes(LR) + 16; }
 };
 
-// Chunk encoder (Sec. III-C): bins with DIFFNB_w, BIT_w, RZE_1; subbins with BIT_w,
-// RZE_w, RZE_1 (record prefixed by the u32 RZE_w length).  A record that would not
-// be shorter than the raw chunk is stored raw (size flag bit 31).
+// Subbin record of each chunk (Sec. III-C, LC-generated pipeline): BIT_w, RZE_w,
+// RZE_1, prefixed by the u32 length of the RZE_w output; raw if not shorter.
 template <typename T, int ND>
-__global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_encode(Geometry g, const Params* P,
-                                                               const uint32_t* __restrict__ s_glob,
-                                                               const typename Traits<T>::Bin* __restrict__ b_glob,
-                                                               uint8_t* __restrict__ slots, uint32_t* __restrict__ sizes) {
-  using C = TileCfg<T, ND>;
+__global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_encode_sub(Geometry g, const Params* P,
+                                                                   const uint32_t* __restrict__ s_glob,
+                                                                   uint8_t* __restrict__ slots,
+                                                                   uint32_t* __restrict__ sizes) {
+  using G = TileGeom<T, ND>;
   using ES = EncSmem<T, ND>;
   using W_t = typename Traits<T>::Bits;
-  constexpr int NT = C::NT, W = Traits<T>::W;
+  constexpr int NT = G::NT, W = Traits<T>::W;
   if (P->status & kErrNonfinite) return;
   if (P->constant) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  W_t* wb = reinterpret_cast<W_t*>(smem);
-  W_t* ws = wb + ES::NP;
-  uint32_t* planes = reinterpret_cast<uint32_t*>(ws + ES::NP);
-  uint8_t* rzw = reinterpret_cast<uint8_t*>(planes) + ES::L;
-  RzeScratch sc;
-  sc.m0 = rzw + ES::LR;
-  sc.m1 = sc.m0 + ES::LR / 8 + 16;
-  sc.m2 = sc.m1 + ES::LR / 64 + 16;
-  sc.pre = reinterpret_cast<uint32_t*>(((uintptr_t)(sc.m2 + ES::LR / 512 + 16) + 15) & ~(uintptr_t)15);
-  sc.tmp = sc.pre + (ES::LR / 8 + 16) / 4 + 8;
+  W_t* ws = reinterpret_cast<W_t*>(smem);
+  uint8_t* stage = smem;
+  uint32_t* planes = reinterpret_cast<uint32_t*>(smem + ES::L);
+  uint8_t* rzw = smem + 2 * ES::L;
+  const RzeWork w = rze_work_at(rzw + ES::LR, ES::LR);
 
   const int64_t tid = blockIdx.x;
   const TileBox tb = tile_box(g, tid);
   const int n = tb.n, n32 = (n + 31) & ~31;
   const int64_t plane = g.ny * g.nx;
-  for (int i = threadIdx.x; i < n; i += NT) {
-    const int lx = i % tb.cx, ly = (i / tb.cx) % tb.cy, lz = i / (tb.cx * tb.cy);
-    const int64_t gi = (tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx;
-    wb[i] = (W_t)b_glob[gi];
-    ws[i] = (W_t)s_glob[gi];
+  if (n == G::NP) {
+    for (int i = threadIdx.x; i < n; i += NT) {
+      const int lx = i % G::TX, ly = (i / G::TX) % G::TY, lz = i / (G::TX * G::TY);
+      ws[i] = (W_t)s_glob[(tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx];
+    }
+  } else {
+    for (int i = threadIdx.x; i < n; i += NT) {
+      const int lx = i % tb.cx, ly = (i / tb.cx) % tb.cy, lz = i / (tb.cx * tb.cy);
+      ws[i] = (W_t)s_glob[(tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx];
+    }
   }
   __syncthreads();
   const uint32_t raw = (uint32_t)n * W;
-  uint8_t* slot_b = slots + (size_t)tid * kSlotBytes;
-  uint8_t* slot_s = slots + ((size_t)g.ntiles + tid) * kSlotBytes;
-  __shared__ uint32_t rec_len;
-
-  // bins: DIFFNB_w on the fly, BIT_w, RZE_1
-  constexpr W_t M = (W_t)0xAAAAAAAAAAAAAAAAULL;
-  bit_transpose<NT, W>(n32, [&](int i) -> uint64_t {
-    if (i >= n) return 0;
-    const W_t d = wb[i] - (i ? wb[i - 1] : (W_t)0);
-    return (uint64_t)((W_t)(d + M) ^ M);
-  }, planes);
-  __syncthreads();
-  uint32_t len = rze_encode<NT>(reinterpret_cast<const uint8_t*>(planes), W * n32, 1, slot_b, raw, sc);
-  if (len >= raw) {
-    for (int i = threadIdx.x; i < n; i += NT) reinterpret_cast<W_t*>(slot_b)[i] = wb[i];
-    len = raw | kRawFlag;
-  }
-  if (threadIdx.x == 0) rec_len = len;
-  __syncthreads();
-  len = rec_len;
-  {
-    const uint32_t l = len & ~kRawFlag, lp = (l + 15) & ~15u;
-    for (uint32_t j = l + threadIdx.x; j < lp; j += NT) slot_b[j] = 0;
-    if (threadIdx.x == 0) sizes[tid] = len;
-  }
-  __syncthreads();
-
-  // subbins: BIT_w, RZE_w (to shared memory), RZE_1
+  uint8_t* slot = slots + ((size_t)g.ntiles + tid) * kSlotBytes;
   bit_transpose<NT, W>(n32, [&](int i) -> uint64_t { return i < n ? (uint64_t)ws[i] : 0ULL; }, planes);
   __syncthreads();
-  const uint32_t l2 = rze_encode<NT>(reinterpret_cast<const uint8_t*>(planes), W * n32, W, rzw, 0xffffffffu, sc);
-  __syncthreads();
-  uint32_t len2 = 0;
-  if (raw > 4) len2 = rze_encode<NT>(rzw, l2, 1, slot_s + 4, raw - 4, sc);
-  if (raw <= 4 || len2 + 4 >= raw) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += NT) reinterpret_cast<W_t*>(slot_s)[i] = ws[i];
-    len2 = raw | kRawFlag;
-  } else {
-    if (threadIdx.x == 0) {
-      slot_s[0] = (uint8_t)l2;
-      slot_s[1] = (uint8_t)(l2 >> 8);
-      slot_s[2] = (uint8_t)(l2 >> 16);
-      slot_s[3] = (uint8_t)(l2 >> 24);
-    }
-    len2 += 4;
+  const uint32_t l2 = rze_encode<NT, W>(reinterpret_cast<const uint8_t*>(planes), W * n32, rzw, 0xffffffffu, w);
+  // the words in A are still intact: only B and C were written so far
+  uint32_t len = 0xffffffffu;
+  if (raw > 4) len = rze_encode<NT, 1>(rzw, l2, stage + 4, raw - 4, w);
+  if (raw <= 4 || len + 4 >= raw) {  // nothing was staged
+    for (int i = threadIdx.x; i < n; i += NT) reinterpret_cast<W_t*>(slot)[i] = ws[i];
+    if (threadIdx.x == 0) sizes[g.ntiles + tid] = raw | kRawFlag;
+    return;
   }
-  if (threadIdx.x == 0) rec_len = len2;
+  if (threadIdx.x == 0) *reinterpret_cast<uint32_t*>(stage) = l2;
+  zero_tail16<NT>(stage, len + 4);
   __syncthreads();
-  len2 = rec_len;
-  {
-    const uint32_t l = len2 & ~kRawFlag, lp = (l + 15) & ~15u;
-    for (uint32_t j = l + threadIdx.x; j < lp; j += NT) slot_s[j] = 0;
-    if (threadIdx.x == 0) sizes[g.ntiles + tid] = len2;
-  }
+  copy16<NT>(slot, stage, len + 4);
+  if (threadIdx.x == 0) sizes[g.ntiles + tid] = len + 4;
 }
 
 // ------------------------------------------------------------- scan + pack
@@ -526,14 +785,10 @@ __global__ void k_pack(HeaderInfo h, int64_t ntiles, const uint32_t* __restrict_
   }
 }
 
-// Exports bins and subbins (for stage-by-stage tests).
-template <typename T>
-__global__ void k_export(int64_t n, const uint32_t* __restrict__ s_glob, const typename Traits<T>::Bin* __restrict__ b_glob,
-                         int64_t* __restrict__ bins, uint64_t* __restrict__ subbins) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    bins[i] = (int64_t)b_glob[i];
+// Exports subbins (for stage-by-stage tests).
+__global__ void k_export_subbins(int64_t n, const uint32_t* __restrict__ s_glob, uint64_t* __restrict__ subbins) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     subbins[i] = (uint64_t)s_glob[i];
-  }
 }
 
 }  // namespace lopc

@@ -3,6 +3,7 @@
 // x_hat = succ^s(lowest value of bin b) (Sec. III-D, III-E).
 #pragma once
 #include "lopc_compress.cuh"
+#include "lopc_codec.cuh"
 
 namespace lopc {
 
@@ -35,44 +36,47 @@ __global__ void __launch_bounds__(NT) k_dec_offsets(const uint8_t* __restrict__ 
 
 template <typename T, int ND>
 struct DecSmem {
-  using C = TileCfg<T, ND>;
-  static constexpr int NP = C::TZ * C::TY * C::TX;
+  using G = TileGeom<T, ND>;
+  static constexpr int NP = G::NP;
   static constexpr int W = Traits<T>::W;
-  static constexpr uint32_t L = (uint32_t)NP * W;
-  static constexpr uint32_t LR = L + L / 8 + L / 64 + L / 512 + 16;  // largest legal RZE_w output
-  static constexpr size_t bytes() {
-    return (size_t)NP * W * 2 + L + LR + (LR / 8 + 16) + (LR / 64 + 16) + (LR / 512 + 16) +
-           ((LR / 8 + 16) / 4 + 8) * 4 + 64 * 4 + 64;
-  }
+  static constexpr uint32_t L = (uint32_t)NP * W;                                   // planes of a full tile
+  static constexpr uint32_t LR = (L + L / 8 + L / 64 + L / 512 + 16 + 15) & ~15u;  // largest legal RZE_w output
+  static constexpr uint32_t CACHE = 16384;                                          // bytes of bin-lowest keys
+  // A: staged record / subbin planes; B: bin planes / RZE_w bytes; C: key cache; WB: bins
+  static constexpr size_t bytes() { return (size_t)L + LR + CACHE + (size_t)NP * W + RzeWork::bytes(LR) + 16; }
 };
 
+// One block per chunk: bins (RZE_1, BIT_w, DIFFNB_w inverses), then the lowest value
+// of every bin of the tile's bin range (when it is small enough to cache), then
+// subbins (RZE_1, RZE_w, BIT_w inverses) and x_hat = the subbin-th value above the
+// bin's lowest value (Sec. III-E), written as the subbin words come out.
 template <typename T, int ND>
 __global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_decode(const uint8_t* __restrict__ in, Geometry g,
                                                                DecodeInfo di, const uint64_t* __restrict__ offs,
                                                                T* __restrict__ xhat, unsigned int* status) {
-  using C = TileCfg<T, ND>;
+  using G = TileGeom<T, ND>;
   using DS = DecSmem<T, ND>;
   using W_t = typename Traits<T>::Bits;
   using K = typename Traits<T>::Key;
-  constexpr int NT = C::NT, W = Traits<T>::W;
+  using B = typename Traits<T>::Bin;
+  constexpr int NT = G::NT, W = Traits<T>::W;
+  constexpr int CAPN = DS::CACHE / sizeof(K);
+  constexpr K kNone = (K)(-Traits<T>::kMaxKey - 1);  // never a valid key
   extern __shared__ __align__(16) unsigned char smem[];
-  W_t* wb = reinterpret_cast<W_t*>(smem);
-  W_t* ws = wb + DS::NP;
-  uint32_t* planes = reinterpret_cast<uint32_t*>(ws + DS::NP);
-  uint8_t* rz1 = reinterpret_cast<uint8_t*>(planes) + DS::L;
-  RzeScratch sc;
-  sc.m0 = rz1 + DS::LR;
-  sc.m1 = sc.m0 + DS::LR / 8 + 16;
-  sc.m2 = sc.m1 + DS::LR / 64 + 16;
-  sc.pre = reinterpret_cast<uint32_t*>(((uintptr_t)(sc.m2 + DS::LR / 512 + 16) + 15) & ~(uintptr_t)15);
-  sc.tmp = sc.pre + (DS::LR / 8 + 16) / 4 + 8;
+  uint8_t* A = smem;
+  uint8_t* Bf = smem + DS::L;
+  K* cache = reinterpret_cast<K*>(smem + DS::L + DS::LR);
+  W_t* wb = reinterpret_cast<W_t*>(smem + DS::L + DS::LR + DS::CACHE);
+  const RzeWork w = rze_work_at(reinterpret_cast<uint8_t*>(wb + DS::NP), DS::LR);
   __shared__ int bad;
+  __shared__ B red_min[NT / 32], red_max[NT / 32];
   if (*status & kErrCorrupt) return;
 
   const int64_t tid = blockIdx.x;
   const TileBox tb = tile_box(g, tid);
   const int n = tb.n, n32 = (n + 31) & ~31;
   const uint32_t raw = (uint32_t)n * W;
+  const bool full = n == G::NP;
   const uint32_t* tab = reinterpret_cast<const uint32_t*>(in + kHeaderBytes);
   const uint32_t sb = tab[tid], ss = tab[g.ntiles + tid];
   const uint8_t* rb = in + offs[tid];
@@ -86,11 +90,17 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_decode(const uint8_t* __
     for (int i = threadIdx.x; i < n; i += NT) wb[i] = reinterpret_cast<const W_t*>(rb)[i];
     __syncthreads();
   } else {
-    if (!rze_decode<NT>(rb, sb, (uint32_t)W * n32, 1, reinterpret_cast<uint8_t*>(planes), sc)) bad = 1;
+    if (sb >= raw) bad = 1;  // an encoded record is shorter than the raw chunk
     __syncthreads();
     if (!bad) {
+      copy16<NT>(A, rb, sb);
+      __syncthreads();
+      if (!rze_decode<NT, 1>(A, sb, (uint32_t)W * n32, Bf, w)) bad = 1;
+      __syncthreads();
+    }
+    if (!bad) {
       constexpr W_t M = (W_t)0xAAAAAAAAAAAAAAAAULL;
-      bit_untranspose<NT, W>(n32, planes, [&](int i, uint64_t u) {
+      bit_untranspose<NT, W>(n32, reinterpret_cast<const uint32_t*>(Bf), [&](int i, uint64_t u) {
         if (i < n)
           wb[i] = (W_t)(((W_t)u ^ M) - M);
         else if (u != 0)
@@ -111,60 +121,104 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_decode(const uint8_t* __
     }
     __syncthreads();
   }
-  // subbins
-  if (!bad) {
-    if (ss & kRawFlag) {
-      if ((ss & ~kRawFlag) != raw) bad = 1;
-      for (int i = threadIdx.x; i < n; i += NT) ws[i] = reinterpret_cast<const W_t*>(rs)[i];
-      __syncthreads();
-    } else {
-      const uint32_t len = ss;
-      uint32_t l2 = 0;
-      if (len < 4) {
-        bad = 1;
-      } else {
-        l2 = (uint32_t)rs[0] | ((uint32_t)rs[1] << 8) | ((uint32_t)rs[2] << 16) | ((uint32_t)rs[3] << 24);
-        if (l2 > DS::LR) bad = 1;
-      }
-      __syncthreads();
-      if (!bad && !rze_decode<NT>(rs + 4, len - 4, l2, 1, rz1, sc)) bad = 1;
-      __syncthreads();
-      if (!bad && !rze_decode<NT>(rz1, l2, (uint32_t)W * n32, W, reinterpret_cast<uint8_t*>(planes), sc)) bad = 1;
-      __syncthreads();
-      if (!bad) {
-        bit_untranspose<NT, W>(n32, planes, [&](int i, uint64_t u) {
-          if (i < n)
-            ws[i] = (W_t)u;
-          else if (u != 0)
-            bad = 1;
-        });
-      }
-      __syncthreads();
-    }
-  }
   if (bad) {
     if (threadIdx.x == 0) atomicOr(status, kErrCorrupt);
     return;
   }
-  // reconstruct
+
+  // the lowest value of every bin in [bmin, bmax], when that range is small
+  B lo_b = (B)(Traits<T>::kAbsent == INT32_MIN ? INT32_MAX : INT64_MAX), hi_b = (B)Traits<T>::kAbsent;
+  for (int i = threadIdx.x; i < n; i += NT) {
+    const B b = (B)wb[i];
+    lo_b = b < lo_b ? b : lo_b;
+    hi_b = b > hi_b ? b : hi_b;
+  }
+  for (int o = 16; o; o >>= 1) {
+    const B a = __shfl_xor_sync(0xffffffffu, lo_b, o), c = __shfl_xor_sync(0xffffffffu, hi_b, o);
+    lo_b = a < lo_b ? a : lo_b;
+    hi_b = c > hi_b ? c : hi_b;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red_min[threadIdx.x >> 5] = lo_b;
+    red_max[threadIdx.x >> 5] = hi_b;
+  }
+  __syncthreads();
+  B bmin = red_min[0], bmax = red_max[0];
+  for (int k = 1; k < NT / 32; ++k) {
+    bmin = red_min[k] < bmin ? red_min[k] : bmin;
+    bmax = red_max[k] > bmax ? red_max[k] : bmax;
+  }
+  const bool cached = (unsigned long long)((long long)bmax - (long long)bmin) < (unsigned long long)CAPN;
+  if (cached) {
+    const int range = (int)((long long)bmax - (long long)bmin) + 1;
+    for (int r = threadIdx.x; r < range; r += NT) {
+      K k;
+      cache[r] = lowest_key_in_bin<T>((long long)bmin + r, di.eps_q, di.inv_m, di.inv_e, k) ? k : kNone;
+    }
+  }
+  __syncthreads();
+
   const int64_t plane = g.ny * g.nx;
   bool fail = false;
-  for (int i = threadIdx.x; i < n; i += NT) {
-    const long long b = (long long)(typename Traits<T>::Bin)wb[i];
+  auto put = [&](int i, uint64_t s) {
+    const long long b = (long long)(B)wb[i];
     K k;
-    if (!lowest_key_in_bin<T>(b, di.eps_q, di.inv_m, di.inv_e, k)) {
+    if (cached) {
+      k = cache[b - (long long)bmin];
+      if (k == kNone) {
+        fail = true;
+        return;
+      }
+    } else if (!lowest_key_in_bin<T>(b, di.eps_q, di.inv_m, di.inv_e, k)) {
       fail = true;
-      continue;
+      return;
     }
-    const uint64_t s = (uint64_t)ws[i];
-    if (s > (uint64_t)(Traits<T>::kMaxKey - k)) {
+    if (s > (uint64_t)(long long)Traits<T>::kMaxKey - (uint64_t)(long long)k) {
       fail = true;
-      continue;
+      return;
     }
-    const int lx = i % tb.cx, ly = (i / tb.cx) % tb.cy, lz = i / (tb.cx * tb.cy);
+    int lx, ly, lz;
+    if (full) {
+      lx = i % G::TX;
+      ly = (i / G::TX) % G::TY;
+      lz = i / (G::TX * G::TY);
+    } else {
+      lx = i % tb.cx;
+      ly = (i / tb.cx) % tb.cy;
+      lz = i / (tb.cx * tb.cy);
+    }
     xhat[(tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx] = value_of_key<T>((K)(k + (K)s));
+  };
+
+  // subbins, reconstructed as they are decoded
+  if (ss & kRawFlag) {
+    if ((ss & ~kRawFlag) != raw) fail = true;
+    else
+      for (int i = threadIdx.x; i < n; i += NT) put(i, (uint64_t)reinterpret_cast<const W_t*>(rs)[i]);
+  } else {
+    if (ss < 4 || ss >= raw) bad = 1;
+    __syncthreads();
+    uint32_t l2 = 0;
+    if (!bad) {
+      copy16<NT>(A, rs, ss);
+      __syncthreads();
+      l2 = *reinterpret_cast<const uint32_t*>(A);
+      if (l2 > DS::LR) bad = 1;  // uniform: every thread reads the same word
+    }
+    if (!bad && !rze_decode<NT, 1>(A + 4, ss - 4, l2, Bf, w)) bad = 1;
+    __syncthreads();
+    if (!bad && !rze_decode<NT, W>(Bf, l2, (uint32_t)W * n32, A, w)) bad = 1;
+    __syncthreads();
+    if (!bad) {
+      bit_untranspose<NT, W>(n32, reinterpret_cast<const uint32_t*>(A), [&](int i, uint64_t u) {
+        if (i < n)
+          put(i, (uint64_t)(W_t)u);
+        else if (u != 0)
+          fail = true;
+      });
+    }
   }
-  if (__syncthreads_or(fail) && threadIdx.x == 0) atomicOr(status, kErrCorrupt);
+  if ((__syncthreads_or(fail) || bad) && threadIdx.x == 0) atomicOr(status, kErrCorrupt);
 }
 
 template <typename T>

@@ -37,10 +37,24 @@ struct Params {
   unsigned int status;            // kErr* bits
   unsigned long long const_bits;  // the constant's bits (float32: low 32 bits)
   unsigned int dirty_count;
+  int fast_ok;                    // inv_f is a normal float: the fast quantizer path may run
+  float inv_f;                    // inv rounded to float
   unsigned int pad0;
   unsigned long long total;       // stream bytes
   unsigned long long rounds;
+  unsigned long long fix_iters;   // sum over tile runs of fixpoint sweeps
+  unsigned long long fix_iters_max;
+  unsigned long long phase[8];    // SM cycles spent per kernel phase (block-summed, for measurement)
 };
+
+// Adds the cycles since `t0` to phase counter `k` (thread 0 of the block only).
+__device__ __forceinline__ void phase_mark(Params* P, int k, long long& t0) {
+  if (threadIdx.x == 0) {
+    const long long t = clock64();
+    atomicAdd(&P->phase[k], (unsigned long long)(t - t0));
+    t0 = t;
+  }
+}
 
 // ------------------------------------------------------------------- traits
 
@@ -162,12 +176,106 @@ __device__ __forceinline__ bool quantize_exact(T x, unsigned long long inv_m, in
   return true;
 }
 
-// q(v) >= b, comparing through the exact quantizer (overflow counts as +-inf).
+// Bin of a value, fast path first: t = x * inv in binary32 carries a relative error
+// below 2^-22.4 (x rounded to float when it is float64, inv rounded to float, one
+// product rounding).  When t lies farther than |t| * 2^-20 from every half-integer
+// the rounding of the exact product is the rounding of t; otherwise, and outside
+// the ranges where that bound holds, the exact integer path decides.
+template <typename T>
+__device__ __forceinline__ bool quantize_fast(T x, float inv_f, int fast_ok, unsigned long long inv_m, int inv_e,
+                                              long long& bin) {
+  if (fast_ok) {
+    float xf;
+    bool in_range;
+    if (sizeof(T) == 4) {
+      xf = (float)x;
+      in_range = true;
+    } else {
+      const double ax = fabs((double)x);
+      in_range = ax == 0.0 || (ax >= 1.1754943508222875e-38 && ax < 1.7014118346046923e38);
+      xf = __double2float_rn((double)x);
+    }
+    if (in_range) {
+      const float t = __fmul_rn(xf, inv_f);
+      const float at = fabsf(t);
+      if (at < 2097152.0f) {  // 2^21: rint(t) and t - rint(t) are exact
+        const float r = rintf(t);
+        const float room = __fsub_rn(0.5f, fabsf(__fsub_rn(t, r)));
+        if (room > __fmul_rn(at, 9.5367431640625e-07f)) {  // 2^-20
+          bin = (long long)r;
+          return true;
+        }
+      }
+    }
+  }
+  return quantize_exact<T>(x, inv_m, inv_e, bin);
+}
+
+// Significand and exponent of a finite value: |v| = m * 2^e.
+template <typename T>
+__device__ __forceinline__ void split_value(T v, uint64_t& m, int& e, bool& neg) {
+  if (sizeof(T) == 4) {
+    const uint32_t u = __float_as_uint((float)v);
+    neg = u >> 31;
+    const int ex = (u >> 23) & 0xff;
+    m = u & 0x7fffffu;
+    if (ex) {
+      m |= 0x800000u;
+      e = ex - 150;
+    } else {
+      e = -149;
+    }
+  } else {
+    const uint64_t u = (uint64_t)__double_as_longlong((double)v);
+    neg = u >> 63;
+    const int ex = (int)((u >> 52) & 0x7ff);
+    m = u & 0xfffffffffffffULL;
+    if (ex) {
+      m |= 0x10000000000000ULL;
+      e = ex - 1075;
+    } else {
+      e = -1074;
+    }
+  }
+}
+
+// Sign of (P * 2^sh - C) for a 128-bit P = (ph, pl), any shift, and 0 < C < 2^63.
+__device__ __forceinline__ int cmp_scaled(uint64_t ph, uint64_t pl, int sh, uint64_t C) {
+  const int pbits = ph ? 128 - __clzll((long long)ph) : (pl ? 64 - __clzll((long long)pl) : 0);
+  if (pbits == 0) return -1;
+  if (sh >= 0) {
+    if (pbits + sh > 63) return 1;
+    const uint64_t a = pl << sh;
+    return a > C ? 1 : (a < C ? -1 : 0);
+  }
+  const int r = -sh;
+  const int cbits = 64 - __clzll((long long)C);
+  if (cbits + r > 127) return -1;  // C * 2^r >= 2^127 > P
+  const unsigned __int128 c = (unsigned __int128)C << r;
+  const unsigned __int128 p = ((unsigned __int128)ph << 64) | pl;
+  return p > c ? 1 : (p < c ? -1 : 0);
+}
+
+// q(v) >= b, exactly: with t = v * inv, q(v) = round-half-even(t) is >= b iff
+// 2t > 2b - 1, or 2t == 2b - 1 and b is even.
 template <typename T>
 __device__ __forceinline__ bool bin_at_least(T v, long long b, unsigned long long inv_m, int inv_e) {
-  long long q;
-  if (!quantize_exact<T>(v, inv_m, inv_e, q)) return !(v < (T)0);
-  return q >= b;
+  uint64_t m;
+  int e;
+  bool neg;
+  split_value<T>(v, m, e, neg);
+  const long long c = 2 * b - 1;
+  if (m == 0) return 0 >= b;
+  const uint64_t pl = m * (uint64_t)inv_m, ph = __umul64hi(m, (uint64_t)inv_m);
+  const int sh = e + inv_e + 1;  // |2t| = (m * inv_m) * 2^sh
+  if (!neg) {
+    if (c < 0) return true;
+    const int r = cmp_scaled(ph, pl, sh, (uint64_t)c);
+    return r > 0 || (r == 0 && (b & 1) == 0);
+  }
+  if (c > 0) return false;
+  const int r = cmp_scaled(ph, pl, sh, (uint64_t)(-c));
+  return r < 0 || (r == 0 && (b & 1) == 0);
 }
 
 // Lowest value of the dtype whose bin is b (Sec. III-E: subbin 0 decodes to the
@@ -179,13 +287,13 @@ __device__ bool lowest_key_in_bin(long long b, double eps_q, unsigned long long 
                                   typename Traits<T>::Key& out) {
   using K = typename Traits<T>::Key;
   const K kmax = Traits<T>::kMaxKey;
-  const double g = __dmul_rn(__dsub_rn((double)b, 0.5), eps_q);
   K k;
-  if (!(g == g) || g > 1e300 || g < -1e300) {
-    k = 0;
+  if (sizeof(T) == 4) {
+    const float g = __fmul_rn(__fsub_rn((float)b, 0.5f), (float)eps_q);
+    k = is_finite_bits<float>(g) ? (K)order_key<float>(g) : (g > 0.f ? kmax : -kmax);
   } else {
-    const T gv = (T)g;
-    k = is_finite_bits<T>(gv) ? order_key<T>(gv) : (gv > (T)0 ? kmax : -kmax);
+    const double g = __dmul_rn(__dsub_rn((double)b, 0.5), eps_q);
+    k = is_finite_bits<double>(g) ? (K)order_key<double>(g) : (g > 0.0 ? kmax : -kmax);
   }
   bool ok = false;
   for (int step = 0; step < 8; ++step) {
@@ -218,8 +326,7 @@ __device__ bool lowest_key_in_bin(long long b, double eps_q, unsigned long long 
     }
     k = lo;
   }
-  long long q;
-  if (!quantize_exact<T>(value_of_key<T>(k), inv_m, inv_e, q) || q != b) return false;
+  if (bin_at_least<T>(value_of_key<T>(k), b + 1, inv_m, inv_e)) return false;  // bin b is empty
   out = k;
   return true;
 }
@@ -288,278 +395,6 @@ __device__ __forceinline__ V block_exclusive_scan(V v, V* tmp, V* total) {
   if (total) *total = tmp[NW];
   __syncthreads();
   return res;
-}
-
-// ------------------------------------------------------------- BIT_w stage
-
-// Bit-plane transpose of n32 words (a multiple of 32): plane k (k = 0 least
-// significant) is n32/32 u32 words, bit j of word g being bit k of word 32g+j.
-// `word(i)` supplies input word i (zero for padding).  One warp per group of 32.
-template <int NT, int W, typename WordFn>
-__device__ __forceinline__ void bit_transpose(int n32, WordFn word, uint32_t* planes) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int G = n32 >> 5;
-  for (int g = wid; g < G; g += NT / 32) {
-    const uint64_t v = word(32 * g + lane);
-    uint32_t lo_plane = 0, hi_plane = 0;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      const uint32_t r = __ballot_sync(0xffffffffu, (uint32_t)(v >> k) & 1u);
-      if (lane == k) lo_plane = r;
-    }
-    planes[lane * G + g] = lo_plane;
-    if (W == 8) {
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        const uint32_t r = __ballot_sync(0xffffffffu, (uint32_t)(v >> (32 + k)) & 1u);
-        if (lane == k) hi_plane = r;
-      }
-      planes[(32 + lane) * G + g] = hi_plane;
-    }
-  }
-}
-
-// Inverse of bit_transpose: `emit(i, word)` receives word i of the n32.
-template <int NT, int W, typename EmitFn>
-__device__ __forceinline__ void bit_untranspose(int n32, const uint32_t* planes, EmitFn emit) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int G = n32 >> 5;
-  for (int g = wid; g < G; g += NT / 32) {
-    const uint32_t lo_plane = planes[lane * G + g];
-    const uint32_t hi_plane = W == 8 ? planes[(32 + lane) * G + g] : 0u;
-    uint32_t lo = 0, hi = 0;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const uint32_t r = __ballot_sync(0xffffffffu, (lo_plane >> j) & 1u);
-      if (lane == j) lo = r;
-    }
-    if (W == 8) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const uint32_t r = __ballot_sync(0xffffffffu, (hi_plane >> j) & 1u);
-        if (lane == j) hi = r;
-      }
-    }
-    emit(32 * g + lane, (uint64_t)lo | ((uint64_t)hi << 32));
-  }
-}
-
-// ------------------------------------------------------------- RZE_g stage
-
-struct RzeScratch {
-  uint8_t* m0;   // level-0 bitmap (>= ceil(U/8) bytes)
-  uint8_t* m1;   // level-1 bitmap
-  uint8_t* m2;   // level-2 bitmap
-  uint32_t* pre; // per-word prefix counts (>= ceil(l0/4) + 1 words)
-  uint32_t* tmp; // scan scratch (NT/32 + 1)
-};
-
-__device__ __forceinline__ uint32_t bytes_ceil8(uint32_t n) { return (n + 7u) >> 3; }
-
-// Encodes `in` (L bytes, shared memory) with RZE_g: [level-2 bitmap][level-1 kept]
-// [level-0 kept][non-zero units].  If the encoding would not be shorter than
-// `limit` bytes nothing is written.  Returns the encoded length.
-template <int NT>
-__device__ uint32_t rze_encode(const uint8_t* in, uint32_t L, int g, uint8_t* out, uint32_t limit,
-                               const RzeScratch& sc) {
-  const uint32_t U = L / (uint32_t)g;
-  const uint32_t l0 = bytes_ceil8(U), l1 = bytes_ceil8(l0), l2 = bytes_ceil8(l1);
-  const int t = threadIdx.x;
-  // level 0: contiguous ranges of bitmap bytes per thread
-  const uint32_t per0 = (l0 + NT - 1) / NT;
-  const uint32_t a0 = min(l0, t * per0), b0 = min(l0, a0 + per0);
-  uint32_t cnt = 0;
-  for (uint32_t j = a0; j < b0; ++j) {
-    uint32_t byte = 0;
-    for (int bit = 0; bit < 8; ++bit) {
-      const uint32_t u = 8 * j + bit;
-      if (u >= U) break;
-      uint32_t nz = 0;
-      for (int k = 0; k < g; ++k) nz |= in[u * g + k];
-      if (nz) {
-        byte |= 1u << bit;
-        ++cnt;
-      }
-    }
-    sc.m0[j] = (uint8_t)byte;
-  }
-  uint32_t np;
-  const uint32_t pay_off = block_exclusive_scan<NT, uint32_t>(cnt, sc.tmp, &np);
-  // level 1: repeat elimination of m0
-  const uint32_t per1 = (l1 + NT - 1) / NT;
-  const uint32_t a1 = min(l1, t * per1), b1 = min(l1, a1 + per1);
-  uint32_t c1 = 0;
-  for (uint32_t jj = a1; jj < b1; ++jj) {
-    uint32_t byte = 0;
-    for (int bit = 0; bit < 8; ++bit) {
-      const uint32_t j = 8 * jj + bit;
-      if (j >= l0) break;
-      const uint8_t prev = j ? sc.m0[j - 1] : 0;
-      if (sc.m0[j] != prev) {
-        byte |= 1u << bit;
-        ++c1;
-      }
-    }
-    sc.m1[jj] = (uint8_t)byte;
-  }
-  uint32_t nk0;
-  const uint32_t k0_off = block_exclusive_scan<NT, uint32_t>(c1, sc.tmp, &nk0);
-  // level 2: repeat elimination of m1
-  const uint32_t per2 = (l2 + NT - 1) / NT;
-  const uint32_t a2 = min(l2, t * per2), b2 = min(l2, a2 + per2);
-  uint32_t c2 = 0;
-  for (uint32_t jj = a2; jj < b2; ++jj) {
-    uint32_t byte = 0;
-    for (int bit = 0; bit < 8; ++bit) {
-      const uint32_t j = 8 * jj + bit;
-      if (j >= l1) break;
-      const uint8_t prev = j ? sc.m1[j - 1] : 0;
-      if (sc.m1[j] != prev) {
-        byte |= 1u << bit;
-        ++c2;
-      }
-    }
-    sc.m2[jj] = (uint8_t)byte;
-  }
-  uint32_t nk1;
-  const uint32_t k1_off = block_exclusive_scan<NT, uint32_t>(c2, sc.tmp, &nk1);
-  const uint32_t total = l2 + nk1 + nk0 + np * (uint32_t)g;
-  if (total >= limit) return total;
-  // write
-  for (uint32_t j = t; j < l2; j += NT) out[j] = sc.m2[j];
-  {
-    uint32_t r = 0;
-    for (uint32_t jj = a2; jj < b2; ++jj)
-      for (int bit = 0; bit < 8; ++bit) {
-        const uint32_t j = 8 * jj + bit;
-        if (j >= l1) break;
-        if ((sc.m2[jj] >> bit) & 1u) out[l2 + k1_off + r++] = sc.m1[j];
-      }
-  }
-  {
-    uint32_t r = 0;
-    for (uint32_t jj = a1; jj < b1; ++jj)
-      for (int bit = 0; bit < 8; ++bit) {
-        const uint32_t j = 8 * jj + bit;
-        if (j >= l0) break;
-        if ((sc.m1[jj] >> bit) & 1u) out[l2 + nk1 + k0_off + r++] = sc.m0[j];
-      }
-  }
-  {
-    uint32_t r = 0;
-    uint8_t* pay = out + l2 + nk1 + nk0;
-    for (uint32_t j = a0; j < b0; ++j)
-      for (int bit = 0; bit < 8; ++bit) {
-        const uint32_t u = 8 * j + bit;
-        if (u >= U) break;
-        if ((sc.m0[j] >> bit) & 1u) {
-          for (int k = 0; k < g; ++k) pay[(pay_off + r) * g + k] = in[u * g + k];
-          ++r;
-        }
-      }
-  }
-  return total;
-}
-
-// Counts set bits of `bm` (nbits valid) into prefix words: pre[w] = set bits in
-// words [0, w), pre[nw] = total.  Bitmap bytes are read little-endian into words.
-template <int NT>
-__device__ uint32_t bitmap_prefix(const uint8_t* bm, uint32_t nbytes, uint32_t* pre, uint32_t* tmp) {
-  const uint32_t nw = (nbytes + 3) >> 2;
-  const uint32_t per = (nw + NT - 1) / NT;
-  const uint32_t a = min(nw, threadIdx.x * per), b = min(nw, a + per);
-  uint32_t c = 0;
-  for (uint32_t w = a; w < b; ++w) {
-    uint32_t v = 0;
-    for (int k = 0; k < 4; ++k) {
-      const uint32_t i = 4 * w + k;
-      if (i < nbytes) v |= (uint32_t)bm[i] << (8 * k);
-    }
-    c += __popc(v);
-  }
-  uint32_t total;
-  uint32_t run = block_exclusive_scan<NT, uint32_t>(c, tmp, &total);
-  for (uint32_t w = a; w < b; ++w) {
-    pre[w] = run;
-    uint32_t v = 0;
-    for (int k = 0; k < 4; ++k) {
-      const uint32_t i = 4 * w + k;
-      if (i < nbytes) v |= (uint32_t)bm[i] << (8 * k);
-    }
-    run += __popc(v);
-  }
-  if (threadIdx.x == 0) pre[nw] = total;
-  __syncthreads();
-  return total;
-}
-
-// Set bits of bm strictly before position j, from the prefix words.
-__device__ __forceinline__ uint32_t rank_before(const uint8_t* bm, uint32_t nbytes, const uint32_t* pre,
-                                                uint32_t j) {
-  const uint32_t w = j >> 5, off = j & 31;
-  uint32_t v = 0;
-  for (int k = 0; k < 4; ++k) {
-    const uint32_t i = 4 * w + k;
-    if (i < nbytes) v |= (uint32_t)bm[i] << (8 * k);
-  }
-  const uint32_t below = off ? (v & ((1u << off) - 1u)) : 0u;
-  return pre[w] + __popc(below);
-}
-
-__device__ __forceinline__ bool bit_of(const uint8_t* bm, uint32_t j) { return (bm[j >> 3] >> (j & 7)) & 1u; }
-
-// Tail bits [nbits, 8*ceil(nbits/8)) of a bitmap are zero.
-__device__ __forceinline__ bool tail_zero(const uint8_t* bm, uint32_t nbits) {
-  const uint32_t r = nbits & 7;
-  if (!r) return true;
-  return (bm[nbits >> 3] >> r) == 0;
-}
-
-// Inverse of rze_encode: `in` holds exactly in_len bytes (global or shared), `out`
-// receives L bytes (shared).  Returns false when the record is inconsistent.
-template <int NT>
-__device__ bool rze_decode(const uint8_t* in, uint32_t in_len, uint32_t L, int g, uint8_t* out,
-                           const RzeScratch& sc) {
-  const uint32_t U = L / (uint32_t)g;
-  const uint32_t l0 = bytes_ceil8(U), l1 = bytes_ceil8(l0), l2 = bytes_ceil8(l1);
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = in_len < l2;
-  __syncthreads();
-  if (bad) return false;
-  for (uint32_t j = threadIdx.x; j < l2; j += NT) sc.m2[j] = in[j];
-  __syncthreads();
-  if (threadIdx.x == 0 && !tail_zero(sc.m2, l1)) bad = 1;
-  const uint32_t nk1 = bitmap_prefix<NT>(sc.m2, l2, sc.pre, sc.tmp);
-  if (bad || l2 + nk1 > in_len) return false;
-  // level 1 bitmap: byte j = last kept byte at or before j
-  for (uint32_t j = threadIdx.x; j < l1; j += NT) {
-    const uint32_t r = rank_before(sc.m2, l2, sc.pre, j) + (bit_of(sc.m2, j) ? 1u : 0u);
-    sc.m1[j] = r ? in[l2 + r - 1] : 0;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0 && !tail_zero(sc.m1, l0)) bad = 1;
-  const uint32_t nk0 = bitmap_prefix<NT>(sc.m1, l1, sc.pre, sc.tmp);
-  if (bad || l2 + nk1 + nk0 > in_len) return false;
-  const uint8_t* k0 = in + l2 + nk1;
-  for (uint32_t j = threadIdx.x; j < l0; j += NT) {
-    const uint32_t r = rank_before(sc.m1, l1, sc.pre, j) + (bit_of(sc.m1, j) ? 1u : 0u);
-    sc.m0[j] = r ? k0[r - 1] : 0;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0 && !tail_zero(sc.m0, U)) bad = 1;
-  const uint32_t np = bitmap_prefix<NT>(sc.m0, l0, sc.pre, sc.tmp);
-  if (bad || (uint64_t)l2 + nk1 + nk0 + (uint64_t)np * g != in_len) return false;
-  const uint8_t* pay = in + l2 + nk1 + nk0;
-  for (uint32_t u = threadIdx.x; u < U; u += NT) {
-    if (bit_of(sc.m0, u)) {
-      const uint32_t r = rank_before(sc.m0, l0, sc.pre, u);
-      for (int k = 0; k < g; ++k) out[u * g + k] = pay[r * g + k];
-    } else {
-      for (int k = 0; k < g; ++k) out[u * g + k] = 0;
-    }
-  }
-  __syncthreads();
-  return true;
 }
 
 }  // namespace lopc

@@ -68,6 +68,8 @@ def lib():
         L.lopc_set_round_cap.argtypes = [C.c_int64]
         L.lopc_set_round_cap.restype = C.c_int64
         L.lopc_last_stats.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.lopc_last_fixpoint_stats.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.lopc_last_phase_cycles.argtypes = [C.POINTER(C.c_int64), C.c_int]
         L.lopc_profile_enable.argtypes = [C.c_int]
         L.lopc_profile_reset.argtypes = []
         L.lopc_profile_read.argtypes = [C.POINTER(C.c_char_p), C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int]
@@ -197,6 +199,20 @@ def last_stats() -> Tuple[int, int]:
     r, t = C.c_int64(), C.c_int64()
     lib().lopc_last_stats(C.byref(r), C.byref(t))
     return r.value, t.value
+
+
+def last_fixpoint_stats() -> Tuple[int, int]:
+    """(sweeps summed over tile runs, most sweeps of one run) of the last compression."""
+    a, b = C.c_int64(), C.c_int64()
+    lib().lopc_last_fixpoint_stats(C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def last_phase_cycles() -> list:
+    """SM cycles per kernel phase of the last compression (see include/lopc.h)."""
+    a = (C.c_int64 * 8)()
+    lib().lopc_last_phase_cycles(a, 8)
+    return [int(v) for v in a]
 
 
 def compress_status(x: torch.Tensor, eb: float, mode: int = NOA, out_cap: Optional[int] = None,
