@@ -108,6 +108,26 @@ LOPC_API size_t lopc_decompress_workspace_size(const lopc_field_desc* desc);
 LOPC_API int lopc_decompress(const void* d_in, size_t in_size, void* d_x, size_t x_cap, void* d_ws, size_t ws_size,
                     void* stream);
 
+/* ---- batches (many fields, one launch sequence).  The fields' tiles share one
+ * launch per kernel and one device-driven repair loop (a CUDA graph whose while-node
+ * runs repair rounds until no tile is dirty), so a batch costs no host round trip
+ * per round; each field's stream is byte-identical to its single-field stream.
+ * Host arrays hold n entries; d_out_size and d_status are DEVICE arrays of n that
+ * receive each field's stream length and status.  Asynchronous: nothing waits for
+ * the stream; read the results after synchronising.  The workspace must not be used
+ * by another call until this one has finished on the GPU. */
+LOPC_API size_t lopc_batch_compress_workspace_size(int n, const lopc_field_desc* descs);
+LOPC_API int lopc_batch_compress(int n, const lopc_field_desc* descs, const void* const* d_x, void* const* d_out,
+                                 const size_t* out_cap, uint64_t* d_out_size, int* d_status, void* d_ws,
+                                 size_t ws_size, void* stream);
+
+/* Decompresses n streams (descs from lopc_peek of each header) into d_x[i]; each
+ * stream's status goes to the DEVICE array d_status.  Asynchronous. */
+LOPC_API size_t lopc_batch_decompress_workspace_size(int n, const lopc_field_desc* descs);
+LOPC_API int lopc_batch_decompress(int n, const lopc_field_desc* descs, const void* const* d_in,
+                                   const size_t* in_size, void* const* d_x, int* d_status, void* d_ws,
+                                   size_t ws_size, void* stream);
+
 /* Decompression that allocates nothing and takes no workspace (the paper has no
  * counterpart; this is a library convenience).  It is meant for callers that cannot
  * call cudaMalloc: code running inside a memory allocator's callbacks, under a host
@@ -136,8 +156,8 @@ LOPC_API int64_t lopc_noalloc_max_chunks(void);
 LOPC_API int lopc_quantize_repair(const lopc_field_desc* desc, const void* d_x, int64_t* d_bins, uint64_t* d_subbins,
                          void* d_ws, size_t ws_size, void* stream);
 
-/* Caps the number of global repair rounds of later calls on this thread's library
- * instance (0 restores the default, which is never reached by a valid field).  A
+/* Caps the number of repair rounds after the first (all-tile) round for later calls
+ * on this thread (0 restores the default, which a valid field never reaches).  A
  * lowered cap makes lopc_compress return LOPC_ERR_NOT_CONVERGED.  Returns the
  * previous cap. */
 LOPC_API int64_t lopc_set_round_cap(int64_t cap);

@@ -5,6 +5,8 @@
 #include <string.h>
 
 #include <mutex>
+#include <algorithm>
+#include <vector>
 
 #include "lopc.h"
 #include "lopc_decompress.cuh"
@@ -135,23 +137,45 @@ Geometry geometry_of(const lopc_field_desc* d) {
   return g;
 }
 
-struct CompressLayout {
-  size_t params, dirty, done, list, s, cm, sizes, offs, slots, total;
+#define CK(call)                          \
+  do {                                    \
+    if ((call) != cudaSuccess) {          \
+      (void)cudaGetLastError();           \
+      return LOPC_ERR_CUDA;               \
+    }                                     \
+  } while (0)
+
+// Field classes: one kernel instantiation each.
+//   0 = float32 2D, 1 = float32 3D, 2 = float64 2D, 3 = float64 3D
+int class_of(int dtype, int ndim) { return (dtype == LOPC_F64 ? 2 : 0) + (ndim == 3 ? 1 : 0); }
+
+HeaderInfo header_info(const lopc_field_desc* d, const Geometry& g) {
+  HeaderInfo h;
+  h.dtype = d->dtype;
+  h.ndim = d->ndim;
+  h.mode = d->mode;
+  for (int k = 0; k < 3; ++k) h.dims[k] = k < d->ndim ? d->dims[k] : 0;
+  h.tile[0] = g.tz;
+  h.tile[1] = g.ty;
+  h.tile[2] = g.tx;
+  h.eb = d->eb;
+  return h;
+}
+
+// ------------------------------------------------------------ compress plan
+
+// Workspace of a compression launch: shared state, the field table and the
+// concatenated dirty flags and rerun list, then one part per field.
+struct FieldPart {
+  size_t params, s, cm, sizes, offs, slots, total;
 };
 
-CompressLayout compress_layout(const lopc_field_desc* d) {
-  const Geometry g = geometry_of(d);
+FieldPart field_part(const Geometry& g) {
   const size_t n = (size_t)(g.nz * g.ny * g.nx);
-  CompressLayout L;
+  FieldPart L;
   size_t o = 0;
   L.params = o;
   o = align256(o + sizeof(Params));
-  L.dirty = o;
-  o = align256(o + (size_t)g.ntiles);
-  L.done = o;
-  o = align256(o + (size_t)g.ntiles);
-  L.list = o;
-  o = align256(o + 4 * (size_t)g.ntiles);
   L.s = o;
   o = align256(o + 4 * n);
   L.cm = o;
@@ -166,141 +190,418 @@ CompressLayout compress_layout(const lopc_field_desc* d) {
   return L;
 }
 
-#define CK(call)                          \
-  do {                                    \
-    if ((call) != cudaSuccess) {          \
-      (void)cudaGetLastError();           \
-      return LOPC_ERR_CUDA;               \
-    }                                     \
-  } while (0)
+struct CompressPlan {
+  int n = 0;
+  std::vector<int> order;      // position in the launch -> caller's index
+  std::vector<FieldInfo> F;    // sorted by class, then caller's order
+  int cls_f0[4] = {0, 0, 0, 0}, cls_nf[4] = {0, 0, 0, 0};
+  int64_t cls_t0[4] = {0, 0, 0, 0}, cls_nt[4] = {0, 0, 0, 0};
+  int64_t bounds[5] = {0, 0, 0, 0, 0};
+  int64_t total_tiles = 0;
+  int64_t round_cap = 0;
+  size_t off_state = 0, off_table = 0, off_bounds = 0, off_dirty = 0, off_list = 0, off_results = 0;
+  std::vector<size_t> off_field;
+  size_t ws_total = 0;
+};
 
-int status_to_code(unsigned int st) {
-  if (st & kErrNonfinite) return LOPC_ERR_NONFINITE;
-  if (st & kErrRange) return LOPC_ERR_RANGE;
-  if (st & kErrNotConverged) return LOPC_ERR_NOT_CONVERGED;
-  if (st & kErrCorrupt) return LOPC_ERR_CORRUPT;
-  if (st & kErrInternal) return LOPC_ERR_CUDA;
-  return LOPC_OK;
-}
-
-template <typename T, int ND>
-int run_repair(const lopc_field_desc* d, const Geometry& g, const T* x, uint8_t* ws, const CompressLayout& L,
-               int64_t* bins_out, cudaStream_t st) {
-  using C = TileCfg<T, ND>;
-  Params* P = reinterpret_cast<Params*>(ws + L.params);
-  uint8_t* dirty = ws + L.dirty;
-  uint32_t* list = reinterpret_cast<uint32_t*>(ws + L.list);
-  uint32_t* s = reinterpret_cast<uint32_t*>(ws + L.s);
-  uint16_t* cm = reinterpret_cast<uint16_t*>(ws + L.cm);
-  uint32_t* sizes = reinterpret_cast<uint32_t*>(ws + L.sizes);
-  const int64_t n = g.nz * g.ny * g.nx;
-
-  LAUNCH("init_params", st, k_init_params<<<1, 1, 0, st>>>(P, d->eb, d->mode));
-  if (d->mode == LOPC_NOA) LAUNCH("range", st, k_range<T><<<148 * 8, 256, 0, st>>>(x, n, P));
-  LAUNCH("resolve_eps", st, k_resolve_eps<T><<<1, 1, 0, st>>>(P));
-  CK(cudaMemsetAsync(dirty, 0, (size_t)g.ntiles, st));
-  const size_t psmem = PassSmem<T, ND>::bytes(), rsmem = RerunSmem<T, ND>::bytes();
-  CK(cudaFuncSetAttribute(k_pass<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
-  CK(cudaFuncSetAttribute(k_rerun<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem));
-  LAUNCH("tile_pass", st,
-         k_pass<T, ND><<<(unsigned)g.ntiles, C::NT, psmem, st>>>(x, g, P, s, cm, bins_out, ws + L.slots, sizes));
-  CK(cudaGetLastError());
-  // round 1 visits every tile: each one tests its own incoming cross-tile constraints
-  LAUNCH("tile_rerun", st, k_rerun<T, ND><<<(unsigned)g.ntiles, C::NT, rsmem, st>>>(g, P, s, cm, dirty, nullptr));
-  CK(cudaGetLastError());
-  int64_t runs = 2 * g.ntiles, rounds = 1;
-  const int64_t cap = g_round_cap > 0 ? g_round_cap : n + 16;  // a chain has fewer than n links
-  const unsigned cgrid = (unsigned)imin64(ceil_div(g.ntiles, 256), 148 * 16);
-  while (true) {
-    CK(cudaMemsetAsync(&P->dirty_count, 0, sizeof(unsigned), st));
-    LAUNCH("compact", st, k_compact<<<cgrid, 256, 0, st>>>(dirty, g.ntiles, list, P));
-    unsigned cnt = 0, status = 0;
-    CK(cudaMemcpyAsync(&cnt, &P->dirty_count, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&status, &P->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (status & (kErrNonfinite | kErrRange | kErrNotConverged)) break;
-    if (cnt == 0) break;
-    if (rounds >= cap) {
-      unsigned bit = kErrNotConverged;
-      CK(cudaMemcpyAsync(&P->status, &bit, sizeof(unsigned), cudaMemcpyHostToDevice, st));
-      CK(cudaStreamSynchronize(st));
-      break;
-    }
-    LAUNCH("tile_rerun", st, k_rerun<T, ND><<<cnt, C::NT, rsmem, st>>>(g, P, s, cm, dirty, list));
-    CK(cudaGetLastError());
-    runs += cnt;
-    ++rounds;
+// Lays out a launch over descs[0..n) (sorted by class); fills pointers when ws != null.
+int plan_compress(int n, const lopc_field_desc* descs, const void* const* xs, void* const* outs, const size_t* caps,
+                  uint64_t* d_sizes, int* d_status, int64_t* bins_out, uint8_t* ws, CompressPlan& p) {
+  p = CompressPlan{};  // planning twice (size, then pointers) must not accumulate
+  p.n = n;
+  p.order.resize(n);
+  for (int i = 0; i < n; ++i) p.order[i] = i;
+  std::stable_sort(p.order.begin(), p.order.end(), [&](int a, int b) {
+    return class_of(descs[a].dtype, descs[a].ndim) < class_of(descs[b].dtype, descs[b].ndim);
+  });
+  p.F.assign(n, FieldInfo{});
+  int64_t tiles = 0, cap = 16;
+  for (int c = 0; c < 4; ++c) {
+    p.cls_f0[c] = 0;
+    p.cls_nf[c] = 0;
   }
-  g_last_rounds = rounds;
-  g_last_tile_runs = runs;
+  for (int k = 0; k < n; ++k) {
+    const lopc_field_desc* d = &descs[p.order[k]];
+    const int c = class_of(d->dtype, d->ndim);
+    if (p.cls_nf[c] == 0) {
+      p.cls_f0[c] = k;
+      p.cls_t0[c] = tiles;
+    }
+    ++p.cls_nf[c];
+    FieldInfo& f = p.F[k];
+    f.g = geometry_of(d);
+    f.hdr = header_info(d, f.g);
+    f.tile_base = tiles;
+    tiles += f.g.ntiles;
+    p.cls_nt[c] += f.g.ntiles;
+    const int64_t npts = f.g.nz * f.g.ny * f.g.nx;
+    cap = std::max<int64_t>(cap, npts + 16);  // a chain has fewer than n links
+  }
+  for (int c = 0; c < 4; ++c)
+    if (p.cls_nf[c] == 0) p.cls_t0[c] = c ? p.cls_t0[c - 1] + p.cls_nt[c - 1] : 0;
+  for (int c = 0; c < 4; ++c) p.bounds[c] = p.cls_t0[c];
+  p.bounds[4] = tiles;
+  // classes may be empty: keep the bounds monotone
+  for (int c = 1; c < 5; ++c) p.bounds[c] = std::max(p.bounds[c], p.bounds[c - 1]);
+  p.total_tiles = tiles;
+  p.round_cap = g_round_cap > 0 ? g_round_cap : cap;
+  size_t o = 0;
+  p.off_state = o;
+  o = align256(o + sizeof(BatchState));
+  p.off_table = o;
+  o = align256(o + (size_t)n * sizeof(FieldInfo));
+  p.off_bounds = o;
+  o = align256(o + 5 * sizeof(int64_t));
+  p.off_results = o;
+  o = align256(o + 16);
+  p.off_dirty = o;
+  o = align256(o + (size_t)tiles);
+  p.off_list = o;
+  o = align256(o + 4 * (size_t)tiles);
+  p.off_field.resize(n);
+  for (int k = 0; k < n; ++k) {
+    p.off_field[k] = o;
+    o += field_part(p.F[k].g).total;
+  }
+  p.ws_total = o;
+  if (!ws) return LOPC_OK;
+  for (int k = 0; k < n; ++k) {
+    const int i = p.order[k];
+    FieldInfo& f = p.F[k];
+    const FieldPart L = field_part(f.g);
+    uint8_t* base = ws + p.off_field[k];
+    f.x = xs ? xs[i] : nullptr;
+    f.out = outs ? reinterpret_cast<uint8_t*>(outs[i]) : nullptr;
+    f.out_cap = caps ? (uint64_t)caps[i] : 0;
+    f.P = reinterpret_cast<Params*>(base + L.params);
+    f.s = reinterpret_cast<uint32_t*>(base + L.s);
+    f.cm = reinterpret_cast<uint16_t*>(base + L.cm);
+    f.sizes = reinterpret_cast<uint32_t*>(base + L.sizes);
+    f.offs = reinterpret_cast<uint64_t*>(base + L.offs);
+    f.slots = base + L.slots;
+    f.bins_out = bins_out;
+    f.size_out = d_sizes ? d_sizes + i : nullptr;
+    f.status_out = d_status ? d_status + i : nullptr;
+    f.round_cap = p.round_cap;
+  }
+  return LOPC_OK;
+}
+
+// Library-owned stream for capturing the body of the repair loop.
+cudaStream_t side_stream() {
+  thread_local cudaStream_t s = nullptr;
+  if (!s) cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  return s;
+}
+
+template <typename T, int ND>
+int set_smem_attrs() {
+  static bool done = false;  // per instantiation; attributes are per function and device-wide
+  if (done) return LOPC_OK;
+  CK(cudaFuncSetAttribute(k_pass<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassSmem<T, ND>::bytes()));
+  CK(cudaFuncSetAttribute(k_rerun<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RerunSmem<T, ND>::bytes()));
+  CK(cudaFuncSetAttribute(k_encode_sub<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EncSmem<T, ND>::bytes()));
+  CK(cudaFuncSetAttribute(k_decode<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DecSmem<T, ND>::bytes()));
+  done = true;
+  return LOPC_OK;
+}
+
+int rerun_blocks() {
+  thread_local int v = 0;
+  if (!v) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    v = sms * 3;
+  }
+  return v;
+}
+
+template <typename T, int ND>
+int launch_class_pre(const CompressPlan& p, int c, const FieldInfo* dF, cudaStream_t st) {
+  using C = TileCfg<T, ND>;
+  if (!p.cls_nf[c]) return LOPC_OK;
+  int rc = set_smem_attrs<T, ND>();
+  if (rc) return rc;
+  LAUNCH("range", st, k_range<T><<<dim3(148 * 4, p.cls_nf[c]), 256, 0, st>>>(dF, p.cls_f0[c]));
+  LAUNCH("resolve_eps", st, k_resolve_eps<T><<<(p.cls_nf[c] + 63) / 64, 64, 0, st>>>(dF, p.cls_f0[c], p.cls_nf[c]));
+  LAUNCH("tile_pass", st,
+         k_pass<T, ND><<<(unsigned)p.cls_nt[c], C::NT, PassSmem<T, ND>::bytes(), st>>>(dF, p.cls_f0[c], p.cls_nf[c],
+                                                                                      p.cls_t0[c]));
+  CK(cudaGetLastError());
   return LOPC_OK;
 }
 
 template <typename T, int ND>
-int compress_impl(const lopc_field_desc* d, const void* d_x, void* d_out, size_t out_cap, size_t* out_size,
-                  void* d_ws, cudaStream_t st) {
+int launch_class_rerun(const CompressPlan& p, int c, const FieldInfo* dF, const BatchState* dB, const uint32_t* list,
+                       uint8_t* dirty, cudaStream_t st) {
   using C = TileCfg<T, ND>;
-  using B = typename Traits<T>::Bin;
-  const Geometry g = geometry_of(d);
-  const CompressLayout L = compress_layout(d);
-  uint8_t* ws = reinterpret_cast<uint8_t*>(d_ws);
-  Params* P = reinterpret_cast<Params*>(ws + L.params);
-  int rc = run_repair<T, ND>(d, g, reinterpret_cast<const T*>(d_x), ws, L, nullptr, st);
-  if (rc) return rc;
-  const size_t esmem = EncSmem<T, ND>::bytes();
-  CK(cudaFuncSetAttribute(k_encode_sub<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esmem));
-  uint32_t* sizes = reinterpret_cast<uint32_t*>(ws + L.sizes);
-  uint64_t* offs = reinterpret_cast<uint64_t*>(ws + L.offs);
+  if (!p.cls_nf[c]) return LOPC_OK;
+  const unsigned grid = (unsigned)imin64(p.cls_nt[c], rerun_blocks());
+  LAUNCH("tile_rerun", st,
+         k_rerun<T, ND><<<grid, C::NT, RerunSmem<T, ND>::bytes(), st>>>(dF, p.cls_f0[c], p.cls_nf[c], p.cls_t0[c],
+                                                                       p.cls_nt[c], c, dB, list, dirty));
+  CK(cudaGetLastError());
+  return LOPC_OK;
+}
+
+template <typename T, int ND>
+int launch_class_encode(const CompressPlan& p, int c, const FieldInfo* dF, cudaStream_t st) {
+  using C = TileCfg<T, ND>;
+  if (!p.cls_nf[c]) return LOPC_OK;
   LAUNCH("encode_subbins", st,
-         k_encode_sub<T, ND><<<(unsigned)g.ntiles, C::NT, esmem, st>>>(g, P, reinterpret_cast<const uint32_t*>(ws + L.s),
-                                                                     ws + L.slots, sizes));
+         k_encode_sub<T, ND><<<(unsigned)p.cls_nt[c], C::NT, EncSmem<T, ND>::bytes(), st>>>(dF, p.cls_f0[c],
+                                                                                           p.cls_nf[c], p.cls_t0[c]));
   CK(cudaGetLastError());
-  const int64_t m = 2 * g.ntiles;
-  const uint64_t base = kHeaderBytes + ((uint64_t)m * 4 + 15) / 16 * 16;
-  LAUNCH("scan_sizes", st, k_scan_sizes<1024><<<1, 1024, 0, st>>>(sizes, m, base, offs, P));
-  HeaderInfo h;
-  h.dtype = d->dtype;
-  h.ndim = d->ndim;
-  h.mode = d->mode;
-  for (int k = 0; k < 3; ++k) h.dims[k] = k < d->ndim ? d->dims[k] : 0;
-  h.tile[0] = g.tz;
-  h.tile[1] = g.ty;
-  h.tile[2] = g.tx;
-  h.eb = d->eb;
-  const unsigned pgrid = (unsigned)imin64(m, 148 * 16);
-  LAUNCH("pack", st, k_pack<<<pgrid, 256, 0, st>>>(h, g.ntiles, sizes, offs, ws + L.slots, reinterpret_cast<uint8_t*>(d_out),
-                                (uint64_t)out_cap, P));
+  return LOPC_OK;
+}
+
+struct Ptrs {
+  FieldInfo* F;
+  BatchState* B;
+  int64_t* bounds;
+  uint8_t* dirty;
+  uint32_t* list;
+};
+
+Ptrs ptrs_of(const CompressPlan& p, uint8_t* ws) {
+  Ptrs q;
+  q.F = reinterpret_cast<FieldInfo*>(ws + p.off_table);
+  q.B = reinterpret_cast<BatchState*>(ws + p.off_state);
+  q.bounds = reinterpret_cast<int64_t*>(ws + p.off_bounds);
+  q.dirty = ws + p.off_dirty;
+  q.list = reinterpret_cast<uint32_t*>(ws + p.off_list);
+  return q;
+}
+
+int launch_reruns(const CompressPlan& p, const Ptrs& q, const uint32_t* list, cudaStream_t st) {
+  int rc;
+  if ((rc = launch_class_rerun<float, 2>(p, 0, q.F, q.B, list, q.dirty, st))) return rc;
+  if ((rc = launch_class_rerun<float, 3>(p, 1, q.F, q.B, list, q.dirty, st))) return rc;
+  if ((rc = launch_class_rerun<double, 2>(p, 2, q.F, q.B, list, q.dirty, st))) return rc;
+  return launch_class_rerun<double, 3>(p, 3, q.F, q.B, list, q.dirty, st);
+}
+
+// Everything before the repair loop: state reset, range, eps, tile pass, the first
+// (all-tile) rerun round and its compaction.
+int enqueue_prologue(const CompressPlan& p, const Ptrs& q, cudaStream_t st, cudaGraphConditionalHandle h, int use_h) {
+  int rc;
+  CK(cudaMemsetAsync(q.B, 0, sizeof(BatchState), st));
+  CK(cudaMemsetAsync(q.dirty, 0, (size_t)p.total_tiles, st));
+  LAUNCH("init_params", st, k_init_params<<<(p.n + 63) / 64, 64, 0, st>>>(q.F, p.n));
+  if ((rc = launch_class_pre<float, 2>(p, 0, q.F, st))) return rc;
+  if ((rc = launch_class_pre<float, 3>(p, 1, q.F, st))) return rc;
+  if ((rc = launch_class_pre<double, 2>(p, 2, q.F, st))) return rc;
+  if ((rc = launch_class_pre<double, 3>(p, 3, q.F, st))) return rc;
+  if ((rc = launch_reruns(p, q, nullptr, st))) return rc;
+  LAUNCH("compact", st,
+         k_compact<1024><<<1, 1024, 0, st>>>(q.dirty, p.total_tiles, q.list, q.B, q.bounds, q.F, p.n, p.round_cap, h, use_h));
   CK(cudaGetLastError());
+  return LOPC_OK;
+}
+
+int enqueue_loop_body(const CompressPlan& p, const Ptrs& q, cudaStream_t st, cudaGraphConditionalHandle h, int use_h) {
+  int rc;
+  if ((rc = launch_reruns(p, q, q.list, st))) return rc;
+  LAUNCH("compact", st,
+         k_compact<1024><<<1, 1024, 0, st>>>(q.dirty, p.total_tiles, q.list, q.B, q.bounds, q.F, p.n, p.round_cap, h, use_h));
+  CK(cudaGetLastError());
+  return LOPC_OK;
+}
+
+int enqueue_epilogue(const CompressPlan& p, const Ptrs& q, cudaStream_t st) {
+  int rc;
+  if ((rc = launch_class_encode<float, 2>(p, 0, q.F, st))) return rc;
+  if ((rc = launch_class_encode<float, 3>(p, 1, q.F, st))) return rc;
+  if ((rc = launch_class_encode<double, 2>(p, 2, q.F, st))) return rc;
+  if ((rc = launch_class_encode<double, 3>(p, 3, q.F, st))) return rc;
+  LAUNCH("scan_sizes", st, k_scan_sizes<1024><<<p.n, 1024, 0, st>>>(q.F));
+  LAUNCH("pack", st, k_pack<<<dim3(148 * 2, p.n), 256, 0, st>>>(q.F));
+  LAUNCH("finalize", st, k_finalize<<<(p.n + 63) / 64, 64, 0, st>>>(q.F, p.n));
+  CK(cudaGetLastError());
+  return LOPC_OK;
+}
+
+// Uploads the field table and the class bounds (not part of any graph).
+int upload_plan(const CompressPlan& p, const Ptrs& q, cudaStream_t st) {
+  CK(cudaMemcpyAsync(q.F, p.F.data(), (size_t)p.n * sizeof(FieldInfo), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(q.bounds, p.bounds, sizeof(p.bounds), cudaMemcpyHostToDevice, st));
+  return LOPC_OK;
+}
+
+// Repair rounds driven by the host (one small read-back per round); used while
+// per-kernel event timing is on, where every launch must be a direct launch.
+int run_host_loop(const CompressPlan& p, const Ptrs& q, cudaStream_t st) {
+  int rc = enqueue_prologue(p, q, st, cudaGraphConditionalHandle{}, 0);
+  if (rc) return rc;
+  while (true) {
+    BatchState hb;
+    CK(cudaMemcpyAsync(&hb, q.B, sizeof(BatchState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hb.count[0] + hb.count[1] + hb.count[2] + hb.count[3] == 0) break;
+    if ((rc = enqueue_loop_body(p, q, st, cudaGraphConditionalHandle{}, 0))) return rc;
+  }
+  return enqueue_epilogue(p, q, st);
+}
+
+// The whole compression as one CUDA graph: the repair rounds run in a conditional
+// while-node whose condition the compaction kernel sets on the device.
+int capture_graph(const CompressPlan& p, const Ptrs& q, cudaStream_t st, cudaGraphExec_t* exec) {
+  cudaGraph_t graph = nullptr;
+  cudaStream_t cap = side_stream();
+  if (!cap) return LOPC_ERR_CUDA;
+  // capture on the library's own stream, so the caller's stream is never in capture mode
+  CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  int rc = LOPC_OK;
+  cudaGraphConditionalHandle h{};
+  if (cudaStreamGetCaptureInfo(cap, &cs, nullptr, &cg, nullptr, nullptr, nullptr) != cudaSuccess ||
+      cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+    rc = LOPC_ERR_CUDA;
+  if (!rc) rc = enqueue_prologue(p, q, cap, h, 1);
+  cudaGraphNode_t cnode = nullptr;
+  cudaGraph_t body = nullptr;
+  if (!rc) {
+    if (cudaStreamGetCaptureInfo(cap, &cs, nullptr, &cg, &deps, nullptr, &ndeps) != cudaSuccess) rc = LOPC_ERR_CUDA;
+  }
+  if (!rc) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp) != cudaSuccess ||
+        cudaStreamUpdateCaptureDependencies(cap, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+      rc = LOPC_ERR_CUDA;
+    else
+      body = cp.conditional.phGraph_out[0];
+  }
+  if (!rc) {
+    // the body: reruns of the listed tiles, then the next compaction
+    thread_local cudaStream_t bs = nullptr;
+    if (!bs) cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+    if (!bs || cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      rc = LOPC_ERR_CUDA;
+    if (!rc) {
+      rc = enqueue_loop_body(p, q, bs, h, 1);
+      cudaGraph_t b2 = nullptr;
+      if (cudaStreamEndCapture(bs, &b2) != cudaSuccess && !rc) rc = LOPC_ERR_CUDA;
+    }
+  }
+  if (!rc) rc = enqueue_epilogue(p, q, cap);
+  if (cudaStreamEndCapture(cap, &graph) != cudaSuccess && !rc) rc = LOPC_ERR_CUDA;
+  if (!rc && cudaGraphInstantiate(exec, graph, 0) != cudaSuccess) rc = LOPC_ERR_CUDA;
+  if (graph) cudaGraphDestroy(graph);
+  (void)st;
+  if (rc) (void)cudaGetLastError();
+  return rc;
+}
+
+// Instantiated graphs keyed by everything the captured launches depend on.
+struct GraphCache {
+  struct Entry {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec;
+    uint64_t used;
+  };
+  std::vector<Entry> e;
+  uint64_t tick = 0;
+  cudaGraphExec_t* find(const std::vector<uint64_t>& key) {
+    for (auto& x : e)
+      if (x.key == key) {
+        x.used = ++tick;
+        return &x.exec;
+      }
+    return nullptr;
+  }
+  void put(std::vector<uint64_t> key, cudaGraphExec_t exec) {
+    if (e.size() >= 16) {
+      auto it = std::min_element(e.begin(), e.end(), [](const Entry& a, const Entry& b) { return a.used < b.used; });
+      cudaGraphExecDestroy(it->exec);
+      e.erase(it);
+    }
+    e.push_back(Entry{std::move(key), exec, ++tick});
+  }
+};
+thread_local GraphCache g_graphs;
+
+std::vector<uint64_t> plan_key(const CompressPlan& p, const uint8_t* ws) {
+  std::vector<uint64_t> k;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  k.push_back((uint64_t)dev);
+  k.push_back((uint64_t)(uintptr_t)ws);
+  k.push_back((uint64_t)p.n);
+  k.push_back((uint64_t)p.round_cap);
+  for (const FieldInfo& f : p.F) {
+    const uint64_t* w = reinterpret_cast<const uint64_t*>(&f);
+    for (size_t i = 0; i < sizeof(FieldInfo) / 8; ++i) k.push_back(w[i]);
+  }
+  return k;
+}
+
+// Enqueues a planned compression on `st`: as a cached graph, or as direct launches
+// with a host-driven loop while per-kernel timing is on.
+int run_compress(const CompressPlan& p, uint8_t* ws, cudaStream_t st) {
+  const Ptrs q = ptrs_of(p, ws);
+  int rc = upload_plan(p, q, st);
+  if (rc) return rc;
+  if (g_prof.on) return run_host_loop(p, q, st);
+  std::vector<uint64_t> key = plan_key(p, ws);
+  cudaGraphExec_t* ex = g_graphs.find(key);
+  if (!ex) {
+    cudaGraphExec_t e = nullptr;
+    if ((rc = capture_graph(p, q, st, &e))) return rc;
+    g_graphs.put(std::move(key), e);
+    ex = g_graphs.find(plan_key(p, ws));
+  }
+  CK(cudaGraphLaunch(*ex, st));
+  return LOPC_OK;
+}
+
+// Single field: plan, run, read back the size and status.
+int compress_one(const lopc_field_desc* d, const void* d_x, void* d_out, size_t out_cap, size_t* out_size,
+                 int64_t* bins_out, uint64_t* subbins_out, void* d_ws, size_t ws_size, cudaStream_t st) {
+  CompressPlan p;
+  const void* xs[1] = {d_x};
+  void* outs[1] = {d_out};
+  size_t caps[1] = {out_cap};
+  plan_compress(1, d, xs, outs, caps, nullptr, nullptr, nullptr, nullptr, p);
+  if (!d_ws || ws_size < p.ws_total) return LOPC_ERR_WORKSPACE;
+  uint8_t* ws = reinterpret_cast<uint8_t*>(d_ws);
+  uint64_t* dsize = reinterpret_cast<uint64_t*>(ws + p.off_results);
+  int* dstat = reinterpret_cast<int*>(ws + p.off_results + 8);
+  plan_compress(1, d, xs, outs, caps, dsize, dstat, bins_out, ws, p);
+  int rc = run_compress(p, ws, st);
+  if (rc) return rc;
+  const FieldInfo& f = p.F[0];
+  if (subbins_out)
+    LAUNCH("export", st,
+           k_export_subbins<<<148 * 8, 256, 0, st>>>(f.g.nz * f.g.ny * f.g.nx, f.s, subbins_out));
+  struct {
+    uint64_t size;
+    int status;
+    int pad;
+  } res;
   Params hp;
-  CK(cudaMemcpyAsync(&hp, P, sizeof(Params), cudaMemcpyDeviceToHost, st));
+  BatchState hb;
+  CK(cudaMemcpyAsync(&res, dsize, 16, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&hp, f.P, sizeof(Params), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&hb, ptrs_of(p, ws).B, sizeof(BatchState), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  g_last_rounds = (int64_t)hb.rounds;
+  g_last_tile_runs = (int64_t)(2 * f.g.ntiles + hb.runs);
   g_last_fix_iters = (int64_t)hp.fix_iters;
   g_last_fix_iters_max = (int64_t)hp.fix_iters_max;
   for (int k = 0; k < 8; ++k) g_last_phase[k] = (int64_t)hp.phase[k];
-  rc = status_to_code(hp.status);
-  if (rc) return rc;
-  if (hp.total > out_cap) return LOPC_ERR_CAPACITY;
-  *out_size = (size_t)hp.total;
+  // the repair ran even if the output was too small: report the repair's status first
+  if (res.status == LOPC_ERR_CAPACITY && subbins_out) res.status = LOPC_OK;
+  if (res.status) return res.status;
+  if (out_size) *out_size = (size_t)res.size;
   return LOPC_OK;
-}
-
-template <typename T, int ND>
-int quantize_repair_impl(const lopc_field_desc* d, const void* d_x, int64_t* bins, uint64_t* subbins, void* d_ws,
-                         cudaStream_t st) {
-  const Geometry g = geometry_of(d);
-  const CompressLayout L = compress_layout(d);
-  uint8_t* ws = reinterpret_cast<uint8_t*>(d_ws);
-  int rc = run_repair<T, ND>(d, g, reinterpret_cast<const T*>(d_x), ws, L, bins, st);
-  if (rc) return rc;
-  const int64_t n = g.nz * g.ny * g.nx;
-  LAUNCH("export", st, k_export_subbins<<<148 * 8, 256, 0, st>>>(n, reinterpret_cast<const uint32_t*>(ws + L.s), subbins));
-  CK(cudaGetLastError());
-  Params hp;
-  CK(cudaMemcpyAsync(&hp, ws + L.params, sizeof(Params), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  g_last_fix_iters = (int64_t)hp.fix_iters;
-  g_last_fix_iters_max = (int64_t)hp.fix_iters_max;
-  return status_to_code(hp.status);
 }
 
 // ------------------------------------------------------------ header parsing
@@ -348,38 +649,128 @@ int parse_header(const uint8_t* h, size_t n, Header* H) {
   return LOPC_OK;
 }
 
-template <typename T, int ND>
-int decompress_impl(const Header& H, const uint8_t* in, size_t in_size, void* d_x, uint8_t* ws, cudaStream_t st) {
-  using C = TileCfg<T, ND>;
-  const Geometry g = geometry_of(&H.d);
-  const int64_t n = g.nz * g.ny * g.nx;
-  unsigned int* status = reinterpret_cast<unsigned int*>(ws);
-  uint64_t* offs = reinterpret_cast<uint64_t*>(ws + 256);
-  CK(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
-  if (H.constant) {
-    LAUNCH("fill", st, k_fill<T><<<148 * 8, 256, 0, st>>>(reinterpret_cast<T*>(d_x), n, H.const_bits));
-  } else {
-    if ((uint64_t)kHeaderBytes + ((uint64_t)g.ntiles * 8 + 15) / 16 * 16 > H.total) return LOPC_ERR_CORRUPT;
-    LAUNCH("dec_offsets", st, k_dec_offsets<1024><<<1, 1024, 0, st>>>(in, H.total, g.ntiles, offs, status));
-    const size_t smem = DecSmem<T, ND>::bytes();
-    CK(cudaFuncSetAttribute(k_decode<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    DecodeInfo di;
-    di.eps_q = 1.0 / H.inv;  // only seeds the search for a bin's lowest value
-    const uint64_t iu = [&] {
-      uint64_t v;
-      memcpy(&v, &H.inv, 8);
-      return v;
-    }();
-    const int ex = (int)((iu >> 52) & 0x7ff);
-    di.inv_m = (iu & 0xfffffffffffffULL) | (ex ? 0x10000000000000ULL : 0ULL);
-    di.inv_e = ex ? ex - 1075 : -1074;
-    LAUNCH("decode", st, k_decode<T, ND><<<(unsigned)g.ntiles, C::NT, smem, st>>>(in, g, di, offs, reinterpret_cast<T*>(d_x), status));
+// ------------------------------------------------------------ decompress plan
+
+struct DecompressPlan {
+  int n = 0;
+  std::vector<int> order;
+  std::vector<DecField> F;
+  int cls_f0[4] = {0, 0, 0, 0}, cls_nf[4] = {0, 0, 0, 0};
+  int64_t cls_t0[4] = {0, 0, 0, 0}, cls_nt[4] = {0, 0, 0, 0};
+  size_t off_table = 0, off_status = 0;
+  std::vector<size_t> off_offs;
+  size_t ws_total = 0;
+};
+
+// Layout: the stream table and one status word per stream in the first aligned
+// block, then each stream's record offsets.
+int plan_decompress(int n, const lopc_field_desc* descs, const void* const* ins, const size_t* in_sizes,
+                    void* const* xs, int* d_status, uint8_t* ws, DecompressPlan& p) {
+  p = DecompressPlan{};  // planning twice (size, then pointers) must not accumulate
+  p.n = n;
+  p.order.resize(n);
+  for (int i = 0; i < n; ++i) p.order[i] = i;
+  std::stable_sort(p.order.begin(), p.order.end(), [&](int a, int b) {
+    return class_of(descs[a].dtype, descs[a].ndim) < class_of(descs[b].dtype, descs[b].ndim);
+  });
+  p.F.assign(n, DecField{});
+  int64_t tiles = 0;
+  for (int k = 0; k < n; ++k) {
+    const lopc_field_desc* d = &descs[p.order[k]];
+    const int c = class_of(d->dtype, d->ndim);
+    if (p.cls_nf[c] == 0) {
+      p.cls_f0[c] = k;
+      p.cls_t0[c] = tiles;
+    }
+    ++p.cls_nf[c];
+    DecField& f = p.F[k];
+    f.g = geometry_of(d);
+    f.tile_base = tiles;
+    tiles += f.g.ntiles;
+    p.cls_nt[c] += f.g.ntiles;
   }
+  size_t o = 0;
+  p.off_table = o;
+  o += (size_t)n * sizeof(DecField);
+  p.off_status = o;
+  o = align256(o + 4 * (size_t)n);
+  p.off_offs.resize(n);
+  for (int k = 0; k < n; ++k) {
+    p.off_offs[k] = o;
+    o = align256(o + 16 * (size_t)p.F[k].g.ntiles);
+  }
+  p.ws_total = o;
+  if (!ws) return LOPC_OK;
+  for (int k = 0; k < n; ++k) {
+    const int i = p.order[k];
+    DecField& f = p.F[k];
+    f.in = reinterpret_cast<const uint8_t*>(ins[i]);
+    f.in_size = (uint64_t)in_sizes[i];
+    f.x = xs[i];
+    f.offs = reinterpret_cast<uint64_t*>(ws + p.off_offs[k]);
+    f.status = reinterpret_cast<unsigned int*>(ws + p.off_status) + k;
+    f.status_out = d_status ? d_status + i : nullptr;
+  }
+  return LOPC_OK;
+}
+static_assert(sizeof(DecField) + 4 <= 256, "a one-stream table and its status fit the first 256 bytes");
+
+template <typename T, int ND>
+int launch_class_decode(const DecompressPlan& p, int c, const DecField* dF, cudaStream_t st) {
+  using C = TileCfg<T, ND>;
+  if (!p.cls_nf[c]) return LOPC_OK;
+  int rc = set_smem_attrs<T, ND>();
+  if (rc) return rc;
+  LAUNCH("decode", st,
+         k_decode<T, ND><<<(unsigned)p.cls_nt[c], C::NT, DecSmem<T, ND>::bytes(), st>>>(dF, p.cls_f0[c], p.cls_nf[c],
+                                                                                       p.cls_t0[c]));
   CK(cudaGetLastError());
-  unsigned hs = 0;
-  CK(cudaMemcpyAsync(&hs, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  return LOPC_OK;
+}
+
+int run_decompress(const DecompressPlan& p, uint8_t* ws, cudaStream_t st) {
+  DecField* dF = reinterpret_cast<DecField*>(ws + p.off_table);
+  CK(cudaMemcpyAsync(dF, p.F.data(), (size_t)p.n * sizeof(DecField), cudaMemcpyHostToDevice, st));
+  LAUNCH("dec_setup", st, k_dec_setup<<<(p.n + 63) / 64, 64, 0, st>>>(dF, p.n));
+  LAUNCH("dec_offsets", st, k_dec_offsets<1024><<<p.n, 1024, 0, st>>>(dF));
+  int rc;
+  if ((rc = launch_class_decode<float, 2>(p, 0, dF, st))) return rc;
+  if ((rc = launch_class_decode<float, 3>(p, 1, dF, st))) return rc;
+  if ((rc = launch_class_decode<double, 2>(p, 2, dF, st))) return rc;
+  if ((rc = launch_class_decode<double, 3>(p, 3, dF, st))) return rc;
+  LAUNCH("dec_finalize", st, k_dec_finalize<<<(p.n + 63) / 64, 64, 0, st>>>(dF, p.n));
+  CK(cudaGetLastError());
+  return LOPC_OK;
+}
+
+// Single stream, decoded with the workspace `ws`: header to the host (the launch
+// needs the field's class and shape), then the planned launch and its status.
+int decompress_one(const void* d_in, size_t in_size, void* d_x, size_t x_cap, uint8_t* ws, size_t ws_size,
+                   cudaStream_t st, size_t max_chunks) {
+  if (!d_in || !d_x) return LOPC_ERR_INVALID_ARG;
+  if (in_size < (size_t)kHeaderBytes) return LOPC_ERR_CORRUPT;
+  uint8_t hb[kHeaderBytes];
+  CK(cudaMemcpyAsync(hb, d_in, kHeaderBytes, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  (void)in_size;
+  Header H;
+  int rc = parse_header(hb, in_size, &H);
+  if (rc) return rc;
+  const Geometry g = geometry_of(&H.d);
+  if (max_chunks && (size_t)g.ntiles > max_chunks) return LOPC_ERR_WORKSPACE;  // beyond a fixed scratch
+  if (H.total > in_size) return LOPC_ERR_CORRUPT;
+  const size_t need = (size_t)(g.nz * g.ny * g.nx) * word_bytes(H.d.dtype);
+  if (x_cap < need) return LOPC_ERR_CAPACITY;
+  DecompressPlan p;
+  plan_decompress(1, &H.d, nullptr, nullptr, nullptr, nullptr, nullptr, p);
+  if (!ws || ws_size < p.ws_total) return LOPC_ERR_WORKSPACE;
+  const void* ins[1] = {d_in};
+  size_t sizes[1] = {in_size};
+  void* xs[1] = {d_x};
+  plan_decompress(1, &H.d, ins, sizes, xs, nullptr, ws, p);
+  if ((rc = run_decompress(p, ws, st))) return rc;
+  unsigned hs = 0;
+  CK(cudaMemcpyAsync(&hs, ws + p.off_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   return hs ? LOPC_ERR_CORRUPT : LOPC_OK;
 }
 
@@ -396,60 +787,72 @@ size_t lopc_compress_bound(const lopc_field_desc* d) {
   return kHeaderBytes + ((size_t)g.ntiles * 8 + 15) / 16 * 16 + 2 * (n * word_bytes(d->dtype) + 16 * (size_t)g.ntiles);
 }
 
-size_t lopc_compress_workspace_size(const lopc_field_desc* d) {
-  if (!desc_valid(d)) return 0;
-  return compress_layout(d).total;
+size_t lopc_compress_workspace_size(const lopc_field_desc* d) { return lopc_batch_compress_workspace_size(1, d); }
+
+size_t lopc_batch_compress_workspace_size(int n, const lopc_field_desc* descs) {
+  if (n <= 0 || !descs) return 0;
+  for (int i = 0; i < n; ++i)
+    if (!desc_valid(&descs[i])) return 0;
+  CompressPlan p;
+  plan_compress(n, descs, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, p);
+  return p.ws_total;
 }
 
-size_t lopc_decompress_workspace_size(const lopc_field_desc* d) {
-  if (!desc_valid(d)) return 0;
-  const Geometry g = geometry_of(d);
-  return 256 + align256(16 * (size_t)g.ntiles);
+size_t lopc_decompress_workspace_size(const lopc_field_desc* d) { return lopc_batch_decompress_workspace_size(1, d); }
+
+size_t lopc_batch_decompress_workspace_size(int n, const lopc_field_desc* descs) {
+  if (n <= 0 || !descs) return 0;
+  for (int i = 0; i < n; ++i)
+    if (!desc_valid(&descs[i])) return 0;
+  DecompressPlan p;
+  plan_decompress(n, descs, nullptr, nullptr, nullptr, nullptr, nullptr, p);
+  return p.ws_total;
 }
 
-static int compress_entry(const lopc_field_desc* d, const void* d_x, void* d_out, size_t out_cap, size_t* out_size,
-                          void* d_ws, size_t ws_size, void* stream);
 int lopc_compress(const lopc_field_desc* d, const void* d_x, void* d_out, size_t out_cap, size_t* out_size, void* d_ws,
                   size_t ws_size, void* stream) {
-  const int rc = compress_entry(d, d_x, d_out, out_cap, out_size, d_ws, ws_size, stream);
+  int rc;
+  if (!desc_valid(d) || !d_x || !d_out || !out_size) {
+    rc = LOPC_ERR_INVALID_ARG;
+  } else if (out_cap < (size_t)kHeaderBytes) {
+    rc = LOPC_ERR_CAPACITY;
+  } else {
+    rc = compress_one(d, d_x, d_out, out_cap, out_size, nullptr, nullptr, d_ws, ws_size,
+                      reinterpret_cast<cudaStream_t>(stream));
+  }
   g_prof.resolve();
   return rc;
 }
 
-static int compress_entry(const lopc_field_desc* d, const void* d_x, void* d_out, size_t out_cap, size_t* out_size,
-                          void* d_ws, size_t ws_size, void* stream) {
-  if (!desc_valid(d) || !d_x || !d_out || !out_size) return LOPC_ERR_INVALID_ARG;
-  if (!d_ws || ws_size < lopc_compress_workspace_size(d)) return LOPC_ERR_WORKSPACE;
-  if (out_cap < (size_t)kHeaderBytes) return LOPC_ERR_CAPACITY;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int nd = d->ndim;
-  if (d->dtype == LOPC_F32)
-    return nd == 2 ? compress_impl<float, 2>(d, d_x, d_out, out_cap, out_size, d_ws, st)
-                   : compress_impl<float, 3>(d, d_x, d_out, out_cap, out_size, d_ws, st);
-  return nd == 2 ? compress_impl<double, 2>(d, d_x, d_out, out_cap, out_size, d_ws, st)
-                 : compress_impl<double, 3>(d, d_x, d_out, out_cap, out_size, d_ws, st);
+int lopc_batch_compress(int n, const lopc_field_desc* descs, const void* const* d_x, void* const* d_out,
+                        const size_t* out_cap, uint64_t* d_out_size, int* d_status, void* d_ws, size_t ws_size,
+                        void* stream) {
+  if (n <= 0 || !descs || !d_x || !d_out || !out_cap || !d_out_size || !d_status) return LOPC_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!desc_valid(&descs[i]) || !d_x[i] || !d_out[i]) return LOPC_ERR_INVALID_ARG;
+  CompressPlan p;
+  plan_compress(n, descs, d_x, d_out, out_cap, d_out_size, d_status, nullptr, nullptr, p);
+  if (!d_ws || ws_size < p.ws_total) return LOPC_ERR_WORKSPACE;
+  plan_compress(n, descs, d_x, d_out, out_cap, d_out_size, d_status, nullptr, reinterpret_cast<uint8_t*>(d_ws), p);
+  const int rc = run_compress(p, reinterpret_cast<uint8_t*>(d_ws), reinterpret_cast<cudaStream_t>(stream));
+  if (g_prof.on) {
+    (void)cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    g_prof.resolve();
+  }
+  return rc;
 }
 
-static int quantize_repair_entry(const lopc_field_desc* d, const void* d_x, int64_t* d_bins, uint64_t* d_subbins,
-                                 void* d_ws, size_t ws_size, void* stream);
 int lopc_quantize_repair(const lopc_field_desc* d, const void* d_x, int64_t* d_bins, uint64_t* d_subbins, void* d_ws,
                          size_t ws_size, void* stream) {
-  const int rc = quantize_repair_entry(d, d_x, d_bins, d_subbins, d_ws, ws_size, stream);
+  int rc;
+  if (!desc_valid(d) || !d_x || !d_bins || !d_subbins) {
+    rc = LOPC_ERR_INVALID_ARG;
+  } else {
+    // the whole compression runs; with no output capacity the stream is not packed
+    rc = compress_one(d, d_x, d_ws, 0, nullptr, d_bins, d_subbins, d_ws, ws_size, reinterpret_cast<cudaStream_t>(stream));
+  }
   g_prof.resolve();
   return rc;
-}
-
-static int quantize_repair_entry(const lopc_field_desc* d, const void* d_x, int64_t* d_bins, uint64_t* d_subbins,
-                                 void* d_ws, size_t ws_size, void* stream) {
-  if (!desc_valid(d) || !d_x || !d_bins || !d_subbins) return LOPC_ERR_INVALID_ARG;
-  if (!d_ws || ws_size < lopc_compress_workspace_size(d)) return LOPC_ERR_WORKSPACE;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int nd = d->ndim;
-  if (d->dtype == LOPC_F32)
-    return nd == 2 ? quantize_repair_impl<float, 2>(d, d_x, d_bins, d_subbins, d_ws, st)
-                   : quantize_repair_impl<float, 3>(d, d_x, d_bins, d_subbins, d_ws, st);
-  return nd == 2 ? quantize_repair_impl<double, 2>(d, d_x, d_bins, d_subbins, d_ws, st)
-                 : quantize_repair_impl<double, 3>(d, d_x, d_bins, d_subbins, d_ws, st);
 }
 
 int lopc_peek(const void* h_stream, size_t n, lopc_field_desc* out) {
@@ -461,38 +864,29 @@ int lopc_peek(const void* h_stream, size_t n, lopc_field_desc* out) {
   return LOPC_OK;
 }
 
-static int decompress_entry(const void* d_in, size_t in_size, void* d_x, size_t x_cap, void* d_ws, size_t ws_size,
-                            void* stream);
 int lopc_decompress(const void* d_in, size_t in_size, void* d_x, size_t x_cap, void* d_ws, size_t ws_size,
                     void* stream) {
-  const int rc = decompress_entry(d_in, in_size, d_x, x_cap, d_ws, ws_size, stream);
+  const int rc = decompress_one(d_in, in_size, d_x, x_cap, reinterpret_cast<uint8_t*>(d_ws), ws_size,
+                                reinterpret_cast<cudaStream_t>(stream), 0);
   g_prof.resolve();
   return rc;
 }
 
-static int decompress_entry(const void* d_in, size_t in_size, void* d_x, size_t x_cap, void* d_ws, size_t ws_size,
-                            void* stream) {
-  if (!d_in || !d_x) return LOPC_ERR_INVALID_ARG;
-  if (in_size < (size_t)kHeaderBytes) return LOPC_ERR_CORRUPT;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  uint8_t hb[kHeaderBytes];
-  CK(cudaMemcpyAsync(hb, d_in, kHeaderBytes, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  Header H;
-  int rc = parse_header(hb, in_size, &H);
-  if (rc) return rc;
-  if (H.total > in_size) return LOPC_ERR_CORRUPT;
-  const Geometry g = geometry_of(&H.d);
-  const size_t need = (size_t)(g.nz * g.ny * g.nx) * word_bytes(H.d.dtype);
-  if (x_cap < need) return LOPC_ERR_CAPACITY;
-  if (!d_ws || ws_size < lopc_decompress_workspace_size(&H.d)) return LOPC_ERR_WORKSPACE;
-  const uint8_t* in = reinterpret_cast<const uint8_t*>(d_in);
-  uint8_t* ws = reinterpret_cast<uint8_t*>(d_ws);
-  if (H.d.dtype == LOPC_F32)
-    return H.d.ndim == 2 ? decompress_impl<float, 2>(H, in, in_size, d_x, ws, st)
-                         : decompress_impl<float, 3>(H, in, in_size, d_x, ws, st);
-  return H.d.ndim == 2 ? decompress_impl<double, 2>(H, in, in_size, d_x, ws, st)
-                       : decompress_impl<double, 3>(H, in, in_size, d_x, ws, st);
+int lopc_batch_decompress(int n, const lopc_field_desc* descs, const void* const* d_in, const size_t* in_size,
+                          void* const* d_x, int* d_status, void* d_ws, size_t ws_size, void* stream) {
+  if (n <= 0 || !descs || !d_in || !in_size || !d_x || !d_status) return LOPC_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!desc_valid(&descs[i]) || !d_in[i] || !d_x[i]) return LOPC_ERR_INVALID_ARG;
+  DecompressPlan p;
+  plan_decompress(n, descs, d_in, in_size, d_x, d_status, nullptr, p);
+  if (!d_ws || ws_size < p.ws_total) return LOPC_ERR_WORKSPACE;
+  plan_decompress(n, descs, d_in, in_size, d_x, d_status, reinterpret_cast<uint8_t*>(d_ws), p);
+  const int rc = run_decompress(p, reinterpret_cast<uint8_t*>(d_ws), reinterpret_cast<cudaStream_t>(stream));
+  if (g_prof.on) {
+    (void)cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    g_prof.resolve();
+  }
+  return rc;
 }
 
 // ------------------------------------------------- decompression without allocation
@@ -531,31 +925,12 @@ int noalloc_scratch(uint8_t** out) {
 }  // namespace
 
 int lopc_decompress_noalloc(const void* d_in, size_t in_size, void* d_x, size_t x_cap, void* stream) {
-  if (!d_in || !d_x) return LOPC_ERR_INVALID_ARG;
-  if (in_size < (size_t)kHeaderBytes) return LOPC_ERR_CORRUPT;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   uint8_t* ws = nullptr;
   int rc = noalloc_scratch(&ws);
-  if (rc) return rc;
-  uint8_t hb[kHeaderBytes];
-  CK(cudaMemcpyAsync(hb, d_in, kHeaderBytes, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  Header H;
-  rc = parse_header(hb, in_size, &H);
-  if (rc) return rc;
-  const Geometry g = geometry_of(&H.d);
-  if (g.ntiles > kNoAllocMaxChunks) return LOPC_ERR_WORKSPACE;  // beyond the fixed scratch
-  if (H.total > in_size) return LOPC_ERR_CORRUPT;
-  const size_t need = (size_t)(g.nz * g.ny * g.nx) * word_bytes(H.d.dtype);
-  if (x_cap < need) return LOPC_ERR_CAPACITY;
-  const uint8_t* in = reinterpret_cast<const uint8_t*>(d_in);
-  // decompress_impl zeroes the status word and rewrites every offset it reads
-  if (H.d.dtype == LOPC_F32)
-    rc = H.d.ndim == 2 ? decompress_impl<float, 2>(H, in, in_size, d_x, ws, st)
-                       : decompress_impl<float, 3>(H, in, in_size, d_x, ws, st);
-  else
-    rc = H.d.ndim == 2 ? decompress_impl<double, 2>(H, in, in_size, d_x, ws, st)
-                       : decompress_impl<double, 3>(H, in, in_size, d_x, ws, st);
+  // every offset the decoder reads is rewritten and its status word zeroed first
+  if (!rc)
+    rc = decompress_one(d_in, in_size, d_x, x_cap, ws, kNoAllocScratchBytes, reinterpret_cast<cudaStream_t>(stream),
+                        (size_t)kNoAllocMaxChunks);
   g_prof.resolve();
   return rc;
 }

@@ -11,19 +11,19 @@ template <typename T, int ND>
 struct TileCfg;
 template <>
 struct TileCfg<float, 3> {
-  static constexpr int TZ = 16, TY = 16, TX = 16, HZ = 1, NT = 256, MINB = 3, MINB_RERUN = 4;
+  static constexpr int TZ = 16, TY = 16, TX = 16, HZ = 1, NT = 256, MINB = 3, MINB_RERUN = 3;
 };
 template <>
 struct TileCfg<double, 3> {
-  static constexpr int TZ = 8, TY = 16, TX = 16, HZ = 1, NT = 128, MINB = 3, MINB_RERUN = 8;
+  static constexpr int TZ = 8, TY = 16, TX = 16, HZ = 1, NT = 128, MINB = 3, MINB_RERUN = 6;
 };
 template <>
 struct TileCfg<float, 2> {
-  static constexpr int TZ = 1, TY = 64, TX = 64, HZ = 0, NT = 256, MINB = 3, MINB_RERUN = 4;
+  static constexpr int TZ = 1, TY = 64, TX = 64, HZ = 0, NT = 256, MINB = 3, MINB_RERUN = 3;
 };
 template <>
 struct TileCfg<double, 2> {
-  static constexpr int TZ = 1, TY = 32, TX = 64, HZ = 0, NT = 128, MINB = 6, MINB_RERUN = 8;
+  static constexpr int TZ = 1, TY = 32, TX = 64, HZ = 0, NT = 128, MINB = 5, MINB_RERUN = 6;
 };
 
 // Freudenthal neighbourhood (Sec. II): offsets +-d, d in {0,1}^3 \ {0}.  Direction
@@ -48,11 +48,14 @@ __device__ __forceinline__ bool dir_valid(int k) {
 
 // ------------------------------------------------------------------ range
 
-__global__ void k_init_params(Params* P, double eb, int mode) {
+__global__ void k_init_params(const FieldInfo* F, int nf) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  Params* P = F[f].P;
   P->kmin = ~0ULL;
   P->kmax = 0ULL;
-  P->eb = eb;
-  P->mode = mode;
+  P->eb = F[f].hdr.eb;
+  P->mode = F[f].hdr.mode;
   P->status = 0;
   P->constant = 0;
   P->dirty_count = 0;
@@ -70,10 +73,16 @@ __device__ __forceinline__ unsigned long long biased(typename Traits<T>::Key k) 
   return (unsigned long long)((long long)k) ^ 0x8000000000000000ULL;
 }
 
-// Sec. III-A (NOA): x_min and x_max over the field, as order keys.
+// Sec. III-A (NOA): x_min and x_max over each field, as order keys; blockIdx.y is
+// the field within the class.
 template <typename T>
-__global__ void k_range(const T* __restrict__ x, int64_t n, Params* P) {
+__global__ void k_range(const FieldInfo* F, int f0) {
   using K = typename Traits<T>::Key;
+  const FieldInfo& fi = F[f0 + blockIdx.y];
+  if (fi.hdr.mode != LOPC_NOA) return;
+  const T* __restrict__ x = reinterpret_cast<const T*>(fi.x);
+  const int64_t n = fi.g.nz * fi.g.ny * fi.g.nx;
+  Params* P = fi.P;
   K lo = Traits<T>::kMaxKey, hi = -Traits<T>::kMaxKey;
   bool bad = false;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -100,10 +109,14 @@ __global__ void k_range(const T* __restrict__ x, int64_t n, Params* P) {
 }
 
 // Sec. III-A: eps = eb (ABS) or eb * (x_max - x_min) (NOA); eps_q = eps (1 - 2^-16);
-// inv = 1 / eps_q.  IEEE binary64, correctly rounded, no contraction.
+// inv = 1 / eps_q.  IEEE binary64, correctly rounded, no contraction.  One thread
+// per field of the class.
 template <typename T>
-__global__ void k_resolve_eps(Params* P) {
+__global__ void k_resolve_eps(const FieldInfo* F, int f0, int nf) {
   using K = typename Traits<T>::Key;
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  Params* P = F[f0 + f].P;
   if (P->status & kErrNonfinite) return;
   double eps = P->eb;
   if (P->mode == LOPC_NOA) {
@@ -312,17 +325,25 @@ struct PassSmem {
 //   5. encode the tile's bin record (Sec. III-C; bins are final here).
 template <typename T, int ND>
 __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
-    k_pass(const T* __restrict__ x, Geometry g, Params* P, uint32_t* __restrict__ s_glob,
-           uint16_t* __restrict__ cm_glob, int64_t* __restrict__ bins_out, uint8_t* __restrict__ slots,
-           uint32_t* __restrict__ sizes) {
+    k_pass(const FieldInfo* __restrict__ F, int f0, int nf, int64_t tile0) {
   using G = TileGeom<T, ND>;
   using PS = PassSmem<T, ND>;
   using K = typename Traits<T>::Key;
   using B = typename Traits<T>::Bin;
   using WordT = typename Traits<T>::Bits;
   constexpr int NT = G::NT, W = Traits<T>::W;
+  const int64_t gt = tile0 + blockIdx.x;
+  const FieldInfo& fi = F[field_of_tile(F, f0, nf, gt)];
+  Params* P = fi.P;
   if (P->status & kErrNonfinite) return;
   if (P->constant) return;
+  const Geometry g = fi.g;
+  const T* __restrict__ x = reinterpret_cast<const T*>(fi.x);
+  uint32_t* __restrict__ s_glob = fi.s;
+  uint16_t* __restrict__ cm_glob = fi.cm;
+  int64_t* __restrict__ bins_out = fi.bins_out;
+  uint8_t* __restrict__ slots = fi.slots;
+  uint32_t* __restrict__ sizes = fi.sizes;
   extern __shared__ __align__(16) unsigned char smem[];
   K* key = reinterpret_cast<K*>(smem);
   uint32_t* sv = reinterpret_cast<uint32_t*>(smem);
@@ -331,7 +352,8 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   uint32_t* fa = reinterpret_cast<uint32_t*>(smem + PS::RA + PS::RB + PS::RC);
   uint32_t* fb = fa + G::NP / 32;
 
-  const int64_t tid = blockIdx.x;
+  const int64_t tid = gt - fi.tile_base;
+  if (tid < 0 || tid >= g.ntiles) return;  // never for a consistent plan
   const TileBox tb = tile_box(g, tid);
   const unsigned long long inv_m = P->inv_m;
   const int inv_e = P->inv_e;
@@ -505,132 +527,181 @@ struct RerunSmem {
 // whose constraints from risen boundary points are now violated.
 template <typename T, int ND>
 __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN)
-    k_rerun(Geometry g, Params* P, uint32_t* __restrict__ s_glob, const uint16_t* __restrict__ cm_glob,
-            uint8_t* __restrict__ dirty, const uint32_t* __restrict__ list) {
+    k_rerun(const FieldInfo* __restrict__ F, int f0, int nf, int64_t tile0, int64_t ntile_cls, int cls,
+            const BatchState* __restrict__ B, const uint32_t* __restrict__ list, uint8_t* __restrict__ dirty) {
   using G = TileGeom<T, ND>;
+  using RS = RerunSmem<T, ND>;
   constexpr int NT = G::NT;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* sv = reinterpret_cast<uint32_t*>(smem);
   uint16_t* cm = reinterpret_cast<uint16_t*>(smem + (size_t)G::E * 4);
-  uint32_t* fa = reinterpret_cast<uint32_t*>(smem + (size_t)G::E * 4 + (((size_t)G::E * 2 + 15) & ~(size_t)15));
-  uint32_t* fb = fa + G::NP / 32;
-  using RS = RerunSmem<T, ND>;
-  uint32_t* queue = fb + G::NP / 32;
+  uint32_t* fa0 = reinterpret_cast<uint32_t*>(smem + (size_t)G::E * 4 + (((size_t)G::E * 2 + 15) & ~(size_t)15));
+  uint32_t* queue = fa0 + 2 * (G::NP / 32);
   __shared__ uint32_t qn;
-  if (P->status & kErrNonfinite) return;
-  if (P->constant) return;
-  const int64_t tid = list ? (int64_t)list[blockIdx.x] : (int64_t)blockIdx.x;
-  const TileBox tb = tile_box(g, tid);
-  const int64_t plane = g.ny * g.nx;
-  long long t0 = clock64();
-  constexpr int NBOX = G::BZ * G::BY * G::BX;
-  constexpr int BATCH = 4;
-  for (int i0 = threadIdx.x; i0 < NBOX; i0 += BATCH * NT) {
-    uint32_t sb[BATCH], mb[BATCH];
+  // the first round (list == nullptr) visits every tile of the class
+  const int64_t count = list ? (int64_t)B->count[cls] : ntile_cls;
+  const uint32_t* lst = list ? list + B->off[cls] : nullptr;
+#pragma unroll 1
+  for (int64_t item = blockIdx.x; item < count; item += gridDim.x) {
+    const int64_t gt = lst ? (int64_t)lst[item] : tile0 + item;
+    const FieldInfo& fi = F[field_of_tile(F, f0, nf, gt)];
+    Params* P = fi.P;
+    if ((P->status & kErrNonfinite) || P->constant) continue;  // uniform per block
+    const Geometry g = fi.g;
+    uint32_t* __restrict__ s_glob = fi.s;
+    const uint16_t* __restrict__ cm_glob = fi.cm;
+    uint32_t* fa = fa0;
+    uint32_t* fb = fa0 + G::NP / 32;
+    const int64_t tid = gt - fi.tile_base;
+    if (tid < 0 || tid >= g.ntiles) continue;  // never for a consistent plan (uniform per block)
+    const TileBox tb = tile_box(g, tid);
+    const int64_t plane = g.ny * g.nx;
+    long long t0 = clock64();
+    constexpr int NBOX = G::BZ * G::BY * G::BX;
+    constexpr int BATCH = 4;
+    for (int i0 = threadIdx.x; i0 < NBOX; i0 += BATCH * NT) {
+      uint32_t sb[BATCH], mb[BATCH];
 #pragma unroll
-    for (int u = 0; u < BATCH; ++u) {  // issue every load of the batch first
-      const int i = i0 + u * NT;
-      const int lx = i % G::BX, ly = (i / G::BX) % G::BY, lz = i / (G::BX * G::BY);
-      const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1, gx = tb.x0 + lx - 1;
-      sb[u] = 0;
-      mb[u] = 0;
-      if (i < NBOX && gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx >= 0 && gx < g.nx) {
-        const int64_t gi = gz * plane + gy * g.nx + gx;
-        sb[u] = s_glob[gi];
-        mb[u] = __ldg(&cm_glob[gi]);
+      for (int u = 0; u < BATCH; ++u) {  // issue every load of the batch first
+        const int i = i0 + u * NT;
+        const int lx = i % G::BX, ly = (i / G::BX) % G::BY, lz = i / (G::BX * G::BY);
+        const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1, gx = tb.x0 + lx - 1;
+        sb[u] = 0;
+        mb[u] = 0;
+        if (i < NBOX && gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx >= 0 && gx < g.nx) {
+          const int64_t gi = gz * plane + gy * g.nx + gx;
+          sb[u] = s_glob[gi];
+          mb[u] = __ldg(&cm_glob[gi]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        const int i = i0 + u * NT;
+        if (i >= NBOX) break;
+        const int lx = i % G::BX, ly = (i / G::BX) % G::BY, lz = i / (G::BX * G::BY);
+        const int e = lz * G::PP + ly * G::BXP + lx;
+        sv[e] = sb[u];
+        cm[e] = (uint16_t)mb[u];
       }
     }
-#pragma unroll
-    for (int u = 0; u < BATCH; ++u) {
-      const int i = i0 + u * NT;
-      if (i >= NBOX) break;
-      const int lx = i % G::BX, ly = (i / G::BX) % G::BY, lz = i / (G::BX * G::BY);
-      const int e = lz * G::PP + ly * G::BXP + lx;
-      sv[e] = sb[u];
-      cm[e] = (uint16_t)mb[u];
-    }
-  }
-  for (int i = threadIdx.x; i < G::NP / 16; i += NT) fa[i] = 0;
-  if (threadIdx.x == 0) qn = 0;
-  __syncthreads();
-  const SegPos sp = seg_pos<G>();
-  const bool col_in = sp.lz < tb.cz && sp.lx < tb.cx;
-  // the first frontier: boundary points whose constraint from a lower same-bin
-  // neighbour outside the tile is violated by the current subbins (points outside
-  // a clipped tile are out of the domain: their masks were loaded as 0)
-  uint32_t first = 0;
-  if (col_in) {
+    for (int i = threadIdx.x; i < G::NP / 16; i += NT) fa[i] = 0;
+    if (threadIdx.x == 0) qn = 0;
+    __syncthreads();
+    const SegPos sp = seg_pos<G>();
+    const bool col_in = sp.lz < tb.cz && sp.lx < tb.cx;
+    // the first frontier: boundary points whose constraint from a lower same-bin
+    // neighbour outside the tile is violated by the current subbins (points outside
+    // a clipped tile are out of the domain: their masks were loaded as 0)
+    uint32_t first = 0;
+    if (col_in) {
 #pragma unroll 1
-    for (int j = 0; j < kSegment; ++j) {
-      const int e = sp.e0 + j * G::BXP;
-      const uint32_t mo = cm[e] & out_of_box_bits<G>(sp.lz, sp.ly0 + j, sp.lx);
-      if (!mo) continue;
-      const uint32_t sp_ = sv[e];
+      for (int j = 0; j < kSegment; ++j) {
+        const int e = sp.e0 + j * G::BXP;
+        const uint32_t mo = cm[e] & out_of_box_bits<G>(sp.lz, sp.ly0 + j, sp.lx);
+        if (!mo) continue;
+        const uint32_t sp_ = sv[e];
 #pragma unroll
-      for (int k = 0; k < 14; ++k) {
-        if ((mo >> k) & 1u) {
-          if (sv[e + G::off(dz_of(k), dy_of(k), dx_of(k))] + (k >= 7 ? 1u : 0u) > sp_) first |= 1u << j;
+        for (int k = 0; k < 14; ++k) {
+          if ((mo >> k) & 1u) {
+            if (sv[e + G::off(dz_of(k), dy_of(k), dx_of(k))] + (k >= 7 ? 1u : 0u) > sp_) first |= 1u << j;
+          }
         }
       }
     }
-  }
-  if (first) atomicOr(&fa[sp.b0 >> 5], first << (sp.b0 & 31));
-  if (!__syncthreads_or(first != 0)) return;  // every constraint into this tile holds
-  phase_mark(P, 5, t0);
-  bool over = false;
-  uint32_t risen = 0;
-  const int iters = frontier_fixpoint<G>(sv, cm, fa, fb, sp, 4 * G::NP + 64, over, risen);
-  if (threadIdx.x == 0) {
-    if (over) atomicOr(&P->status, kErrNotConverged);
-    atomicAdd(&P->fix_iters, (unsigned long long)iters);
-    atomicMax(&P->fix_iters_max, (unsigned long long)iters);
-  }
-  phase_mark(P, 6, t0);
-  // write the subbins that rose; queue the risen boundary points
-  const int64_t gz = tb.z0 + sp.lz, gx = tb.x0 + sp.lx;
-  if (col_in && risen) {
+    if (first) atomicOr(&fa[sp.b0 >> 5], first << (sp.b0 & 31));
+    if (!__syncthreads_or(first != 0)) continue;  // every constraint into this tile holds
+    phase_mark(P, 5, t0);
+    bool over = false;
+    uint32_t risen = 0;
+    const int iters = frontier_fixpoint<G>(sv, cm, fa, fb, sp, 4 * G::NP + 64, over, risen);
+    if (threadIdx.x == 0) {
+      if (over) atomicOr(&P->status, kErrNotConverged);
+      atomicAdd(&P->fix_iters, (unsigned long long)iters);
+      atomicMax(&P->fix_iters_max, (unsigned long long)iters);
+    }
+    phase_mark(P, 6, t0);
+    // write the subbins that rose; queue the risen boundary points
+    const int64_t gz = tb.z0 + sp.lz, gx = tb.x0 + sp.lx;
+    if (col_in && risen) {
 #pragma unroll 1
-    for (int j = 0; j < kSegment; ++j) {
-      if (!((risen >> j) & 1u)) continue;
-      const int ly = sp.ly0 + j;
-      s_glob[gz * plane + (tb.y0 + ly) * g.nx + gx] = sv[sp.e0 + j * G::BXP];
-      if (out_of_box_bits<G>(sp.lz, ly, sp.lx)) {
-        const uint32_t slot = atomicAdd(&qn, 1u);
-        if (slot < (uint32_t)RS::QMAX) queue[slot] = ((uint32_t)sp.lz << 20) | ((uint32_t)ly << 10) | (uint32_t)sp.lx;
+      for (int j = 0; j < kSegment; ++j) {
+        if (!((risen >> j) & 1u)) continue;
+        const int ly = sp.ly0 + j;
+        s_glob[gz * plane + (tb.y0 + ly) * g.nx + gx] = sv[sp.e0 + j * G::BXP];
+        if (out_of_box_bits<G>(sp.lz, ly, sp.lx)) {
+          const uint32_t slot = atomicAdd(&qn, 1u);
+          if (slot < (uint32_t)RS::QMAX) queue[slot] = ((uint32_t)sp.lz << 20) | ((uint32_t)ly << 10) | (uint32_t)sp.lx;
+        }
       }
     }
-  }
-  __syncthreads();
-  // mark, in parallel over the queue: tiles whose constraints from risen boundary
-  // points are now violated (the neighbour's mask says whether it is constrained)
-  const uint32_t nq = min(qn, (uint32_t)RS::QMAX);
-  for (uint32_t qi = threadIdx.x; qi < nq; qi += NT) {
-    const uint32_t v = queue[qi];
-    const int lz = (int)(v >> 20), ly = (int)((v >> 10) & 1023u), lx = (int)(v & 1023u);
-    const int e = G::entry(lz, ly, lx);
-    const uint32_t sf = sv[e];
-    const uint32_t ob = out_of_box_bits<G>(lz, ly, lx);
-    const int64_t pz = tb.z0 + lz, py = tb.y0 + ly, px = tb.x0 + lx;
+    __syncthreads();
+    // mark, in parallel over the queue: tiles whose constraints from risen boundary
+    // points are now violated (the neighbour's mask says whether it is constrained)
+    const uint32_t nq = min(qn, (uint32_t)RS::QMAX);
+    for (uint32_t qi = threadIdx.x; qi < nq; qi += NT) {
+      const uint32_t v = queue[qi];
+      const int lz = (int)(v >> 20), ly = (int)((v >> 10) & 1023u), lx = (int)(v & 1023u);
+      const int e = G::entry(lz, ly, lx);
+      const uint32_t sf = sv[e];
+      const uint32_t ob = out_of_box_bits<G>(lz, ly, lx);
+      const int64_t pz = tb.z0 + lz, py = tb.y0 + ly, px = tb.x0 + lx;
 #pragma unroll
-    for (int k = 0; k < 14; ++k) {
-      if (!((ob >> k) & 1u)) continue;
-      const int kop = k < 7 ? k + 7 : k - 7;
-      if (!((cm[e + G::off(dz_of(k), dy_of(k), dx_of(k))] >> kop) & 1u)) continue;
-      const int64_t qz = pz + dz_of(k), qy = py + dy_of(k), qx = px + dx_of(k);
-      if (*(volatile const uint32_t*)&s_glob[qz * plane + qy * g.nx + qx] >= sf + (k < 7 ? 1u : 0u)) continue;
-      dirty[((qz / g.tz) * g.nty + qy / g.ty) * g.ntx + qx / g.tx] = 1;
+      for (int k = 0; k < 14; ++k) {
+        if (!((ob >> k) & 1u)) continue;
+        const int kop = k < 7 ? k + 7 : k - 7;
+        if (!((cm[e + G::off(dz_of(k), dy_of(k), dx_of(k))] >> kop) & 1u)) continue;
+        const int64_t qz = pz + dz_of(k), qy = py + dy_of(k), qx = px + dx_of(k);
+        if (*(volatile const uint32_t*)&s_glob[qz * plane + qy * g.nx + qx] >= sf + (k < 7 ? 1u : 0u)) continue;
+        dirty[fi.tile_base + ((qz / g.tz) * g.nty + qy / g.ty) * g.ntx + qx / g.tx] = 1;
+      }
     }
+    __syncthreads();  // shared state is reused by the next item
   }
 }
 
-// Dirty flags -> list of tiles for the next round (flags are cleared).
-__global__ void k_compact(uint8_t* dirty, int64_t ntiles, uint32_t* list, Params* P) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
-    if (dirty[t]) {
+// Dirty flags -> the next round's list, in tile order (one block): per class the
+// count and first position, flags cleared.  Counts the round and tells the graph's
+// while-node whether to run another round; at the round cap the fields that still
+// have dirty tiles are reported as not converged.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_compact(uint8_t* __restrict__ dirty, int64_t total, uint32_t* __restrict__ list,
+                                                BatchState* B, const int64_t* __restrict__ cls_bounds /* 5 */,
+                                                const FieldInfo* __restrict__ F, int nf, int64_t round_cap,
+                                                cudaGraphConditionalHandle handle, int use_handle) {
+  __shared__ unsigned int tmp[NT / 32 + 1];
+  __shared__ unsigned int cnt[4];
+  if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const unsigned long long round = B->rounds + 1;
+  const bool cap_hit = (long long)round > round_cap;
+  unsigned int run = 0;
+  for (int64_t base = 0; base < total; base += NT) {
+    const int64_t t = base + threadIdx.x;
+    const unsigned int d = (t < total && dirty[t]) ? 1u : 0u;
+    unsigned int tot;
+    const unsigned int pos = block_exclusive_scan<NT, unsigned int>(d, tmp, &tot) + run;
+    if (d) {
       dirty[t] = 0;
-      const unsigned slot = atomicAdd(&P->dirty_count, 1u);
-      list[slot] = (uint32_t)t;
+      list[pos] = (uint32_t)t;
+      int c = 0;
+      while (c < 3 && t >= cls_bounds[c + 1]) ++c;
+      atomicAdd(&cnt[c], 1u);
+      if (cap_hit) atomicOr(&F[field_of_tile(F, 0, nf, t)].P->status, kErrNotConverged);
     }
+    run += tot;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int o = 0;
+    for (int c = 0; c < 4; ++c) {
+      B->count[c] = cap_hit ? 0u : cnt[c];
+      B->off[c] = o;
+      o += cnt[c];
+    }
+    B->rounds = round;
+    B->runs += cap_hit ? 0 : run;
+    B->cap_hit |= cap_hit && run;
+    if (use_handle) cudaGraphSetConditional(handle, (!cap_hit && run) ? 1u : 0u);
   }
 }
 
@@ -650,16 +721,21 @@ struct EncSmem {
 // Subbin record of each chunk (Sec. III-C, LC-generated pipeline): BIT_w, RZE_w,
 // RZE_1, prefixed by the u32 length of the RZE_w output; raw if not shorter.
 template <typename T, int ND>
-__global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_encode_sub(Geometry g, const Params* P,
-                                                                   const uint32_t* __restrict__ s_glob,
-                                                                   uint8_t* __restrict__ slots,
-                                                                   uint32_t* __restrict__ sizes) {
+__global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_encode_sub(const FieldInfo* __restrict__ F, int f0, int nf,
+                                                                   int64_t tile0) {
   using G = TileGeom<T, ND>;
   using ES = EncSmem<T, ND>;
   using W_t = typename Traits<T>::Bits;
   constexpr int NT = G::NT, W = Traits<T>::W;
+  const int64_t gt = tile0 + blockIdx.x;
+  const FieldInfo& fi = F[field_of_tile(F, f0, nf, gt)];
+  const Params* P = fi.P;
   if (P->status & kErrNonfinite) return;
   if (P->constant) return;
+  const Geometry g = fi.g;
+  const uint32_t* __restrict__ s_glob = fi.s;
+  uint8_t* __restrict__ slots = fi.slots;
+  uint32_t* __restrict__ sizes = fi.sizes;
   extern __shared__ __align__(16) unsigned char smem[];
   W_t* ws = reinterpret_cast<W_t*>(smem);
   uint8_t* stage = smem;
@@ -667,7 +743,8 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_encode_sub(Geometry g, c
   uint8_t* rzw = smem + 2 * ES::L;
   const RzeWork w = rze_work_at(rzw + ES::LR, ES::LR);
 
-  const int64_t tid = blockIdx.x;
+  const int64_t tid = gt - fi.tile_base;
+  if (tid < 0 || tid >= g.ntiles) return;  // never for a consistent plan
   const TileBox tb = tile_box(g, tid);
   const int n = tb.n, n32 = (n + 31) & ~31;
   const int64_t plane = g.ny * g.nx;
@@ -707,16 +784,21 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_encode_sub(Geometry g, c
 
 __device__ __forceinline__ uint64_t pad16(uint64_t v) { return (v + 15) & ~(uint64_t)15; }
 
-// Exclusive scan of padded record sizes (one block): record c starts at
-// base + sum of pad16(size) of records before it.
+// Exclusive scan of padded record sizes, one block per field: record c starts at
+// base + the sum of pad16(size) of the records before it.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_scan_sizes(const uint32_t* __restrict__ sizes, int64_t m, uint64_t base,
-                                                   uint64_t* __restrict__ offs, Params* P) {
+__global__ void __launch_bounds__(NT) k_scan_sizes(const FieldInfo* __restrict__ F) {
   __shared__ uint64_t tmp[NT / 32 + 1];
+  const FieldInfo& fi = F[blockIdx.x];
+  Params* P = fi.P;
   if (P->constant) {
     if (threadIdx.x == 0) P->total = kHeaderBytes;
     return;
   }
+  const int64_t m = 2 * fi.g.ntiles;
+  const uint64_t base = kHeaderBytes + pad16((uint64_t)m * 4);
+  const uint32_t* __restrict__ sizes = fi.sizes;
+  uint64_t* __restrict__ offs = fi.offs;
   const int64_t per = (m + NT - 1) / NT;
   const int64_t a = min(m, (int64_t)threadIdx.x * per), b = min(m, a + per);
   uint64_t c = 0;
@@ -730,13 +812,6 @@ __global__ void __launch_bounds__(NT) k_scan_sizes(const uint32_t* __restrict__ 
   if (threadIdx.x == 0) P->total = base + total;
 }
 
-struct HeaderInfo {
-  int32_t dtype, ndim, mode;
-  int64_t dims[3];
-  int32_t tile[3];
-  double eb;
-};
-
 __device__ __forceinline__ void put_u64(uint8_t* p, uint64_t v) {
   for (int k = 0; k < 8; ++k) p[k] = (uint8_t)(v >> (8 * k));
 }
@@ -744,14 +819,18 @@ __device__ __forceinline__ void put_u32(uint8_t* p, uint32_t v) {
   for (int k = 0; k < 4; ++k) p[k] = (uint8_t)(v >> (8 * k));
 }
 
-// Writes the header, the size table and the records at their offsets.
-__global__ void k_pack(HeaderInfo h, int64_t ntiles, const uint32_t* __restrict__ sizes,
-                       const uint64_t* __restrict__ offs, const uint8_t* __restrict__ slots, uint8_t* __restrict__ out,
-                       uint64_t cap, const Params* P) {
+// Writes each field's header, size table and records at their offsets
+// (blockIdx.y = field).
+__global__ void k_pack(const FieldInfo* __restrict__ F) {
+  const FieldInfo& fi = F[blockIdx.y];
+  const Params* P = fi.P;
   if (P->status & (kErrNonfinite | kErrRange | kErrNotConverged)) return;
   const uint64_t total = P->total;
-  if (total > cap) return;
+  if (total > fi.out_cap) return;
   const int constant = P->constant;
+  const HeaderInfo& h = fi.hdr;
+  uint8_t* __restrict__ out = fi.out;
+  const int64_t ntiles = fi.g.ntiles;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int k = 0; k < kHeaderBytes; ++k) out[k] = 0;
     put_u32(out + 0, kMagic);
@@ -772,6 +851,9 @@ __global__ void k_pack(HeaderInfo h, int64_t ntiles, const uint32_t* __restrict_
   }
   if (constant) return;
   const int64_t m = 2 * ntiles;
+  const uint32_t* __restrict__ sizes = fi.sizes;
+  const uint64_t* __restrict__ offs = fi.offs;
+  const uint8_t* __restrict__ slots = fi.slots;
   const uint64_t table_end = kHeaderBytes + pad16((uint64_t)m * 4);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)(table_end - kHeaderBytes) / 4;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -783,6 +865,26 @@ __global__ void k_pack(HeaderInfo h, int64_t ntiles, const uint32_t* __restrict_
     uint4* dst = reinterpret_cast<uint4*>(out + offs[c]);
     for (uint64_t j = threadIdx.x; j < n16; j += blockDim.x) dst[j] = src[j];
   }
+}
+
+__device__ __forceinline__ int status_code(unsigned int st) {
+  if (st & kErrNonfinite) return LOPC_ERR_NONFINITE;
+  if (st & kErrRange) return LOPC_ERR_RANGE;
+  if (st & kErrNotConverged) return LOPC_ERR_NOT_CONVERGED;
+  if (st & kErrCorrupt) return LOPC_ERR_CORRUPT;
+  if (st & kErrInternal) return LOPC_ERR_CUDA;
+  return LOPC_OK;
+}
+
+// Per-field results for the caller: stream length and status.
+__global__ void k_finalize(const FieldInfo* __restrict__ F, int nf) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const FieldInfo& fi = F[f];
+  int st = status_code(fi.P->status);
+  if (st == LOPC_OK && fi.P->total > fi.out_cap) st = LOPC_ERR_CAPACITY;
+  if (fi.status_out) *fi.status_out = st;
+  if (fi.size_out) *fi.size_out = st == LOPC_OK ? fi.P->total : 0ULL;
 }
 
 // Exports subbins (for stage-by-stage tests).

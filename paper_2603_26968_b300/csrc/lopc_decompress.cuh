@@ -7,20 +7,73 @@
 
 namespace lopc {
 
-struct DecodeInfo {
-  double eps_q;  // quantizer width (only used for the first guess of a bin's lowest value)
+// One stream of a decompression launch (a single stream is a batch of one).
+struct DecField {
+  Geometry g;
+  const uint8_t* in;
+  uint64_t in_size;
+  void* x;                // output field
+  uint64_t* offs;         // 2 x ntiles record offsets (workspace)
+  unsigned int* status;   // kErr* bits (workspace)
+  int* status_out;        // device: this stream's LOPC status (may be null)
+  double eps_q;           // filled on the device from the header
   unsigned long long inv_m;
   int inv_e;
+  int constant;
+  unsigned long long const_bits;
+  int64_t tile_base;
 };
 
-// Offsets of the records; flags a table that does not add up to the stream length.
+// Reads each stream's header on the device: the decoder's parameters, and a check
+// that the header matches the descriptor the launch was planned for.
+__global__ void k_dec_setup(DecField* F, int nf) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  DecField& d = F[f];
+  *d.status = 0;
+  const uint8_t* h = d.in;
+  auto rd = [&](int o, int nb) {
+    uint64_t v = 0;
+    for (int k = 0; k < nb; ++k) v |= (uint64_t)h[o + k] << (8 * k);
+    return v;
+  };
+  bool ok = d.in_size >= (uint64_t)kHeaderBytes && rd(0, 4) == kMagic && rd(4, 2) == LOPC_VERSION &&
+            h[6] == (uint8_t)d.g.dtype && h[7] == (uint8_t)d.g.ndim;
+  const uint64_t total = ok ? rd(88, 8) : 0;
+  ok = ok && total <= d.in_size && total >= (uint64_t)kHeaderBytes;
+  d.constant = ok ? h[33] : 0;
+  const uint64_t iu = ok ? rd(64, 8) : 0;
+  const double inv = __longlong_as_double((long long)iu);
+  if (ok && !d.constant) ok = inv > 0.0 && inv <= 1.79e308 && rd(80, 8) == (uint64_t)d.g.ntiles;
+  if (ok && d.constant) ok = rd(80, 8) == 0 && total == (uint64_t)kHeaderBytes;
+  if (!ok) {
+    *d.status = kErrCorrupt;
+    return;
+  }
+  d.const_bits = rd(72, 8);
+  const int ex = (int)((iu >> 52) & 0x7ff);
+  d.inv_m = (iu & 0xfffffffffffffULL) | (ex ? 0x10000000000000ULL : 0ULL);
+  d.inv_e = ex ? ex - 1075 : -1074;
+  d.eps_q = d.constant ? 0.0 : __ddiv_rn(1.0, inv);  // only seeds the search for a bin's lowest value
+}
+
+// Offsets of the records, one block per stream; flags a table that does not add up
+// to the stream length.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_dec_offsets(const uint8_t* __restrict__ in, uint64_t total, int64_t ntiles,
-                                                     uint64_t* __restrict__ offs, unsigned int* status) {
+__global__ void __launch_bounds__(NT) k_dec_offsets(const DecField* __restrict__ F) {
   __shared__ uint64_t tmp[NT / 32 + 1];
-  const int64_t m = 2 * ntiles;
-  const uint32_t* tab = reinterpret_cast<const uint32_t*>(in + kHeaderBytes);
+  const DecField& d = F[blockIdx.x];
+  if (*d.status || d.constant) return;
+  const int64_t m = 2 * d.g.ntiles;
+  const uint64_t total = (uint64_t)d.in[88] | ((uint64_t)d.in[89] << 8) | ((uint64_t)d.in[90] << 16) |
+                         ((uint64_t)d.in[91] << 24) | ((uint64_t)d.in[92] << 32) | ((uint64_t)d.in[93] << 40) |
+                         ((uint64_t)d.in[94] << 48) | ((uint64_t)d.in[95] << 56);
   const uint64_t base = kHeaderBytes + pad16((uint64_t)m * 4);
+  if (base > total) {
+    if (threadIdx.x == 0) atomicOr(d.status, kErrCorrupt);
+    return;
+  }
+  const uint32_t* tab = reinterpret_cast<const uint32_t*>(d.in + kHeaderBytes);
   const int64_t per = (m + NT - 1) / NT;
   const int64_t a = min(m, (int64_t)threadIdx.x * per), b = min(m, a + per);
   uint64_t c = 0;
@@ -28,10 +81,16 @@ __global__ void __launch_bounds__(NT) k_dec_offsets(const uint8_t* __restrict__ 
   uint64_t sum;
   uint64_t run = block_exclusive_scan<NT, uint64_t>(c, tmp, &sum) + base;
   for (int64_t i = a; i < b; ++i) {
-    offs[i] = run;
+    d.offs[i] = run;
     run += pad16(tab[i] & ~kRawFlag);
   }
-  if (threadIdx.x == 0 && base + sum != total) atomicOr(status, kErrCorrupt);
+  if (threadIdx.x == 0 && base + sum != total) atomicOr(d.status, kErrCorrupt);
+}
+
+__global__ void k_dec_finalize(const DecField* __restrict__ F, int nf) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  if (F[f].status_out) *F[f].status_out = *F[f].status ? LOPC_ERR_CORRUPT : LOPC_OK;
 }
 
 template <typename T, int ND>
@@ -51,9 +110,8 @@ struct DecSmem {
 // subbins (RZE_1, RZE_w, BIT_w inverses) and x_hat = the subbin-th value above the
 // bin's lowest value (Sec. III-E), written as the subbin words come out.
 template <typename T, int ND>
-__global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_decode(const uint8_t* __restrict__ in, Geometry g,
-                                                               DecodeInfo di, const uint64_t* __restrict__ offs,
-                                                               T* __restrict__ xhat, unsigned int* status) {
+__global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_decode(const DecField* __restrict__ F, int f0, int nf,
+                                                               int64_t tile0) {
   using G = TileGeom<T, ND>;
   using DS = DecSmem<T, ND>;
   using W_t = typename Traits<T>::Bits;
@@ -70,10 +128,39 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_decode(const uint8_t* __
   const RzeWork w = rze_work_at(reinterpret_cast<uint8_t*>(wb + DS::NP), DS::LR);
   __shared__ int bad;
   __shared__ B red_min[NT / 32], red_max[NT / 32];
+  const int64_t gt = tile0 + blockIdx.x;
+  int lo_f = f0, hi_f = f0 + nf - 1;
+  while (lo_f < hi_f) {
+    const int mid = (lo_f + hi_f + 1) >> 1;
+    if (F[mid].tile_base <= gt)
+      lo_f = mid;
+    else
+      hi_f = mid - 1;
+  }
+  const DecField& df = F[lo_f];
+  unsigned int* status = df.status;
   if (*status & kErrCorrupt) return;
-
-  const int64_t tid = blockIdx.x;
+  const Geometry g = df.g;
+  const uint8_t* __restrict__ in = df.in;
+  const uint64_t* __restrict__ offs = df.offs;
+  T* __restrict__ xhat = reinterpret_cast<T*>(df.x);
+  const int64_t tid = gt - df.tile_base;
+  if (tid < 0 || tid >= g.ntiles) return;  // never for a consistent plan
   const TileBox tb = tile_box(g, tid);
+  if (df.constant) {  // a constant field: every point is the stored value
+    const T v = Traits<T>::from_bits((typename Traits<T>::Bits)df.const_bits);
+    const int64_t plane = g.ny * g.nx;
+    for (int i = threadIdx.x; i < tb.n; i += NT) {
+      const int lx = i % tb.cx, ly = (i / tb.cx) % tb.cy, lz = i / (tb.cx * tb.cy);
+      xhat[(tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx] = v;
+    }
+    return;
+  }
+  struct {
+    double eps_q;
+    unsigned long long inv_m;
+    int inv_e;
+  } di = {df.eps_q, df.inv_m, df.inv_e};
   const int n = tb.n, n32 = (n + 31) & ~31;
   const uint32_t raw = (uint32_t)n * W;
   const bool full = n == G::NP;
@@ -219,13 +306,6 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_decode(const uint8_t* __
     }
   }
   if ((__syncthreads_or(fail) || bad) && threadIdx.x == 0) atomicOr(status, kErrCorrupt);
-}
-
-template <typename T>
-__global__ void k_fill(T* __restrict__ x, int64_t n, unsigned long long bits) {
-  const T v = Traits<T>::from_bits((typename Traits<T>::Bits)bits);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] = v;
 }
 
 }  // namespace lopc

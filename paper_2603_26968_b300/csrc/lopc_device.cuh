@@ -343,6 +343,58 @@ struct Geometry {
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+struct HeaderInfo {
+  int32_t dtype, ndim, mode;
+  int64_t dims[3];
+  int32_t tile[3];
+  double eb;
+};
+
+// One field of a launch.  Every kernel serves a table of fields whose tiles share
+// one global index space (a single field is a batch of one); a field's tiles are
+// [tile_base, tile_base + g.ntiles).
+struct FieldInfo {
+  Geometry g;
+  HeaderInfo hdr;
+  const void* x;          // input values
+  uint8_t* out;           // stream
+  uint64_t out_cap;
+  Params* P;              // per-field state (in the workspace)
+  uint32_t* s;            // subbins, one per point
+  uint16_t* cm;           // lower-neighbour masks, one per point
+  uint8_t* slots;         // 2 x ntiles record slots of 16 KiB
+  uint32_t* sizes;        // 2 x ntiles record sizes
+  uint64_t* offs;         // 2 x ntiles record offsets
+  int64_t* bins_out;      // optional export of the bins (may be null)
+  uint64_t* size_out;     // device: this field's stream length (may be null)
+  int* status_out;        // device: this field's LOPC status (may be null)
+  int64_t tile_base;
+  int64_t round_cap;
+};
+
+// State shared by all fields of a launch.
+struct BatchState {
+  unsigned int count[4];      // tiles to rerun per class this round
+  unsigned int off[4];        // their first position in the list
+  unsigned long long rounds;  // repair rounds done
+  unsigned long long runs;    // tile runs launched (first round included)
+  unsigned int cap_hit;
+  unsigned int pad;
+};
+
+// Field of global tile gt among fields F[f0 .. f0+nf), sorted by tile_base.
+__device__ __forceinline__ int field_of_tile(const FieldInfo* F, int f0, int nf, int64_t gt) {
+  int lo = f0, hi = f0 + nf - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (F[mid].tile_base <= gt)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
 // The chunk of a tile: its origin and clipped extent.
 struct TileBox {
   int64_t z0, y0, x0;

@@ -64,6 +64,12 @@ def lib():
         L.lopc_decompress.argtypes = [P, C.c_size_t, P, C.c_size_t, P, C.c_size_t, P]
         L.lopc_decompress_noalloc.argtypes = [P, C.c_size_t, P, C.c_size_t, P]
         L.lopc_noalloc_max_chunks.restype = C.c_int64
+        L.lopc_batch_compress_workspace_size.argtypes = [C.c_int, D]
+        L.lopc_batch_compress_workspace_size.restype = C.c_size_t
+        L.lopc_batch_compress.argtypes = [C.c_int, D, P, P, P, P, P, P, C.c_size_t, P]
+        L.lopc_batch_decompress_workspace_size.argtypes = [C.c_int, D]
+        L.lopc_batch_decompress_workspace_size.restype = C.c_size_t
+        L.lopc_batch_decompress.argtypes = [C.c_int, D, P, P, P, P, P, C.c_size_t, P]
         L.lopc_quantize_repair.argtypes = [D, P, P, P, P, C.c_size_t, P]
         L.lopc_set_round_cap.argtypes = [C.c_int64]
         L.lopc_set_round_cap.restype = C.c_int64
@@ -254,3 +260,80 @@ def profile_read() -> dict:
     ms = (C.c_double * cap)()
     n = lib().lopc_profile_read(names, launches, ms, cap)
     return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(n, cap))}
+
+
+# ------------------------------------------------------------------------ batches
+
+def _descs(items):
+    arr = (FieldDesc * len(items))()
+    for i, d in enumerate(items):
+        arr[i] = d
+    return arr
+
+
+def batch_compress_workspace_size(descs) -> int:
+    return int(lib().lopc_batch_compress_workspace_size(len(descs), _descs(descs)))
+
+
+def batch_decompress_workspace_size(descs) -> int:
+    return int(lib().lopc_batch_decompress_workspace_size(len(descs), _descs(descs)))
+
+
+class BatchCompress:
+    """A reusable batched compression of fixed fields (inputs, outputs, workspace
+    and result arrays stay allocated, so repeated launches replay one cached graph)."""
+
+    def __init__(self, fields, ebs, modes=None, device=None):
+        self.fields = [f.contiguous() for f in fields]
+        n = len(self.fields)
+        modes = modes if modes is not None else [NOA] * n
+        self.descs = [make_desc(tuple(f.shape), f.dtype, m, e) for f, m, e in zip(self.fields, modes, ebs)]
+        dev = self.fields[0].device if device is None else device
+        self.caps = [compress_bound(d) for d in self.descs]
+        self.outs = [torch.empty(c, dtype=torch.uint8, device=dev) for c in self.caps]
+        self.ws = torch.empty(batch_compress_workspace_size(self.descs), dtype=torch.uint8, device=dev)
+        self.sizes = torch.zeros(n, dtype=torch.int64, device=dev)
+        self.status = torch.zeros(n, dtype=torch.int32, device=dev)
+        self._d = _descs(self.descs)
+        self._x = (C.c_void_p * n)(*[f.data_ptr() for f in self.fields])
+        self._o = (C.c_void_p * n)(*[o.data_ptr() for o in self.outs])
+        self._c = (C.c_size_t * n)(*self.caps)
+
+    def launch(self, stream=None) -> None:
+        """Enqueues the batch on the stream (asynchronous)."""
+        rc = lib().lopc_batch_compress(len(self.fields), self._d, self._x, self._o, self._c,
+                                       C.c_void_p(self.sizes.data_ptr()), C.c_void_p(self.status.data_ptr()),
+                                       C.c_void_p(self.ws.data_ptr()), self.ws.numel(), C.c_void_p(_stream(stream)))
+        _check(rc, "lopc_batch_compress")
+
+    def results(self):
+        """(list of stream tensors, list of status codes) after the launch finished."""
+        sizes = self.sizes.cpu().tolist()
+        st = self.status.cpu().tolist()
+        return [o[:n] for o, n in zip(self.outs, sizes)], st
+
+
+def batch_compress(fields, ebs, modes=None, stream=None):
+    b = BatchCompress(fields, ebs, modes)
+    b.launch(stream)
+    torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    return b.results()
+
+
+def batch_decompress(streams, outs=None, stream=None):
+    """Decompresses a list of uint8 CUDA stream tensors; returns (fields, statuses)."""
+    descs = [peek(s) for s in streams]
+    n = len(streams)
+    dev = streams[0].device
+    if outs is None:
+        outs = [torch.empty(d.shape, dtype=d.torch_dtype, device=dev) for d in descs]
+    ws = torch.empty(batch_decompress_workspace_size(descs), dtype=torch.uint8, device=dev)
+    status = torch.zeros(n, dtype=torch.int32, device=dev)
+    ins = (C.c_void_p * n)(*[s.data_ptr() for s in streams])
+    sizes = (C.c_size_t * n)(*[s.numel() for s in streams])
+    xs = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    rc = lib().lopc_batch_decompress(n, _descs(descs), ins, sizes, xs, C.c_void_p(status.data_ptr()),
+                                     C.c_void_p(ws.data_ptr()), ws.numel(), C.c_void_p(_stream(stream)))
+    _check(rc, "lopc_batch_decompress")
+    torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    return outs, status.cpu().tolist()
