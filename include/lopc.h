@@ -57,6 +57,7 @@ extern "C" {
 #define LOPC_ERR_NOT_CONVERGED (-6) /* repair round cap reached (only with a lowered cap) */
 #define LOPC_ERR_CUDA (-7)          /* a CUDA runtime call failed */
 #define LOPC_ERR_WORKSPACE (-8)     /* workspace missing or smaller than required */
+#define LOPC_ERR_BUSY (-9)          /* serving engine full: no result slot or rerun-list room */
 
 /* Element type and error-bound mode (Sec. III-A). */
 #define LOPC_F32 0
@@ -184,6 +185,58 @@ LOPC_API int lopc_last_phase_cycles(int64_t* cycles, int n);
 LOPC_API void lopc_profile_enable(int on);
 LOPC_API void lopc_profile_reset(void);
 LOPC_API int lopc_profile_read(const char** names, int64_t* launches, double* total_ms, int cap);
+
+/* ---- serving engine (round-level continuous batching; the paper compresses one
+ * field per call and has no counterpart).  Fields are submitted as they arrive and
+ * join the repair between rounds: each lopc_engine_step runs `rounds` repair rounds
+ * (compaction of the dirty tiles, then their reruns) over every field in repair on
+ * the engine's rounds stream, while on its aux stream it runs the tile pass and the
+ * first round of the fields submitted since the last step, and encodes and packs
+ * the fields whose last compaction found no dirty tile.  A field's state stays in
+ * its own workspace from submit to completion; its stream is byte-identical to
+ * lopc_compress's.  One host thread drives an engine.
+ *
+ * Create: max_fields result slots and room for max_tiles tiles of fields in repair
+ * (chunk tiles: 4096 float32 or 2048 float64 points each); allocates its tables and
+ * two streams once.  Errors: INVALID_ARG, CUDA. */
+typedef struct lopc_engine lopc_engine;
+LOPC_API int lopc_engine_create(int max_fields, int64_t max_tiles, lopc_engine** out);
+
+/* Waits for the engine's streams and frees it; fields still in flight are dropped. */
+LOPC_API void lopc_engine_destroy(lopc_engine* e);
+
+/* Device bytes of the per-field state that lopc_engine_submit needs (0 if invalid). */
+LOPC_API size_t lopc_engine_field_workspace_size(const lopc_field_desc* desc);
+
+/* Queues one field.  d_x, d_out (out_cap bytes) and d_ws (ws_size bytes, 256-byte
+ * aligned) are device memory owned by the caller and must stay valid until
+ * lopc_engine_poll reports `tag`.  The engine's work on the field waits for
+ * everything enqueued so far on ready_stream (the stream that produced d_x).
+ * Errors: INVALID_ARG, WORKSPACE, BUSY (no slot or list room: retry after a poll),
+ * CUDA. */
+LOPC_API int lopc_engine_submit(lopc_engine* e, const lopc_field_desc* desc, const void* d_x, void* d_out,
+                                size_t out_cap, void* d_ws, size_t ws_size, uint64_t tag, void* ready_stream);
+
+/* One engine step (see above).  Blocks only until the step's last compaction has
+ * been read back; its rerun round is still running when it returns.  *active
+ * (may be NULL) receives the number of fields submitted and not yet polled.
+ * Errors: INVALID_ARG, CUDA. */
+LOPC_API int lopc_engine_step(lopc_engine* e, int rounds, int* active);
+
+/* Non-blocking: copies up to cap finished fields (tag, stream length, status: OK,
+ * NONFINITE, RANGE, CAPACITY, NOT_CONVERGED) and returns how many; their buffers
+ * are the caller's again.  Returns a negative status on error. */
+LOPC_API int lopc_engine_poll(lopc_engine* e, uint64_t* tags, uint64_t* sizes, int* statuses, int cap);
+
+/* Waits until all work enqueued by the engine has finished on the GPU. */
+LOPC_API int lopc_engine_sync(lopc_engine* e);
+
+/* ---- launch tuning.  Persistent rerun blocks per SM for each field class (0 f32
+ * 2D, 1 f32 3D, 2 f64 2D, 3 f64 3D), used by later calls on this thread; values are
+ * clamped to [1, 16].  Output bytes never depend on them.  lopc_tune_get copies
+ * the current four values. */
+LOPC_API void lopc_tune_set(const int* rerun_blocks_per_sm);
+LOPC_API void lopc_tune_get(int* rerun_blocks_per_sm);
 
 /* Human-readable text of a status code (static storage). */
 LOPC_API const char* lopc_strerror(int status);

@@ -6,6 +6,7 @@
 
 #include <mutex>
 #include <algorithm>
+#include <deque>
 #include <vector>
 
 #include "lopc.h"
@@ -162,12 +163,50 @@ HeaderInfo header_info(const lopc_field_desc* d, const Geometry& g) {
   return h;
 }
 
-// ------------------------------------------------------------ compress plan
+// ------------------------------------------------------------ launch tables
 
-// Workspace of a compression launch: shared state, the field table and the
-// concatenated dirty flags and rerun list, then one part per field.
+// A table of fields for one set of launches: sorted by class, every field's tiles
+// and dirty-bitmap words numbered consecutively.  A single field is a table of
+// one; a batch, a serving round and a set of fields being finished are others.
+struct Table {
+  std::vector<FieldInfo> F;
+  int cls_f0[4] = {0, 0, 0, 0}, cls_nf[4] = {0, 0, 0, 0};
+  int64_t cls_t0[4] = {0, 0, 0, 0}, cls_nt[4] = {0, 0, 0, 0};
+  int64_t total_tiles = 0, total_words = 0, max_words = 0;
+  int n() const { return (int)F.size(); }
+};
+
+// Numbers the tiles and dirty words of t.F, which is already sorted by class.
+void layout_table(Table& t) {
+  for (int c = 0; c < 4; ++c) {
+    t.cls_f0[c] = t.cls_nf[c] = 0;
+    t.cls_t0[c] = t.cls_nt[c] = 0;
+  }
+  int64_t tiles = 0, words = 0, maxw = 0;
+  for (int k = 0; k < t.n(); ++k) {
+    FieldInfo& f = t.F[k];
+    const int c = class_of_geometry(f.g);
+    if (t.cls_nf[c] == 0) {
+      t.cls_f0[c] = k;
+      t.cls_t0[c] = tiles;
+    }
+    ++t.cls_nf[c];
+    t.cls_nt[c] += f.g.ntiles;
+    f.tile_base = tiles;
+    tiles += f.g.ntiles;
+    f.word_base = words;
+    words += dirty_words(f.g.ntiles);
+    maxw = std::max<int64_t>(maxw, dirty_words(f.g.ntiles));
+  }
+  t.total_tiles = tiles;
+  t.total_words = words;
+  t.max_words = maxw;
+}
+
+// Per-field part of a compression workspace: state, subbins, lower masks, record
+// sizes and offsets, the dirty bitmap and the record slots.
 struct FieldPart {
-  size_t params, s, cm, sizes, offs, slots, total;
+  size_t params, s, cm, sizes, offs, dirty, slots, total;
 };
 
 FieldPart field_part(const Geometry& g) {
@@ -184,108 +223,47 @@ FieldPart field_part(const Geometry& g) {
   o = align256(o + 8 * (size_t)g.ntiles);
   L.offs = o;
   o = align256(o + 16 * (size_t)g.ntiles);
+  L.dirty = o;
+  o = align256(o + 4 * (size_t)dirty_words(g.ntiles));
   L.slots = o;
   o = align256(o + 2 * (size_t)g.ntiles * kSlotBytes);
   L.total = o;
   return L;
 }
 
-struct CompressPlan {
-  int n = 0;
-  std::vector<int> order;      // position in the launch -> caller's index
-  std::vector<FieldInfo> F;    // sorted by class, then caller's order
-  int cls_f0[4] = {0, 0, 0, 0}, cls_nf[4] = {0, 0, 0, 0};
-  int64_t cls_t0[4] = {0, 0, 0, 0}, cls_nt[4] = {0, 0, 0, 0};
-  int64_t bounds[5] = {0, 0, 0, 0, 0};
-  int64_t total_tiles = 0;
-  int64_t round_cap = 0;
-  size_t off_state = 0, off_table = 0, off_bounds = 0, off_dirty = 0, off_list = 0, off_results = 0;
-  std::vector<size_t> off_field;
-  size_t ws_total = 0;
-};
-
-// Lays out a launch over descs[0..n) (sorted by class); fills pointers when ws != null.
-int plan_compress(int n, const lopc_field_desc* descs, const void* const* xs, void* const* outs, const size_t* caps,
-                  uint64_t* d_sizes, int* d_status, int64_t* bins_out, uint8_t* ws, CompressPlan& p) {
-  p = CompressPlan{};  // planning twice (size, then pointers) must not accumulate
-  p.n = n;
-  p.order.resize(n);
-  for (int i = 0; i < n; ++i) p.order[i] = i;
-  std::stable_sort(p.order.begin(), p.order.end(), [&](int a, int b) {
-    return class_of(descs[a].dtype, descs[a].ndim) < class_of(descs[b].dtype, descs[b].ndim);
-  });
-  p.F.assign(n, FieldInfo{});
-  int64_t tiles = 0, cap = 16;
-  for (int c = 0; c < 4; ++c) {
-    p.cls_f0[c] = 0;
-    p.cls_nf[c] = 0;
-  }
-  for (int k = 0; k < n; ++k) {
-    const lopc_field_desc* d = &descs[p.order[k]];
-    const int c = class_of(d->dtype, d->ndim);
-    if (p.cls_nf[c] == 0) {
-      p.cls_f0[c] = k;
-      p.cls_t0[c] = tiles;
-    }
-    ++p.cls_nf[c];
-    FieldInfo& f = p.F[k];
-    f.g = geometry_of(d);
-    f.hdr = header_info(d, f.g);
-    f.tile_base = tiles;
-    tiles += f.g.ntiles;
-    p.cls_nt[c] += f.g.ntiles;
-    const int64_t npts = f.g.nz * f.g.ny * f.g.nx;
-    cap = std::max<int64_t>(cap, npts + 16);  // a chain has fewer than n links
-  }
-  for (int c = 0; c < 4; ++c)
-    if (p.cls_nf[c] == 0) p.cls_t0[c] = c ? p.cls_t0[c - 1] + p.cls_nt[c - 1] : 0;
-  for (int c = 0; c < 4; ++c) p.bounds[c] = p.cls_t0[c];
-  p.bounds[4] = tiles;
-  // classes may be empty: keep the bounds monotone
-  for (int c = 1; c < 5; ++c) p.bounds[c] = std::max(p.bounds[c], p.bounds[c - 1]);
-  p.total_tiles = tiles;
-  p.round_cap = g_round_cap > 0 ? g_round_cap : cap;
-  size_t o = 0;
-  p.off_state = o;
-  o = align256(o + sizeof(BatchState));
-  p.off_table = o;
-  o = align256(o + (size_t)n * sizeof(FieldInfo));
-  p.off_bounds = o;
-  o = align256(o + 5 * sizeof(int64_t));
-  p.off_results = o;
-  o = align256(o + 16);
-  p.off_dirty = o;
-  o = align256(o + (size_t)tiles);
-  p.off_list = o;
-  o = align256(o + 4 * (size_t)tiles);
-  p.off_field.resize(n);
-  for (int k = 0; k < n; ++k) {
-    p.off_field[k] = o;
-    o += field_part(p.F[k].g).total;
-  }
-  p.ws_total = o;
-  if (!ws) return LOPC_OK;
-  for (int k = 0; k < n; ++k) {
-    const int i = p.order[k];
-    FieldInfo& f = p.F[k];
-    const FieldPart L = field_part(f.g);
-    uint8_t* base = ws + p.off_field[k];
-    f.x = xs ? xs[i] : nullptr;
-    f.out = outs ? reinterpret_cast<uint8_t*>(outs[i]) : nullptr;
-    f.out_cap = caps ? (uint64_t)caps[i] : 0;
-    f.P = reinterpret_cast<Params*>(base + L.params);
-    f.s = reinterpret_cast<uint32_t*>(base + L.s);
-    f.cm = reinterpret_cast<uint16_t*>(base + L.cm);
-    f.sizes = reinterpret_cast<uint32_t*>(base + L.sizes);
-    f.offs = reinterpret_cast<uint64_t*>(base + L.offs);
-    f.slots = base + L.slots;
-    f.bins_out = bins_out;
-    f.size_out = d_sizes ? d_sizes + i : nullptr;
-    f.status_out = d_status ? d_status + i : nullptr;
-    f.round_cap = p.round_cap;
-  }
-  return LOPC_OK;
+// The default round cap of a field: a chain of constraints has fewer links than
+// the field has points, so reaching it means a fault, not a slow field.
+int64_t default_round_cap(const Geometry& g) {
+  if (g_round_cap > 0) return g_round_cap;
+  return std::max<int64_t>(16, g.nz * g.ny * g.nx + 16);
 }
+
+// A table entry for one field whose state lives at `base` (a FieldPart layout).
+FieldInfo field_entry(const lopc_field_desc* d, const void* x, void* out, size_t cap, uint64_t* size_out,
+                      int* status_out, int64_t* bins_out, uint8_t* base) {
+  FieldInfo f{};
+  f.g = geometry_of(d);
+  f.hdr = header_info(d, f.g);
+  f.round_cap = default_round_cap(f.g);
+  if (!base) return f;
+  const FieldPart L = field_part(f.g);
+  f.x = x;
+  f.out = reinterpret_cast<uint8_t*>(out);
+  f.out_cap = (uint64_t)cap;
+  f.P = reinterpret_cast<Params*>(base + L.params);
+  f.s = reinterpret_cast<uint32_t*>(base + L.s);
+  f.cm = reinterpret_cast<uint16_t*>(base + L.cm);
+  f.sizes = reinterpret_cast<uint32_t*>(base + L.sizes);
+  f.offs = reinterpret_cast<uint64_t*>(base + L.offs);
+  f.dirty = reinterpret_cast<uint32_t*>(base + L.dirty);
+  f.slots = base + L.slots;
+  f.bins_out = bins_out;
+  f.size_out = size_out;
+  f.status_out = status_out;
+  return f;
+}
+
+// ------------------------------------------------------------ launch sequences
 
 // Library-owned stream for capturing the body of the repair loop.
 cudaStream_t side_stream() {
@@ -306,61 +284,165 @@ int set_smem_attrs() {
   return LOPC_OK;
 }
 
-int rerun_blocks() {
+int sm_count() {
   thread_local int v = 0;
   if (!v) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    v = sms * 3;
+    v = sms;
   }
   return v;
 }
 
+// Persistent rerun blocks per SM, per class (set by lopc_tune_set).
+thread_local int g_rerun_per_sm[4] = {3, 3, 6, 6};
+
+int rerun_blocks(int c) { return sm_count() * g_rerun_per_sm[c]; }
+
+int launch_init(const Table& t, const FieldInfo* dF, cudaStream_t st) {
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (t.max_words + 255) / 256));
+  LAUNCH("init_params", st, k_init_params<<<dim3(gx, (unsigned)t.n()), 256, 0, st>>>(dF, t.n()));
+  CK(cudaGetLastError());
+  return LOPC_OK;
+}
+
 template <typename T, int ND>
-int launch_class_pre(const CompressPlan& p, int c, const FieldInfo* dF, cudaStream_t st) {
+int launch_class_pre(const Table& t, int c, const FieldInfo* dF, cudaStream_t st) {
   using C = TileCfg<T, ND>;
-  if (!p.cls_nf[c]) return LOPC_OK;
+  if (!t.cls_nf[c]) return LOPC_OK;
   int rc = set_smem_attrs<T, ND>();
   if (rc) return rc;
-  LAUNCH("range", st, k_range<T><<<dim3(148 * 4, p.cls_nf[c]), 256, 0, st>>>(dF, p.cls_f0[c]));
-  LAUNCH("resolve_eps", st, k_resolve_eps<T><<<(p.cls_nf[c] + 63) / 64, 64, 0, st>>>(dF, p.cls_f0[c], p.cls_nf[c]));
+  LAUNCH("range", st, k_range<T><<<dim3(sm_count() * 4, t.cls_nf[c]), 256, 0, st>>>(dF, t.cls_f0[c]));
+  LAUNCH("resolve_eps", st, k_resolve_eps<T><<<(t.cls_nf[c] + 63) / 64, 64, 0, st>>>(dF, t.cls_f0[c], t.cls_nf[c]));
   LAUNCH("tile_pass", st,
-         k_pass<T, ND><<<(unsigned)p.cls_nt[c], C::NT, PassSmem<T, ND>::bytes(), st>>>(dF, p.cls_f0[c], p.cls_nf[c],
-                                                                                      p.cls_t0[c]));
+         k_pass<T, ND><<<(unsigned)t.cls_nt[c], C::NT, PassSmem<T, ND>::bytes(), st>>>(dF, t.cls_f0[c], t.cls_nf[c],
+                                                                                      t.cls_t0[c]));
   CK(cudaGetLastError());
   return LOPC_OK;
 }
 
 template <typename T, int ND>
-int launch_class_rerun(const CompressPlan& p, int c, const FieldInfo* dF, const BatchState* dB, const uint32_t* list,
-                       uint8_t* dirty, cudaStream_t st) {
+int launch_class_rerun(const Table& t, int c, const FieldInfo* dF, const BatchState* dB, const uint32_t* list,
+                       cudaStream_t st) {
   using C = TileCfg<T, ND>;
-  if (!p.cls_nf[c]) return LOPC_OK;
-  const unsigned grid = (unsigned)imin64(p.cls_nt[c], rerun_blocks());
+  if (!t.cls_nf[c]) return LOPC_OK;
+  const unsigned grid = (unsigned)imin64(t.cls_nt[c], rerun_blocks(c));
   LAUNCH("tile_rerun", st,
-         k_rerun<T, ND><<<grid, C::NT, RerunSmem<T, ND>::bytes(), st>>>(dF, p.cls_f0[c], p.cls_nf[c], p.cls_t0[c],
-                                                                       p.cls_nt[c], c, dB, list, dirty));
+         k_rerun<T, ND><<<grid, C::NT, RerunSmem<T, ND>::bytes(), st>>>(dF, t.cls_f0[c], t.cls_nf[c], t.cls_t0[c],
+                                                                       t.cls_nt[c], c, dB, list));
   CK(cudaGetLastError());
   return LOPC_OK;
 }
 
 template <typename T, int ND>
-int launch_class_encode(const CompressPlan& p, int c, const FieldInfo* dF, cudaStream_t st) {
+int launch_class_encode(const Table& t, int c, const FieldInfo* dF, cudaStream_t st) {
   using C = TileCfg<T, ND>;
-  if (!p.cls_nf[c]) return LOPC_OK;
+  if (!t.cls_nf[c]) return LOPC_OK;
   LAUNCH("encode_subbins", st,
-         k_encode_sub<T, ND><<<(unsigned)p.cls_nt[c], C::NT, EncSmem<T, ND>::bytes(), st>>>(dF, p.cls_f0[c],
-                                                                                           p.cls_nf[c], p.cls_t0[c]));
+         k_encode_sub<T, ND><<<(unsigned)t.cls_nt[c], C::NT, EncSmem<T, ND>::bytes(), st>>>(dF, t.cls_f0[c],
+                                                                                           t.cls_nf[c], t.cls_t0[c]));
   CK(cudaGetLastError());
+  return LOPC_OK;
+}
+
+// State reset, range, eps and the tile pass of every field of the table.
+int launch_pre(const Table& t, const FieldInfo* dF, cudaStream_t st) {
+  int rc;
+  if ((rc = launch_init(t, dF, st))) return rc;
+  if ((rc = launch_class_pre<float, 2>(t, 0, dF, st))) return rc;
+  if ((rc = launch_class_pre<float, 3>(t, 1, dF, st))) return rc;
+  if ((rc = launch_class_pre<double, 2>(t, 2, dF, st))) return rc;
+  return launch_class_pre<double, 3>(t, 3, dF, st);
+}
+
+// One rerun round: of every tile (list == null, the first round) or of the listed ones.
+int launch_reruns(const Table& t, const FieldInfo* dF, const BatchState* dB, const uint32_t* list, cudaStream_t st) {
+  int rc;
+  if ((rc = launch_class_rerun<float, 2>(t, 0, dF, dB, list, st))) return rc;
+  if ((rc = launch_class_rerun<float, 3>(t, 1, dF, dB, list, st))) return rc;
+  if ((rc = launch_class_rerun<double, 2>(t, 2, dF, dB, list, st))) return rc;
+  return launch_class_rerun<double, 3>(t, 3, dF, dB, list, st);
+}
+
+int launch_compact(const Table& t, FieldInfo* dF, uint32_t* list, BatchState* dB, unsigned int* field_counts,
+                   cudaGraphConditionalHandle h, int use_h, cudaStream_t st) {
+  LAUNCH("compact", st,
+         k_compact<1024><<<1, 1024, 0, st>>>(dF, t.n(), t.total_words, list, dB, field_counts, h, use_h));
+  CK(cudaGetLastError());
+  return LOPC_OK;
+}
+
+// Subbin records, size scan, pack and per-field results of every field of the table.
+int launch_epilogue(const Table& t, const FieldInfo* dF, cudaStream_t st) {
+  int rc;
+  if ((rc = launch_class_encode<float, 2>(t, 0, dF, st))) return rc;
+  if ((rc = launch_class_encode<float, 3>(t, 1, dF, st))) return rc;
+  if ((rc = launch_class_encode<double, 2>(t, 2, dF, st))) return rc;
+  if ((rc = launch_class_encode<double, 3>(t, 3, dF, st))) return rc;
+  LAUNCH("scan_sizes", st, k_scan_sizes<1024><<<t.n(), 1024, 0, st>>>(dF));
+  LAUNCH("pack", st, k_pack<<<dim3(sm_count() * 2, t.n()), 256, 0, st>>>(dF));
+  LAUNCH("finalize", st, k_finalize<<<(t.n() + 63) / 64, 64, 0, st>>>(dF, t.n()));
+  CK(cudaGetLastError());
+  return LOPC_OK;
+}
+
+// ------------------------------------------------------------ compress plan
+
+// Workspace of a compression call: shared state, the field table, the results of a
+// single-field call, the rerun list, then one FieldPart per field.
+struct CompressPlan {
+  Table t;
+  std::vector<int> order;  // position in the table -> caller's index
+  size_t off_state = 0, off_table = 0, off_results = 0, off_list = 0;
+  std::vector<size_t> off_field;
+  size_t ws_total = 0;
+};
+
+// Lays out a call over descs[0..n) (sorted by class); fills pointers when ws != null.
+int plan_compress(int n, const lopc_field_desc* descs, const void* const* xs, void* const* outs, const size_t* caps,
+                  uint64_t* d_sizes, int* d_status, int64_t* bins_out, uint8_t* ws, CompressPlan& p) {
+  p = CompressPlan{};  // planning twice (size, then pointers) must not accumulate
+  p.order.resize(n);
+  for (int i = 0; i < n; ++i) p.order[i] = i;
+  std::stable_sort(p.order.begin(), p.order.end(), [&](int a, int b) {
+    return class_of(descs[a].dtype, descs[a].ndim) < class_of(descs[b].dtype, descs[b].ndim);
+  });
+  p.t.F.resize(n);
+  for (int k = 0; k < n; ++k)
+    p.t.F[k] = field_entry(&descs[p.order[k]], nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr);
+  layout_table(p.t);
+  size_t o = 0;
+  p.off_state = o;
+  o = align256(o + sizeof(BatchState));
+  p.off_table = o;
+  o = align256(o + (size_t)n * sizeof(FieldInfo));
+  p.off_results = o;
+  o = align256(o + 16);
+  p.off_list = o;
+  o = align256(o + 4 * (size_t)p.t.total_tiles);
+  p.off_field.resize(n);
+  for (int k = 0; k < n; ++k) {
+    p.off_field[k] = o;
+    o += field_part(p.t.F[k].g).total;
+  }
+  p.ws_total = o;
+  if (!ws) return LOPC_OK;
+  for (int k = 0; k < n; ++k) {
+    const int i = p.order[k];
+    FieldInfo f = field_entry(&descs[i], xs ? xs[i] : nullptr, outs ? outs[i] : nullptr, caps ? caps[i] : 0,
+                              d_sizes ? d_sizes + i : nullptr, d_status ? d_status + i : nullptr, bins_out,
+                              ws + p.off_field[k]);
+    f.tile_base = p.t.F[k].tile_base;
+    f.word_base = p.t.F[k].word_base;
+    p.t.F[k] = f;
+  }
   return LOPC_OK;
 }
 
 struct Ptrs {
   FieldInfo* F;
   BatchState* B;
-  int64_t* bounds;
-  uint8_t* dirty;
   uint32_t* list;
 };
 
@@ -368,18 +450,8 @@ Ptrs ptrs_of(const CompressPlan& p, uint8_t* ws) {
   Ptrs q;
   q.F = reinterpret_cast<FieldInfo*>(ws + p.off_table);
   q.B = reinterpret_cast<BatchState*>(ws + p.off_state);
-  q.bounds = reinterpret_cast<int64_t*>(ws + p.off_bounds);
-  q.dirty = ws + p.off_dirty;
   q.list = reinterpret_cast<uint32_t*>(ws + p.off_list);
   return q;
-}
-
-int launch_reruns(const CompressPlan& p, const Ptrs& q, const uint32_t* list, cudaStream_t st) {
-  int rc;
-  if ((rc = launch_class_rerun<float, 2>(p, 0, q.F, q.B, list, q.dirty, st))) return rc;
-  if ((rc = launch_class_rerun<float, 3>(p, 1, q.F, q.B, list, q.dirty, st))) return rc;
-  if ((rc = launch_class_rerun<double, 2>(p, 2, q.F, q.B, list, q.dirty, st))) return rc;
-  return launch_class_rerun<double, 3>(p, 3, q.F, q.B, list, q.dirty, st);
 }
 
 // Everything before the repair loop: state reset, range, eps, tile pass, the first
@@ -387,45 +459,20 @@ int launch_reruns(const CompressPlan& p, const Ptrs& q, const uint32_t* list, cu
 int enqueue_prologue(const CompressPlan& p, const Ptrs& q, cudaStream_t st, cudaGraphConditionalHandle h, int use_h) {
   int rc;
   CK(cudaMemsetAsync(q.B, 0, sizeof(BatchState), st));
-  CK(cudaMemsetAsync(q.dirty, 0, (size_t)p.total_tiles, st));
-  LAUNCH("init_params", st, k_init_params<<<(p.n + 63) / 64, 64, 0, st>>>(q.F, p.n));
-  if ((rc = launch_class_pre<float, 2>(p, 0, q.F, st))) return rc;
-  if ((rc = launch_class_pre<float, 3>(p, 1, q.F, st))) return rc;
-  if ((rc = launch_class_pre<double, 2>(p, 2, q.F, st))) return rc;
-  if ((rc = launch_class_pre<double, 3>(p, 3, q.F, st))) return rc;
-  if ((rc = launch_reruns(p, q, nullptr, st))) return rc;
-  LAUNCH("compact", st,
-         k_compact<1024><<<1, 1024, 0, st>>>(q.dirty, p.total_tiles, q.list, q.B, q.bounds, q.F, p.n, p.round_cap, h, use_h));
-  CK(cudaGetLastError());
-  return LOPC_OK;
+  if ((rc = launch_pre(p.t, q.F, st))) return rc;
+  if ((rc = launch_reruns(p.t, q.F, q.B, nullptr, st))) return rc;
+  return launch_compact(p.t, q.F, q.list, q.B, nullptr, h, use_h, st);
 }
 
 int enqueue_loop_body(const CompressPlan& p, const Ptrs& q, cudaStream_t st, cudaGraphConditionalHandle h, int use_h) {
   int rc;
-  if ((rc = launch_reruns(p, q, q.list, st))) return rc;
-  LAUNCH("compact", st,
-         k_compact<1024><<<1, 1024, 0, st>>>(q.dirty, p.total_tiles, q.list, q.B, q.bounds, q.F, p.n, p.round_cap, h, use_h));
-  CK(cudaGetLastError());
-  return LOPC_OK;
+  if ((rc = launch_reruns(p.t, q.F, q.B, q.list, st))) return rc;
+  return launch_compact(p.t, q.F, q.list, q.B, nullptr, h, use_h, st);
 }
 
-int enqueue_epilogue(const CompressPlan& p, const Ptrs& q, cudaStream_t st) {
-  int rc;
-  if ((rc = launch_class_encode<float, 2>(p, 0, q.F, st))) return rc;
-  if ((rc = launch_class_encode<float, 3>(p, 1, q.F, st))) return rc;
-  if ((rc = launch_class_encode<double, 2>(p, 2, q.F, st))) return rc;
-  if ((rc = launch_class_encode<double, 3>(p, 3, q.F, st))) return rc;
-  LAUNCH("scan_sizes", st, k_scan_sizes<1024><<<p.n, 1024, 0, st>>>(q.F));
-  LAUNCH("pack", st, k_pack<<<dim3(148 * 2, p.n), 256, 0, st>>>(q.F));
-  LAUNCH("finalize", st, k_finalize<<<(p.n + 63) / 64, 64, 0, st>>>(q.F, p.n));
-  CK(cudaGetLastError());
-  return LOPC_OK;
-}
-
-// Uploads the field table and the class bounds (not part of any graph).
+// Uploads the field table (not part of any graph).
 int upload_plan(const CompressPlan& p, const Ptrs& q, cudaStream_t st) {
-  CK(cudaMemcpyAsync(q.F, p.F.data(), (size_t)p.n * sizeof(FieldInfo), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(q.bounds, p.bounds, sizeof(p.bounds), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(q.F, p.t.F.data(), (size_t)p.t.n() * sizeof(FieldInfo), cudaMemcpyHostToDevice, st));
   return LOPC_OK;
 }
 
@@ -441,7 +488,7 @@ int run_host_loop(const CompressPlan& p, const Ptrs& q, cudaStream_t st) {
     if (hb.count[0] + hb.count[1] + hb.count[2] + hb.count[3] == 0) break;
     if ((rc = enqueue_loop_body(p, q, st, cudaGraphConditionalHandle{}, 0))) return rc;
   }
-  return enqueue_epilogue(p, q, st);
+  return launch_epilogue(p.t, q.F, st);
 }
 
 // The whole compression as one CUDA graph: the repair rounds run in a conditional
@@ -491,7 +538,7 @@ int capture_graph(const CompressPlan& p, const Ptrs& q, cudaStream_t st, cudaGra
       if (cudaStreamEndCapture(bs, &b2) != cudaSuccess && !rc) rc = LOPC_ERR_CUDA;
     }
   }
-  if (!rc) rc = enqueue_epilogue(p, q, cap);
+  if (!rc) rc = launch_epilogue(p.t, q.F, cap);
   if (cudaStreamEndCapture(cap, &graph) != cudaSuccess && !rc) rc = LOPC_ERR_CUDA;
   if (!rc && cudaGraphInstantiate(exec, graph, 0) != cudaSuccess) rc = LOPC_ERR_CUDA;
   if (graph) cudaGraphDestroy(graph);
@@ -518,7 +565,7 @@ struct GraphCache {
     return nullptr;
   }
   void put(std::vector<uint64_t> key, cudaGraphExec_t exec) {
-    if (e.size() >= 16) {
+    if (e.size() >= 128) {
       auto it = std::min_element(e.begin(), e.end(), [](const Entry& a, const Entry& b) { return a.used < b.used; });
       cudaGraphExecDestroy(it->exec);
       e.erase(it);
@@ -534,9 +581,9 @@ std::vector<uint64_t> plan_key(const CompressPlan& p, const uint8_t* ws) {
   cudaGetDevice(&dev);
   k.push_back((uint64_t)dev);
   k.push_back((uint64_t)(uintptr_t)ws);
-  k.push_back((uint64_t)p.n);
-  k.push_back((uint64_t)p.round_cap);
-  for (const FieldInfo& f : p.F) {
+  k.push_back((uint64_t)p.t.n());
+  for (int c = 0; c < 4; ++c) k.push_back((uint64_t)rerun_blocks(c));
+  for (const FieldInfo& f : p.t.F) {
     const uint64_t* w = reinterpret_cast<const uint64_t*>(&f);
     for (size_t i = 0; i < sizeof(FieldInfo) / 8; ++i) k.push_back(w[i]);
   }
@@ -577,7 +624,7 @@ int compress_one(const lopc_field_desc* d, const void* d_x, void* d_out, size_t 
   plan_compress(1, d, xs, outs, caps, dsize, dstat, bins_out, ws, p);
   int rc = run_compress(p, ws, st);
   if (rc) return rc;
-  const FieldInfo& f = p.F[0];
+  const FieldInfo& f = p.t.F[0];
   if (subbins_out)
     LAUNCH("export", st,
            k_export_subbins<<<148 * 8, 256, 0, st>>>(f.g.nz * f.g.ny * f.g.nx, f.s, subbins_out));
@@ -772,6 +819,187 @@ int decompress_one(const void* d_in, size_t in_size, void* d_x, size_t x_cap, ui
   CK(cudaMemcpyAsync(&hs, ws + p.off_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return hs ? LOPC_ERR_CORRUPT : LOPC_OK;
+}
+
+// ------------------------------------------------------------ serving engine
+// Round-level continuous batching.  Every field admitted so far keeps its state
+// (bins, subbins, lower masks, dirty bitmap) in its own workspace for its whole
+// life.  One step runs a compaction and a rerun round over every field in repair
+// on the rounds stream.  On the aux stream it runs the tile pass and first round
+// of the fields submitted since the last step, and encodes and packs the fields
+// whose last compaction listed no tile.  Fields join and leave between rounds, so
+// a field that arrives while others are repairing is never held back by them.
+
+struct EngineItem {
+  FieldInfo f;
+  uint64_t tag;
+  int slot;
+};
+
+struct EngineBatch {
+  std::vector<EngineItem> items;
+  cudaEvent_t done;
+};
+
+}  // namespace
+
+struct lopc_engine {
+  int max_fields = 0;
+  int64_t max_tiles = 0;
+  cudaStream_t sm = nullptr, sa = nullptr;  // rounds; new and finishing fields
+  cudaEvent_t ev_counts = nullptr, ev_pro = nullptr, ev_ready = nullptr;
+  cudaEvent_t ev_stage[3] = {nullptr, nullptr, nullptr};
+  FieldInfo* dT[3] = {nullptr, nullptr, nullptr};  // tables: 0 = in repair, 1 = new, 2 = finishing
+  FieldInfo* hT[3] = {nullptr, nullptr, nullptr};  // their pinned staging copies
+  BatchState* dB = nullptr;
+  uint32_t* dlist = nullptr;
+  unsigned int* dcounts = nullptr;
+  unsigned int* hcounts = nullptr;  // pinned
+  uint64_t* hsize = nullptr;        // pinned and mapped: k_finalize writes each field's result here
+  int* hstatus = nullptr;
+  uint64_t* dsize = nullptr;        // device aliases of hsize / hstatus
+  int* dstatus = nullptr;
+  std::vector<EngineItem> fresh, running, done;
+  std::deque<EngineBatch> finishing;
+  std::vector<cudaEvent_t> spare_events;
+  std::vector<int> free_slots;
+  bool pro_pending = false;
+  int64_t tiles_held = 0;  // tiles of fresh + running fields (bounds the rerun list)
+};
+
+namespace {
+
+void engine_free(lopc_engine* e) {
+  if (e->sm) cudaStreamSynchronize(e->sm);
+  if (e->sa) cudaStreamSynchronize(e->sa);
+  for (auto& b : e->finishing) cudaEventDestroy(b.done);
+  for (cudaEvent_t ev : e->spare_events) cudaEventDestroy(ev);
+  cudaEvent_t evs[6] = {e->ev_counts, e->ev_pro, e->ev_ready, e->ev_stage[0], e->ev_stage[1], e->ev_stage[2]};
+  for (cudaEvent_t ev : evs)
+    if (ev) cudaEventDestroy(ev);
+  for (int k = 0; k < 3; ++k) {
+    if (e->dT[k]) cudaFree(e->dT[k]);
+    if (e->hT[k]) cudaFreeHost(e->hT[k]);
+  }
+  if (e->dB) cudaFree(e->dB);
+  if (e->dlist) cudaFree(e->dlist);
+  if (e->dcounts) cudaFree(e->dcounts);
+  if (e->hcounts) cudaFreeHost(e->hcounts);
+  if (e->hsize) cudaFreeHost(e->hsize);
+  if (e->hstatus) cudaFreeHost(e->hstatus);
+  if (e->sm) cudaStreamDestroy(e->sm);
+  if (e->sa) cudaStreamDestroy(e->sa);
+  delete e;
+}
+
+int engine_init(lopc_engine* e) {
+  const size_t tb = (size_t)e->max_fields * sizeof(FieldInfo);
+  CK(cudaStreamCreateWithFlags(&e->sm, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&e->sa, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&e->ev_counts, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&e->ev_pro, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&e->ev_ready, cudaEventDisableTiming));
+  for (int k = 0; k < 3; ++k) {
+    CK(cudaEventCreateWithFlags(&e->ev_stage[k], cudaEventDisableTiming));
+    CK(cudaMalloc(&e->dT[k], tb));
+    CK(cudaHostAlloc(&e->hT[k], tb, cudaHostAllocDefault));
+  }
+  CK(cudaMalloc(&e->dB, sizeof(BatchState)));
+  CK(cudaMemset(e->dB, 0, sizeof(BatchState)));
+  CK(cudaMalloc(&e->dlist, 4 * (size_t)std::max<int64_t>(1, e->max_tiles)));
+  CK(cudaMalloc(&e->dcounts, 4 * (size_t)e->max_fields));
+  CK(cudaHostAlloc(&e->hcounts, 4 * (size_t)e->max_fields, cudaHostAllocDefault));
+  CK(cudaHostAlloc(&e->hsize, 8 * (size_t)e->max_fields, cudaHostAllocMapped));
+  CK(cudaHostAlloc(&e->hstatus, 4 * (size_t)e->max_fields, cudaHostAllocMapped));
+  CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&e->dsize), e->hsize, 0));
+  CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&e->dstatus), e->hstatus, 0));
+  for (int s = e->max_fields - 1; s >= 0; --s) e->free_slots.push_back(s);
+  return LOPC_OK;
+}
+
+// Sorts items by class (stable) and builds their table with fresh numbering.
+void engine_table(std::vector<EngineItem>& items, Table& t) {
+  std::stable_sort(items.begin(), items.end(), [](const EngineItem& a, const EngineItem& b) {
+    return class_of_geometry(a.f.g) < class_of_geometry(b.f.g);
+  });
+  t.F.resize(items.size());
+  for (size_t k = 0; k < items.size(); ++k) t.F[k] = items[k].f;
+  layout_table(t);
+}
+
+// Copies table t into device table `which` on stream st (staging reused once the
+// previous copy from it has run).
+int engine_upload(lopc_engine* e, int which, const Table& t, cudaStream_t st) {
+  CK(cudaEventSynchronize(e->ev_stage[which]));
+  memcpy(e->hT[which], t.F.data(), (size_t)t.n() * sizeof(FieldInfo));
+  CK(cudaMemcpyAsync(e->dT[which], e->hT[which], (size_t)t.n() * sizeof(FieldInfo), cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(e->ev_stage[which], st));
+  return LOPC_OK;
+}
+
+int engine_step(lopc_engine* e, int rounds, int* active) {
+  int rc;
+  const bool round = !e->running.empty();
+  Table tr;
+  if (round) {
+    engine_table(e->running, tr);
+    if ((rc = engine_upload(e, 0, tr, e->sm))) return rc;
+    if (e->pro_pending) {
+      CK(cudaStreamWaitEvent(e->sm, e->ev_pro, 0));
+      e->pro_pending = false;
+    }
+    for (int r = 0; r < rounds; ++r) {
+      const bool last = r + 1 == rounds;
+      if ((rc = launch_compact(tr, e->dT[0], e->dlist, e->dB, last ? e->dcounts : nullptr, {}, 0, e->sm))) return rc;
+      if (last) {
+        CK(cudaMemcpyAsync(e->hcounts, e->dcounts, 4 * (size_t)tr.n(), cudaMemcpyDeviceToHost, e->sm));
+        CK(cudaEventRecord(e->ev_counts, e->sm));
+      }
+      if ((rc = launch_reruns(tr, e->dT[0], e->dB, e->dlist, e->sm))) return rc;
+    }
+  }
+  if (!e->fresh.empty()) {
+    Table ta;
+    engine_table(e->fresh, ta);
+    if ((rc = engine_upload(e, 1, ta, e->sa))) return rc;
+    if ((rc = launch_pre(ta, e->dT[1], e->sa))) return rc;
+    if ((rc = launch_reruns(ta, e->dT[1], e->dB, nullptr, e->sa))) return rc;
+    CK(cudaEventRecord(e->ev_pro, e->sa));
+    e->pro_pending = true;
+  }
+  if (round) {
+    // the rerun round is still running on the device while the host sorts the fields
+    CK(cudaEventSynchronize(e->ev_counts));
+    std::vector<EngineItem> keep, fin;
+    for (int k = 0; k < tr.n(); ++k) (e->hcounts[k] ? keep : fin).push_back(e->running[k]);
+    e->running.swap(keep);
+    if (!fin.empty()) {
+      Table tc;
+      engine_table(fin, tc);
+      if ((rc = engine_upload(e, 2, tc, e->sa))) return rc;
+      CK(cudaStreamWaitEvent(e->sa, e->ev_counts, 0));
+      if ((rc = launch_epilogue(tc, e->dT[2], e->sa))) return rc;
+      EngineBatch b;
+      b.items = std::move(fin);
+      if (e->spare_events.empty()) {
+        CK(cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming));
+      } else {
+        b.done = e->spare_events.back();
+        e->spare_events.pop_back();
+      }
+      CK(cudaEventRecord(b.done, e->sa));
+      for (const EngineItem& it : b.items) e->tiles_held -= it.f.g.ntiles;
+      e->finishing.push_back(std::move(b));
+    }
+  }
+  e->running.insert(e->running.end(), e->fresh.begin(), e->fresh.end());
+  e->fresh.clear();
+  if (active) {
+    size_t n = e->running.size() + e->done.size();
+    for (const auto& b : e->finishing) n += b.items.size();
+    *active = (int)n;
+  }
+  return LOPC_OK;
 }
 
 }  // namespace
@@ -989,8 +1217,107 @@ const char* lopc_strerror(int s) {
     case LOPC_ERR_NOT_CONVERGED: return "repair round cap reached";
     case LOPC_ERR_CUDA: return "CUDA runtime error";
     case LOPC_ERR_WORKSPACE: return "workspace missing or too small";
+    case LOPC_ERR_BUSY: return "serving engine full";
     default: return "unknown status";
   }
+}
+
+
+void lopc_tune_set(const int* v) {
+  if (!v) return;
+  for (int c = 0; c < 4; ++c) g_rerun_per_sm[c] = v[c] < 1 ? 1 : (v[c] > 16 ? 16 : v[c]);
+}
+
+void lopc_tune_get(int* v) {
+  if (!v) return;
+  for (int c = 0; c < 4; ++c) v[c] = g_rerun_per_sm[c];
+}
+
+// ------------------------------------------------------------ serving engine ABI
+
+int lopc_engine_create(int max_fields, int64_t max_tiles, lopc_engine** out) {
+  if (!out || max_fields <= 0 || max_fields > 65535 || max_tiles <= 0 || max_tiles > (int64_t(1) << 32))
+    return LOPC_ERR_INVALID_ARG;
+  *out = nullptr;
+  lopc_engine* e = new lopc_engine;
+  e->max_fields = max_fields;
+  e->max_tiles = max_tiles;
+  const int rc = engine_init(e);
+  if (rc) {
+    engine_free(e);
+    return rc;
+  }
+  *out = e;
+  return LOPC_OK;
+}
+
+void lopc_engine_destroy(lopc_engine* e) {
+  if (e) engine_free(e);
+}
+
+size_t lopc_engine_field_workspace_size(const lopc_field_desc* d) {
+  if (!desc_valid(d)) return 0;
+  return field_part(geometry_of(d)).total;
+}
+
+int lopc_engine_submit(lopc_engine* e, const lopc_field_desc* d, const void* d_x, void* d_out, size_t out_cap,
+                       void* d_ws, size_t ws_size, uint64_t tag, void* ready_stream) {
+  if (!e || !desc_valid(d) || !d_x || !d_out) return LOPC_ERR_INVALID_ARG;
+  const Geometry g = geometry_of(d);
+  if (!d_ws || ws_size < field_part(g).total || (reinterpret_cast<uintptr_t>(d_ws) & 255)) return LOPC_ERR_WORKSPACE;
+  if (e->free_slots.empty() || e->tiles_held + g.ntiles > e->max_tiles) return LOPC_ERR_BUSY;
+  // the engine's streams wait for the input to be ready on the caller's stream
+  CK(cudaEventRecord(e->ev_ready, reinterpret_cast<cudaStream_t>(ready_stream)));
+  CK(cudaStreamWaitEvent(e->sa, e->ev_ready, 0));
+  EngineItem it;
+  it.slot = e->free_slots.back();
+  e->free_slots.pop_back();
+  it.tag = tag;
+  it.f = field_entry(d, d_x, d_out, out_cap, e->dsize + it.slot, e->dstatus + it.slot, nullptr,
+                     reinterpret_cast<uint8_t*>(d_ws));
+  e->hsize[it.slot] = 0;
+  e->hstatus[it.slot] = LOPC_ERR_CUDA;
+  e->tiles_held += g.ntiles;
+  e->fresh.push_back(it);
+  return LOPC_OK;
+}
+
+int lopc_engine_step(lopc_engine* e, int rounds, int* active) {
+  if (!e || rounds <= 0) return LOPC_ERR_INVALID_ARG;
+  return engine_step(e, rounds, active);
+}
+
+int lopc_engine_poll(lopc_engine* e, uint64_t* tags, uint64_t* sizes, int* statuses, int cap) {
+  if (!e || cap < 0 || (cap > 0 && (!tags || !sizes || !statuses))) return LOPC_ERR_INVALID_ARG;
+  while (!e->finishing.empty()) {
+    const cudaError_t q = cudaEventQuery(e->finishing.front().done);
+    if (q == cudaErrorNotReady) break;
+    if (q != cudaSuccess) {
+      (void)cudaGetLastError();
+      return LOPC_ERR_CUDA;
+    }
+    EngineBatch& b = e->finishing.front();
+    e->done.insert(e->done.end(), b.items.begin(), b.items.end());
+    e->spare_events.push_back(b.done);
+    e->finishing.pop_front();
+  }
+  const int n = (int)std::min<size_t>((size_t)cap, e->done.size());
+  for (int k = 0; k < n; ++k) {
+    const EngineItem& it = e->done[k];
+    tags[k] = it.tag;
+    sizes[k] = e->hsize[it.slot];
+    statuses[k] = e->hstatus[it.slot];
+    e->free_slots.push_back(it.slot);
+  }
+  e->done.erase(e->done.begin(), e->done.begin() + n);
+  return n;
+}
+
+int lopc_engine_sync(lopc_engine* e) {
+  if (!e) return LOPC_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(e->sm));
+  CK(cudaStreamSynchronize(e->sa));
+  return LOPC_OK;
 }
 
 }  // extern "C"

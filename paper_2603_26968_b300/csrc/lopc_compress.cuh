@@ -48,9 +48,14 @@ __device__ __forceinline__ bool dir_valid(int k) {
 
 // ------------------------------------------------------------------ range
 
+// Per-field state reset and a cleared dirty bitmap; blockIdx.y is the field.
 __global__ void k_init_params(const FieldInfo* F, int nf) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
   if (f >= nf) return;
+  const int64_t nw = dirty_words(F[f].g.ntiles);
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x)
+    F[f].dirty[w] = 0u;
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
   Params* P = F[f].P;
   P->kmin = ~0ULL;
   P->kmax = 0ULL;
@@ -528,7 +533,7 @@ struct RerunSmem {
 template <typename T, int ND>
 __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN)
     k_rerun(const FieldInfo* __restrict__ F, int f0, int nf, int64_t tile0, int64_t ntile_cls, int cls,
-            const BatchState* __restrict__ B, const uint32_t* __restrict__ list, uint8_t* __restrict__ dirty) {
+            const BatchState* __restrict__ B, const uint32_t* __restrict__ list) {
   using G = TileGeom<T, ND>;
   using RS = RerunSmem<T, ND>;
   constexpr int NT = G::NT;
@@ -652,41 +657,63 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
         if (!((cm[e + G::off(dz_of(k), dy_of(k), dx_of(k))] >> kop) & 1u)) continue;
         const int64_t qz = pz + dz_of(k), qy = py + dy_of(k), qx = px + dx_of(k);
         if (*(volatile const uint32_t*)&s_glob[qz * plane + qy * g.nx + qx] >= sf + (k < 7 ? 1u : 0u)) continue;
-        dirty[fi.tile_base + ((qz / g.tz) * g.nty + qy / g.ty) * g.ntx + qx / g.tx] = 1;
+        const int64_t lt = ((qz / g.tz) * g.nty + qy / g.ty) * g.ntx + qx / g.tx;
+        const uint32_t bit = 1u << (lt & 31);
+        if (!(*(volatile const uint32_t*)&fi.dirty[lt >> 5] & bit)) atomicOr(&fi.dirty[lt >> 5], bit);
       }
     }
     __syncthreads();  // shared state is reused by the next item
   }
 }
 
-// Dirty flags -> the next round's list, in tile order (one block): per class the
-// count and first position, flags cleared.  Counts the round and tells the graph's
-// while-node whether to run another round; at the round cap the fields that still
-// have dirty tiles are reported as not converged.
+// Dirty bitmaps -> the next round's list, in table order (one block): per class
+// the count and first position, bits cleared.  The table is sorted by class, so the
+// list is grouped by class.  Counts a round for every field of the table; a field
+// past its round cap drops its dirty tiles and is reported as not converged.
+// field_counts (optional, one per table entry) receives how many tiles each field
+// has in the list: 0 means its subbins are final.  Tells the graph's while-node
+// whether to run another round.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_compact(uint8_t* __restrict__ dirty, int64_t total, uint32_t* __restrict__ list,
-                                                BatchState* B, const int64_t* __restrict__ cls_bounds /* 5 */,
-                                                const FieldInfo* __restrict__ F, int nf, int64_t round_cap,
+__global__ void __launch_bounds__(NT) k_compact(const FieldInfo* __restrict__ F, int nf, int64_t total_words,
+                                                uint32_t* __restrict__ list, BatchState* B,
+                                                unsigned int* __restrict__ field_counts,
                                                 cudaGraphConditionalHandle handle, int use_handle) {
   __shared__ unsigned int tmp[NT / 32 + 1];
   __shared__ unsigned int cnt[4];
+  __shared__ int capped;
   if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
+  if (threadIdx.x == 0) capped = 0;
+  for (int f = threadIdx.x; f < nf; f += NT) {
+    F[f].P->rounds += 1;
+    if (field_counts) field_counts[f] = 0;
+  }
   __syncthreads();
-  const unsigned long long round = B->rounds + 1;
-  const bool cap_hit = (long long)round > round_cap;
   unsigned int run = 0;
-  for (int64_t base = 0; base < total; base += NT) {
-    const int64_t t = base + threadIdx.x;
-    const unsigned int d = (t < total && dirty[t]) ? 1u : 0u;
+  for (int64_t base = 0; base < total_words; base += NT) {
+    const int64_t w = base + threadIdx.x;
+    uint32_t bits = 0;
+    int k = 0;
+    if (w < total_words) {
+      k = field_of_word(F, nf, w);
+      uint32_t* dw = F[k].dirty + (w - F[k].word_base);
+      bits = *dw;
+      if (bits) {
+        *dw = 0u;
+        if ((long long)F[k].P->rounds > F[k].round_cap) {
+          atomicOr(&F[k].P->status, kErrNotConverged);
+          capped = 1;
+          bits = 0;
+        }
+      }
+    }
+    const unsigned int n = __popc(bits);
     unsigned int tot;
-    const unsigned int pos = block_exclusive_scan<NT, unsigned int>(d, tmp, &tot) + run;
-    if (d) {
-      dirty[t] = 0;
-      list[pos] = (uint32_t)t;
-      int c = 0;
-      while (c < 3 && t >= cls_bounds[c + 1]) ++c;
-      atomicAdd(&cnt[c], 1u);
-      if (cap_hit) atomicOr(&F[field_of_tile(F, 0, nf, t)].P->status, kErrNotConverged);
+    unsigned int pos = block_exclusive_scan<NT, unsigned int>(n, tmp, &tot) + run;
+    if (n) {
+      const int64_t t0 = F[k].tile_base + 32 * (w - F[k].word_base);
+      for (uint32_t b = bits; b; b &= b - 1) list[pos++] = (uint32_t)(t0 + __ffs(b) - 1);
+      atomicAdd(&cnt[class_of_geometry(F[k].g)], n);
+      if (field_counts) atomicAdd(&field_counts[k], n);
     }
     run += tot;
   }
@@ -694,14 +721,14 @@ __global__ void __launch_bounds__(NT) k_compact(uint8_t* __restrict__ dirty, int
   if (threadIdx.x == 0) {
     unsigned int o = 0;
     for (int c = 0; c < 4; ++c) {
-      B->count[c] = cap_hit ? 0u : cnt[c];
+      B->count[c] = cnt[c];
       B->off[c] = o;
       o += cnt[c];
     }
-    B->rounds = round;
-    B->runs += cap_hit ? 0 : run;
-    B->cap_hit |= cap_hit && run;
-    if (use_handle) cudaGraphSetConditional(handle, (!cap_hit && run) ? 1u : 0u);
+    B->rounds += 1;
+    B->runs += run;
+    B->cap_hit |= (unsigned int)capped;
+    if (use_handle) cudaGraphSetConditional(handle, run ? 1u : 0u);
   }
 }
 

@@ -368,9 +368,18 @@ struct FieldInfo {
   int64_t* bins_out;      // optional export of the bins (may be null)
   uint64_t* size_out;     // device: this field's stream length (may be null)
   int* status_out;        // device: this field's LOPC status (may be null)
-  int64_t tile_base;
+  uint32_t* dirty;        // tiles to rerun next round: one bit per tile, ceil(ntiles / 32) words
+  int64_t tile_base;      // first tile in the table's tile index space
+  int64_t word_base;      // first dirty word in the table's flat word space
   int64_t round_cap;
 };
+
+__host__ __device__ inline int64_t dirty_words(int64_t ntiles) { return (ntiles + 31) / 32; }
+
+// Field class of a table entry: 0 = f32 2D, 1 = f32 3D, 2 = f64 2D, 3 = f64 3D.
+__host__ __device__ inline int class_of_geometry(const Geometry& g) {
+  return (g.dtype == LOPC_F64 ? 2 : 0) + (g.ndim == 3 ? 1 : 0);
+}
 
 // State shared by all fields of a launch.
 struct BatchState {
@@ -381,6 +390,19 @@ struct BatchState {
   unsigned int cap_hit;
   unsigned int pad;
 };
+
+// Field of flat dirty word w among fields F[0 .. nf), sorted by word_base.
+__device__ __forceinline__ int field_of_word(const FieldInfo* F, int nf, int64_t w) {
+  int lo = 0, hi = nf - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (F[mid].word_base <= w)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
 
 // Field of global tile gt among fields F[f0 .. f0+nf), sorted by tile_base.
 __device__ __forceinline__ int field_of_tile(const FieldInfo* F, int f0, int nf, int64_t gt) {

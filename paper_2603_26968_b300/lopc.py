@@ -18,7 +18,9 @@ LIB_PATH = PKG / "liblopc.so"
 
 OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "NONFINITE", -3: "RANGE", -4: "CAPACITY", -5: "CORRUPT",
-          -6: "NOT_CONVERGED", -7: "CUDA", -8: "WORKSPACE"}
+          -6: "NOT_CONVERGED", -7: "CUDA", -8: "WORKSPACE", -9: "BUSY"}
+ERR_BUSY = -9
+ERRORS_INV = {v: k for k, v in ERRORS.items()}
 F32, F64 = 0, 1
 ABS, NOA = 0, 1
 
@@ -80,6 +82,20 @@ def lib():
         L.lopc_profile_reset.argtypes = []
         L.lopc_profile_read.argtypes = [C.POINTER(C.c_char_p), C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int]
         L.lopc_profile_read.restype = C.c_int
+        E = C.c_void_p
+        L.lopc_engine_create.argtypes = [C.c_int, C.c_int64, C.POINTER(E)]
+        L.lopc_engine_destroy.argtypes = [E]
+        L.lopc_engine_destroy.restype = None
+        L.lopc_engine_field_workspace_size.argtypes = [D]
+        L.lopc_engine_field_workspace_size.restype = C.c_size_t
+        L.lopc_engine_submit.argtypes = [E, D, P, P, C.c_size_t, P, C.c_size_t, C.c_uint64, P]
+        L.lopc_engine_step.argtypes = [E, C.c_int, C.POINTER(C.c_int)]
+        L.lopc_engine_poll.argtypes = [E, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_int), C.c_int]
+        L.lopc_engine_sync.argtypes = [E]
+        L.lopc_tune_set.argtypes = [C.POINTER(C.c_int)]
+        L.lopc_tune_set.restype = None
+        L.lopc_tune_get.argtypes = [C.POINTER(C.c_int)]
+        L.lopc_tune_get.restype = None
         L.lopc_strerror.argtypes = [C.c_int]
         L.lopc_strerror.restype = C.c_char_p
         _lib = L
@@ -337,3 +353,67 @@ def batch_decompress(streams, outs=None, stream=None):
     _check(rc, "lopc_batch_decompress")
     torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
     return outs, status.cpu().tolist()
+
+
+def tune_set(rerun_blocks_per_sm) -> None:
+    """Persistent rerun blocks per SM for classes (f32 2D, f32 3D, f64 2D, f64 3D)."""
+    lib().lopc_tune_set((C.c_int * 4)(*[int(v) for v in rerun_blocks_per_sm]))
+
+
+def tune_get() -> Tuple[int, int, int, int]:
+    v = (C.c_int * 4)()
+    lib().lopc_tune_get(v)
+    return tuple(int(a) for a in v)
+
+
+def engine_field_workspace_size(desc: FieldDesc) -> int:
+    return int(lib().lopc_engine_field_workspace_size(C.byref(desc)))
+
+
+class Engine:
+    """The library's serving engine (round-level continuous batching).  Buffers
+    passed to submit() must stay alive until poll() reports their tag."""
+
+    def __init__(self, max_fields: int = 1024, max_tiles: int = 1 << 22):
+        self._e = C.c_void_p()
+        _check(lib().lopc_engine_create(int(max_fields), int(max_tiles), C.byref(self._e)), "lopc_engine_create")
+        self.max_fields = max_fields
+        self._tags = (C.c_uint64 * max_fields)()
+        self._sizes = (C.c_uint64 * max_fields)()
+        self._stat = (C.c_int * max_fields)()
+
+    def submit(self, x: torch.Tensor, desc: FieldDesc, out: torch.Tensor, ws: torch.Tensor, tag: int,
+               ready_stream=None) -> int:
+        """Queues a field; returns OK or ERR_BUSY (other errors raise)."""
+        rc = lib().lopc_engine_submit(self._e, C.byref(desc), C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
+                                      out.numel(), C.c_void_p(ws.data_ptr()), ws.numel(), C.c_uint64(tag),
+                                      C.c_void_p(_stream(ready_stream)))
+        if rc not in (OK, ERR_BUSY):
+            _check(rc, "lopc_engine_submit")
+        return rc
+
+    def step(self, rounds: int = 1) -> int:
+        active = C.c_int(0)
+        _check(lib().lopc_engine_step(self._e, int(rounds), C.byref(active)), "lopc_engine_step")
+        return int(active.value)
+
+    def poll(self):
+        """[(tag, stream length, status)] of the fields finished since the last poll."""
+        n = lib().lopc_engine_poll(self._e, self._tags, self._sizes, self._stat, self.max_fields)
+        if n < 0:
+            _check(n, "lopc_engine_poll")
+        return [(int(self._tags[k]), int(self._sizes[k]), int(self._stat[k])) for k in range(n)]
+
+    def sync(self) -> None:
+        _check(lib().lopc_engine_sync(self._e), "lopc_engine_sync")
+
+    def close(self) -> None:
+        if self._e:
+            lib().lopc_engine_destroy(self._e)
+            self._e = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
