@@ -177,6 +177,11 @@ LOPC_API void lopc_last_fixpoint_stats(int64_t* sweeps_total, int64_t* sweeps_ma
  * Copies min(n, 8) values and returns 8. */
 LOPC_API int lopc_last_phase_cycles(int64_t* cycles, int n);
 
+/* Measurement aid: work of the tile-local fixpoint in the last compression on this
+ * thread: point evaluations and subbin raises in the tile pass, then the same in
+ * the reruns.  Copies min(n, 4) values and returns 4. */
+LOPC_API int lopc_last_fixpoint_work(int64_t* out, int n);
+
 /* Per-kernel timing for measurement: while enabled, every kernel the library
  * launches is bracketed by CUDA events recorded on the launching stream, and the
  * elapsed times are added up per kernel when the call returns.  Off by default;

@@ -91,6 +91,7 @@ thread_local Profiler g_prof;
   } while (0)
 thread_local int64_t g_last_rounds = 0, g_last_tile_runs = 0, g_last_fix_iters = 0, g_last_fix_iters_max = 0;
 thread_local int64_t g_last_phase[8] = {};
+thread_local int64_t g_last_work[4] = {};
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -644,6 +645,7 @@ int compress_one(const lopc_field_desc* d, const void* d_x, void* d_out, size_t 
   g_last_fix_iters = (int64_t)hp.fix_iters;
   g_last_fix_iters_max = (int64_t)hp.fix_iters_max;
   for (int k = 0; k < 8; ++k) g_last_phase[k] = (int64_t)hp.phase[k];
+  for (int k = 0; k < 4; ++k) g_last_work[k] = (int64_t)hp.work[k];
   // the repair ran even if the output was too small: report the repair's status first
   if (res.status == LOPC_ERR_CAPACITY && subbins_out) res.status = LOPC_OK;
   if (res.status) return res.status;
@@ -1184,6 +1186,11 @@ void lopc_last_fixpoint_stats(int64_t* sweeps_total, int64_t* sweeps_max) {
 int lopc_last_phase_cycles(int64_t* cycles, int n) {
   for (int k = 0; k < n && k < 8; ++k) cycles[k] = g_last_phase[k];
   return 8;
+}
+
+int lopc_last_fixpoint_work(int64_t* out, int n) {
+  for (int k = 0; k < n && k < 4; ++k) out[k] = g_last_work[k];
+  return 4;
 }
 
 void lopc_profile_enable(int on) {

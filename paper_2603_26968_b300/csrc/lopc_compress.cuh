@@ -48,7 +48,7 @@ __device__ __forceinline__ bool dir_valid(int k) {
 
 // ------------------------------------------------------------------ range
 
-// Per-field state reset and a cleared dirty bitmap; blockIdx.y is the field.
+// Per-field state reset and cleared dirty flags; blockIdx.y is the field.
 __global__ void k_init_params(const FieldInfo* F, int nf) {
   const int f = blockIdx.y;
   if (f >= nf) return;
@@ -69,6 +69,7 @@ __global__ void k_init_params(const FieldInfo* F, int nf) {
   P->fix_iters = 0;
   P->fix_iters_max = 0;
   for (int k = 0; k < 8; ++k) P->phase[k] = 0;
+  for (int k = 0; k < 4; ++k) P->work[k] = 0;
   P->fast_ok = 0;
   P->inv_f = 0.f;
 }
@@ -224,66 +225,107 @@ __device__ __forceinline__ uint32_t ld_acquire_u8(const uint8_t* p) {
   return v;
 }
 
-// Tile-local least fixpoint of Alg. 2's update, frontier driven: only points whose
-// lower same-bin neighbours rose are recomputed,
+// Decodes a frontier bit (fbit order) into local coordinates.
+template <typename G>
+__device__ __forceinline__ void point_of_bit(int q, int& lz, int& ly, int& lx) {
+  const int owner = q / kSegment;
+  lx = owner % G::TX;
+  const int r = owner / G::TX;
+  lz = r / G::SEGY;
+  ly = (r % G::SEGY) * kSegment + q % kSegment;
+}
+
+// Shared state of the list-driven fixpoint: two frontiers and the risen points (one
+// bit per tile point, fbit order), two list counters, the frontier list.
+template <typename G>
+struct FixSmem {
+  static constexpr int NW = G::NP / 32;
+  static constexpr size_t bits_bytes() { return (size_t)3 * NW * 4 + 16; }
+  static constexpr size_t list_bytes() { return ((size_t)G::NP * 2 + 15) & ~(size_t)15; }
+};
+
+// Tile-local least fixpoint of Alg. 2's update, by sweeps over a frontier list:
 //   s(p) = max(s(p), max over lower same-bin n of s(n) + [n after p]),
-// and a point that rises puts its greater same-bin neighbours of the tile on the
-// next frontier (its +y neighbour in the same segment is taken in the same sweep).
-// Chaotic relaxation from lower bounds reaches the unique least fixpoint (Sec.
-// III-E) whatever the schedule.  `cml[e]` holds the lower-neighbour bits of entry
-// e; `fa` holds the first frontier (thread-major bits), `fb` must be clear.
-// Returns the number of block-wide sweeps; `risen` gets the thread's risen points.
+// recomputed only for points whose lower same-bin neighbours rose; a point that
+// rises puts its greater same-bin neighbours of the tile on the next frontier.  Each
+// sweep compacts the frontier bitmap into a list that all threads share evenly, so a
+// sweep costs about one evaluation per thread.  Raised subbins are visible to the
+// rest of the sweep at once; a neighbour read before it rose is queued again by
+// that rise.  Chaotic relaxation from lower bounds reaches the unique least fixpoint
+// (Sec. III-E) whatever the schedule.  `cml[e]` holds the lower-neighbour bits of
+// entry e; `fa` holds the first frontier, `fb` and `rb` must be clear; `rb` receives
+// the points that rose.  Returns the number of sweeps.
 template <typename G>
 __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint16_t* cml, uint32_t* fa, uint32_t* fb,
-                                                 const SegPos& sp, int limit, bool& over, uint32_t& risen) {
+                                                 uint32_t* rb, unsigned* cnt, uint16_t* list, int limit, bool& over,
+                                                 unsigned& evals, unsigned& raises) {
+  constexpr int NW = G::NP / 32, NT = G::NT;
+  static_assert(NW <= NT, "one frontier word per thread");
   volatile uint32_t* vs = sv;
-  const int wsh = sp.b0 & 31;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) cnt[0] = cnt[1] = 0;
+  __syncthreads();
   int iter = 0;
   while (true) {
-    uint32_t work = (fa[sp.b0 >> 5] >> wsh) & 0xFFFFu;
-    int changed = 0;
-    while (work) {
-      const int j = __ffs(work) - 1;
-      work &= work - 1;
-      const int e = sp.e0 + j * G::BXP;
+    // compact the frontier into the list; clear it for reuse two sweeps later
+    uint32_t word = 0;
+    if (threadIdx.x < NW) {
+      word = fa[threadIdx.x];
+      if (word) fa[threadIdx.x] = 0u;
+    }
+    const int c = __popc(word);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned base = 0;
+    if (lane == 31 && wtot) base = atomicAdd(&cnt[iter & 1], (unsigned)wtot);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    unsigned pos = base + (unsigned)(incl - c);
+    for (uint32_t b = word; b; b &= b - 1) list[pos++] = (uint16_t)(threadIdx.x * 32 + __ffs(b) - 1);
+    __syncthreads();
+    const unsigned n = cnt[iter & 1];
+    if (n == 0) break;
+    if (++iter > limit) {
+      over = true;
+      break;
+    }
+    if (threadIdx.x == 0) cnt[iter & 1] = 0;  // the counter of the next sweep
+    for (unsigned i = threadIdx.x; i < n; i += NT) {
+      const int q = list[i];
+      int lz, ly, lx;
+      point_of_bit<G>(q, lz, ly, lx);
+      const int e = G::entry(lz, ly, lx);
       const uint32_t m = cml[e];
       const uint32_t before = vs[e];
+      ++evals;
       uint32_t best = before;
 #pragma unroll
       for (int k = 0; k < 14; ++k) {
         if (!G::HZ && dz_of(k) != 0) continue;
         if (m & (1u << k)) {
-          const uint32_t c = vs[e + G::off(dz_of(k), dy_of(k), dx_of(k))] + (k >= 7 ? 1u : 0u);
-          best = c > best ? c : best;
+          const uint32_t cand = vs[e + G::off(dz_of(k), dy_of(k), dx_of(k))] + (k >= 7 ? 1u : 0u);
+          best = cand > best ? cand : best;
         }
       }
       if (best == before) continue;
       vs[e] = best;
-      changed = 1;
-      risen |= 1u << j;
-      const int ly = sp.ly0 + j;
+      ++raises;
+      atomicOr(&rb[q >> 5], 1u << (q & 31));
 #pragma unroll
       for (int k = 0; k < 14; ++k) {
         if (!G::HZ && dz_of(k) != 0) continue;
-        const int nz = sp.lz + dz_of(k), ny = ly + dy_of(k), nx = sp.lx + dx_of(k);
+        const int nz = lz + dz_of(k), ny = ly + dy_of(k), nx = lx + dx_of(k);
         if (nz < 0 || nz >= G::TZ || ny < 0 || ny >= G::TY || nx < 0 || nx >= G::TX) continue;
         const int kop = k < 7 ? k + 7 : k - 7;
         if (!((cml[e + G::off(dz_of(k), dy_of(k), dx_of(k))] >> kop) & 1u)) continue;
-        if (k == kPlusY && j + 1 < kSegment) {
-          work |= 1u << (j + 1);  // +y neighbour, later in this sweep
-        } else {
-          const int q = G::fbit(nz, ny, nx);
-          atomicOr(&fb[q >> 5], 1u << (q & 31));
-        }
+        const int qn = G::fbit(nz, ny, nx);
+        atomicOr(&fb[qn >> 5], 1u << (qn & 31));
       }
     }
-    ++iter;
-    if (!__syncthreads_or(changed)) break;
-    if (iter > limit) {
-      over = true;
-      break;
-    }
-    if (wsh == 0) fa[sp.b0 >> 5] = 0;  // one owner per frontier word
     __syncthreads();
     uint32_t* t = fa;
     fa = fb;
@@ -318,16 +360,17 @@ struct PassSmem {
   static constexpr size_t RA = up16(RAa > RAb ? RAa : RAb);
   static constexpr size_t RB = up16((size_t)G::E * sizeof(B) > L ? (size_t)G::E * sizeof(B) : L);
   static constexpr size_t RC = up16((size_t)G::E * 2);                  // lower masks
-  static constexpr size_t RD = up16((size_t)2 * (G::NP / 32) * 4);      // two frontiers
+  static constexpr size_t RD = up16(FixSmem<G>::bits_bytes());         // frontiers, risen bits, counters
+  static_assert(FixSmem<G>::list_bytes() <= RB, "the frontier list reuses the bins");
   static constexpr size_t bytes() { return RA + RB + RC + RD; }
 };
 
 // Tile pass (one block per chunk-tile):
 //   1. load x on the tile and its halo, quantize (Sec. III-A) and take order keys;
 //   2. flags (Alg. 1): the lower same-bin neighbours of every point;
-//   3. tile-local least fixpoint with halo subbins taken as 0 (a lower bound);
-//   4. write subbins and lower masks (what reruns and the boundary check need);
-//   5. encode the tile's bin record (Sec. III-C; bins are final here).
+//   3. encode the tile's bin record (Sec. III-C; bins are final once quantized);
+//   4. tile-local least fixpoint with halo subbins taken as 0 (a lower bound);
+//   5. write subbins and lower masks (what reruns and the boundary check need).
 template <typename T, int ND>
 __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
     k_pass(const FieldInfo* __restrict__ F, int f0, int nf, int64_t tile0) {
@@ -356,6 +399,9 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   uint16_t* cml = reinterpret_cast<uint16_t*>(smem + PS::RA + PS::RB);
   uint32_t* fa = reinterpret_cast<uint32_t*>(smem + PS::RA + PS::RB + PS::RC);
   uint32_t* fb = fa + G::NP / 32;
+  uint32_t* rb = fb + G::NP / 32;
+  unsigned* cnt = rb + G::NP / 32;
+  uint16_t* list = reinterpret_cast<uint16_t*>(smem + PS::RA + PS::RB - FixSmem<G>::list_bytes());  // bins' region
 
   const int64_t tid = gt - fi.tile_base;
   if (tid < 0 || tid >= g.ntiles) return;  // never for a consistent plan
@@ -391,7 +437,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
     key[e] = k;
     bin[e] = b;
   }
-  for (int i = threadIdx.x; i < G::NP / 16; i += NT) fa[i] = 0;  // both frontiers
+  for (int i = threadIdx.x; i < 3 * (G::NP / 32); i += NT) fa[i] = 0;  // both frontiers, risen bits
   if (bad) {  // tell non-finite from out-of-range, off the fast path
     for (int i = threadIdx.x; i < NBOX; i += NT) {
       const int lx = i % G::BX, ly = (i / G::BX) % G::BY, lz = i / (G::BX * G::BY);
@@ -409,8 +455,10 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   __syncthreads();
   phase_mark(P, 0, t0);
 
-  // 2. flags of the thread's y-segment; the first frontier is every point with a
-  //    lower same-bin neighbour
+  // 2. flags of the thread's y-segment.  With every subbin at 0, only a point with a
+  //    +1 constraint (a lower same-bin neighbour at a higher index, k >= 7) can rise
+  //    in the first sweep: those points are the first frontier, and the others are
+  //    queued when a lower neighbour rises.
   const SegPos sp = seg_pos<G>();
   const bool col_in = sp.lz < tb.cz && sp.lx < tb.cx;
   uint32_t active = 0;
@@ -432,43 +480,18 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
       }
     }
     cml[e] = (uint16_t)lo;
-    active |= (lo != 0) << j;
+    active |= ((lo >> 7) != 0) << j;
   }
   if (active) atomicOr(&fa[sp.b0 >> 5], active << (sp.b0 & 31));
-  __syncthreads();  // keys are dead from here on
-
-  // 3. tile-local least fixpoint, halo subbins 0
-  for (int e = threadIdx.x; e < G::E; e += NT) sv[e] = 0;
-  __syncthreads();
-  phase_mark(P, 1, t0);
-  bool over = false;
-  uint32_t risen = 0;
-  const int iters = frontier_fixpoint<G>(sv, cml, fa, fb, sp, 4 * G::NP + 64, over, risen);
-  if (threadIdx.x == 0) {
-    if (over) atomicOr(&P->status, kErrNotConverged);
-    atomicAdd(&P->fix_iters, (unsigned long long)iters);
-    atomicMax(&P->fix_iters_max, (unsigned long long)iters);
-  }
-  phase_mark(P, 2, t0);
-
-  // 4. write the state reruns need (cross-tile constraints are checked afterwards)
   const int64_t gz = tb.z0 + sp.lz, gx = tb.x0 + sp.lx;
-  if (col_in) {
-#pragma unroll 4
-    for (int j = 0; j < kSegment; ++j) {
-      if (sp.ly0 + j >= tb.cy) break;
-      const int e = sp.e0 + j * G::BXP;
-      const int64_t gi = gz * plane + (tb.y0 + sp.ly0 + j) * g.nx + gx;
-      s_glob[gi] = sv[e];
-      cm_glob[gi] = cml[e];
-      if (bins_out) bins_out[gi] = (int64_t)bin[e];
-    }
+  if (bins_out && col_in) {
+    for (int j = 0; j < kSegment && sp.ly0 + j < tb.cy; ++j)
+      bins_out[gz * plane + (tb.y0 + sp.ly0 + j) * g.nx + gx] = (int64_t)bin[sp.e0 + j * G::BXP];
   }
-  (void)risen;
-  __syncthreads();
-  phase_mark(P, 3, t0);
+  __syncthreads();  // keys are dead from here on
+  phase_mark(P, 1, t0);
 
-  // 5. bin record: DIFFNB_w, BIT_w, RZE_1; raw if that is not shorter
+  // 3. bin record: DIFFNB_w, BIT_w, RZE_1; raw if that is not shorter
   {
     const int n = tb.n, n32 = (n + 31) & ~31;
     const uint32_t raw = (uint32_t)n * W;
@@ -508,7 +531,35 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
       if (threadIdx.x == 0) sizes[tid] = len;
     }
   }
+  __syncthreads();  // bins, planes and the staged record are dead from here on
   phase_mark(P, 4, t0);
+
+  // 4. tile-local least fixpoint, halo subbins 0
+  for (int e = threadIdx.x; e < G::E; e += NT) sv[e] = 0;
+  __syncthreads();
+  bool over = false;
+  unsigned evals = 0, raises = 0;
+  const int iters = frontier_fixpoint<G>(sv, cml, fa, fb, rb, cnt, list, 4 * G::NP + 64, over, evals, raises);
+  if (threadIdx.x == 0) {
+    if (over) atomicOr(&P->status, kErrNotConverged);
+    atomicAdd(&P->fix_iters, (unsigned long long)iters);
+    atomicMax(&P->fix_iters_max, (unsigned long long)iters);
+  }
+  block_add2(evals, raises, &P->work[0]);
+  phase_mark(P, 2, t0);
+
+  // 5. write the state reruns need (cross-tile constraints are checked afterwards)
+  if (col_in) {
+#pragma unroll 4
+    for (int j = 0; j < kSegment; ++j) {
+      if (sp.ly0 + j >= tb.cy) break;
+      const int e = sp.e0 + j * G::BXP;
+      const int64_t gi = gz * plane + (tb.y0 + sp.ly0 + j) * g.nx + gx;
+      s_glob[gi] = sv[e];
+      cm_glob[gi] = cml[e];
+    }
+  }
+  phase_mark(P, 3, t0);
 }
 
 template <typename T, int ND>
@@ -516,10 +567,12 @@ struct RerunSmem {
   using G = TileGeom<T, ND>;
   // boundary points of a tile: an upper bound for the queue of risen boundary points
   static constexpr int QMAX = 2 * (G::TY * G::TX + (G::HZ ? G::TZ * G::TX + G::TZ * G::TY : G::TX + G::TY));
-  static constexpr size_t bytes() {
-    return (size_t)G::E * 4 + (((size_t)G::E * 2 + 15) & ~(size_t)15) + (size_t)2 * (G::NP / 32) * 4 +
-           (size_t)QMAX * 4 + 32;
-  }
+  static constexpr size_t up16(size_t v) { return (v + 15) & ~(size_t)15; }
+  static constexpr size_t CM = (size_t)G::E * 4;                      // subbins, then lower masks
+  static constexpr size_t BITS = CM + up16((size_t)G::E * 2);         // frontiers, risen bits, counters
+  static constexpr size_t LIST = BITS + up16(FixSmem<G>::bits_bytes());
+  static constexpr size_t QUEUE = LIST + FixSmem<G>::list_bytes();
+  static constexpr size_t bytes() { return QUEUE + (size_t)QMAX * 4 + 16; }
 };
 
 // Rerun of a tile whose halo subbins may have risen: the stored lower-neighbour
@@ -539,9 +592,12 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
   constexpr int NT = G::NT;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* sv = reinterpret_cast<uint32_t*>(smem);
-  uint16_t* cm = reinterpret_cast<uint16_t*>(smem + (size_t)G::E * 4);
-  uint32_t* fa0 = reinterpret_cast<uint32_t*>(smem + (size_t)G::E * 4 + (((size_t)G::E * 2 + 15) & ~(size_t)15));
-  uint32_t* queue = fa0 + 2 * (G::NP / 32);
+  uint16_t* cm = reinterpret_cast<uint16_t*>(smem + RS::CM);
+  uint32_t* fa0 = reinterpret_cast<uint32_t*>(smem + RS::BITS);
+  uint32_t* rb = fa0 + 2 * (G::NP / 32);
+  unsigned* cnt = rb + G::NP / 32;
+  uint16_t* flist = reinterpret_cast<uint16_t*>(smem + RS::LIST);
+  uint32_t* queue = reinterpret_cast<uint32_t*>(smem + RS::QUEUE);
   __shared__ uint32_t qn;
   // the first round (list == nullptr) visits every tile of the class
   const int64_t count = list ? (int64_t)B->count[cls] : ntile_cls;
@@ -589,7 +645,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
         cm[e] = (uint16_t)mb[u];
       }
     }
-    for (int i = threadIdx.x; i < G::NP / 16; i += NT) fa[i] = 0;
+    for (int i = threadIdx.x; i < 3 * (G::NP / 32); i += NT) fa0[i] = 0;  // frontiers, risen bits
     if (threadIdx.x == 0) qn = 0;
     __syncthreads();
     const SegPos sp = seg_pos<G>();
@@ -617,13 +673,15 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
     if (!__syncthreads_or(first != 0)) continue;  // every constraint into this tile holds
     phase_mark(P, 5, t0);
     bool over = false;
-    uint32_t risen = 0;
-    const int iters = frontier_fixpoint<G>(sv, cm, fa, fb, sp, 4 * G::NP + 64, over, risen);
+    unsigned evals = 0, raises = 0;
+    const int iters = frontier_fixpoint<G>(sv, cm, fa, fb, rb, cnt, flist, 4 * G::NP + 64, over, evals, raises);
+    const uint32_t risen = (rb[sp.b0 >> 5] >> (sp.b0 & 31)) & ((1u << kSegment) - 1u);
     if (threadIdx.x == 0) {
       if (over) atomicOr(&P->status, kErrNotConverged);
       atomicAdd(&P->fix_iters, (unsigned long long)iters);
       atomicMax(&P->fix_iters_max, (unsigned long long)iters);
     }
+    block_add2(evals, raises, &P->work[2]);
     phase_mark(P, 6, t0);
     // write the subbins that rose; queue the risen boundary points
     const int64_t gz = tb.z0 + sp.lz, gx = tb.x0 + sp.lx;
@@ -657,16 +715,15 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
         if (!((cm[e + G::off(dz_of(k), dy_of(k), dx_of(k))] >> kop) & 1u)) continue;
         const int64_t qz = pz + dz_of(k), qy = py + dy_of(k), qx = px + dx_of(k);
         if (*(volatile const uint32_t*)&s_glob[qz * plane + qy * g.nx + qx] >= sf + (k < 7 ? 1u : 0u)) continue;
-        const int64_t lt = ((qz / g.tz) * g.nty + qy / g.ty) * g.ntx + qx / g.tx;
-        const uint32_t bit = 1u << (lt & 31);
-        if (!(*(volatile const uint32_t*)&fi.dirty[lt >> 5] & bit)) atomicOr(&fi.dirty[lt >> 5], bit);
+        // a plain byte store: every writer stores the same value
+        reinterpret_cast<volatile uint8_t*>(fi.dirty)[((qz / g.tz) * g.nty + qy / g.ty) * g.ntx + qx / g.tx] = 1;
       }
     }
     __syncthreads();  // shared state is reused by the next item
   }
 }
 
-// Dirty bitmaps -> the next round's list, in table order (one block): per class
+// Dirty flags -> the next round's list, in table order (one block): per class
 // the count and first position, bits cleared.  The table is sorted by class, so the
 // list is grouped by class.  Counts a round for every field of the table; a field
 // past its round cap drops its dirty tiles and is reported as not converged.
@@ -696,9 +753,10 @@ __global__ void __launch_bounds__(NT) k_compact(const FieldInfo* __restrict__ F,
     if (w < total_words) {
       k = field_of_word(F, nf, w);
       uint32_t* dw = F[k].dirty + (w - F[k].word_base);
-      bits = *dw;
-      if (bits) {
+      const uint32_t v = *dw;  // four byte flags
+      if (v) {
         *dw = 0u;
+        bits = (v & 0xffu ? 1u : 0u) | (v & 0xff00u ? 2u : 0u) | (v & 0xff0000u ? 4u : 0u) | (v & 0xff000000u ? 8u : 0u);
         if ((long long)F[k].P->rounds > F[k].round_cap) {
           atomicOr(&F[k].P->status, kErrNotConverged);
           capped = 1;
@@ -710,7 +768,7 @@ __global__ void __launch_bounds__(NT) k_compact(const FieldInfo* __restrict__ F,
     unsigned int tot;
     unsigned int pos = block_exclusive_scan<NT, unsigned int>(n, tmp, &tot) + run;
     if (n) {
-      const int64_t t0 = F[k].tile_base + 32 * (w - F[k].word_base);
+      const int64_t t0 = F[k].tile_base + 4 * (w - F[k].word_base);
       for (uint32_t b = bits; b; b &= b - 1) list[pos++] = (uint32_t)(t0 + __ffs(b) - 1);
       atomicAdd(&cnt[class_of_geometry(F[k].g)], n);
       if (field_counts) atomicAdd(&field_counts[k], n);

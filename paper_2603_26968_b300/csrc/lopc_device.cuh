@@ -45,7 +45,26 @@ struct Params {
   unsigned long long fix_iters;   // sum over tile runs of fixpoint sweeps
   unsigned long long fix_iters_max;
   unsigned long long phase[8];    // SM cycles spent per kernel phase (block-summed, for measurement)
+  unsigned long long work[4];     // fixpoint point evaluations and raises: tile pass, reruns
 };
+
+// Adds a and b, summed over the block, to dst[0] and dst[1] (all threads call it).
+__device__ __forceinline__ void block_add2(unsigned long long a, unsigned long long b, unsigned long long* dst) {
+  __shared__ unsigned long long acc[2];
+  if (threadIdx.x == 0) acc[0] = acc[1] = 0;
+  __syncthreads();
+  a = __reduce_add_sync(0xffffffffu, (unsigned)a);
+  b = __reduce_add_sync(0xffffffffu, (unsigned)b);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&acc[0], a);
+    atomicAdd(&acc[1], b);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(&dst[0], acc[0]);
+    atomicAdd(&dst[1], acc[1]);
+  }
+}
 
 // Adds the cycles since `t0` to phase counter `k` (thread 0 of the block only).
 __device__ __forceinline__ void phase_mark(Params* P, int k, long long& t0) {
@@ -368,13 +387,13 @@ struct FieldInfo {
   int64_t* bins_out;      // optional export of the bins (may be null)
   uint64_t* size_out;     // device: this field's stream length (may be null)
   int* status_out;        // device: this field's LOPC status (may be null)
-  uint32_t* dirty;        // tiles to rerun next round: one bit per tile, ceil(ntiles / 32) words
+  uint32_t* dirty;        // tiles to rerun next round: one byte flag per tile, ceil(ntiles / 4) words
   int64_t tile_base;      // first tile in the table's tile index space
   int64_t word_base;      // first dirty word in the table's flat word space
   int64_t round_cap;
 };
 
-__host__ __device__ inline int64_t dirty_words(int64_t ntiles) { return (ntiles + 31) / 32; }
+__host__ __device__ inline int64_t dirty_words(int64_t ntiles) { return (ntiles + 3) / 4; }
 
 // Field class of a table entry: 0 = f32 2D, 1 = f32 3D, 2 = f64 2D, 3 = f64 3D.
 __host__ __device__ inline int class_of_geometry(const Geometry& g) {

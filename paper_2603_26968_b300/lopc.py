@@ -78,6 +78,7 @@ def lib():
         L.lopc_last_stats.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.lopc_last_fixpoint_stats.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.lopc_last_phase_cycles.argtypes = [C.POINTER(C.c_int64), C.c_int]
+        L.lopc_last_fixpoint_work.argtypes = [C.POINTER(C.c_int64), C.c_int]
         L.lopc_profile_enable.argtypes = [C.c_int]
         L.lopc_profile_reset.argtypes = []
         L.lopc_profile_read.argtypes = [C.POINTER(C.c_char_p), C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int]
@@ -235,6 +236,13 @@ def last_phase_cycles() -> list:
     a = (C.c_int64 * 8)()
     lib().lopc_last_phase_cycles(a, 8)
     return [int(v) for v in a]
+
+
+def last_fixpoint_work() -> dict:
+    """Fixpoint point evaluations and raises of the last compression (pass, reruns)."""
+    v = (C.c_int64 * 4)()
+    lib().lopc_last_fixpoint_work(v, 4)
+    return {"pass_evals": v[0], "pass_raises": v[1], "rerun_evals": v[2], "rerun_raises": v[3]}
 
 
 def compress_status(x: torch.Tensor, eb: float, mode: int = NOA, out_cap: Optional[int] = None,
