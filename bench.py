@@ -1,8 +1,14 @@
 """Benchmark of the LOPC hot path on B300.
 
-One step = compress + decompress of a 3D float32 512^3 field (seeded sum of 256
-Gaussian bumps plus 3-octave value noise; NOA bound 1e-3 x range) through the C ABI,
-with inputs resident in HBM.  Prints ONE JSON line (rank 0).
+Headline step = compress + decompress of a 3D float32 512^3 field (seeded sum of
+256 Gaussian bumps plus 3-octave value noise; NOA bound 1e-3 x range) through the C
+ABI, inputs resident in HBM, as the library runs it by default (one CUDA graph per
+call whose repair loop is a device-driven while-node).  Also measured in the same
+run: the per-kernel split (a second pass with per-launch CUDA events), the other
+bounds of the same field, end to end with host buffers, the batched workload (64
+mixed fields: one batched launch vs one launch sequence per field, autotuned), the
+serving workload (Poisson arrivals, p50/p99 latency) and the CPU oracle.  Prints
+ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -15,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing as mp
 import os
 import subprocess
 import sys
@@ -27,6 +34,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "compress/decompress GB/s (1 B300, bit-exact) & % HBM peak; batched vs per-field; p50/p99"
+
+# DRAM bytes (read + write) of one tile-pass launch on the headline workload, from
+# the ncu capture summarised in profiles/ (None until a capture of the current kernel).
+PASS_TRAFFIC = None
 
 
 def peaks():
@@ -93,9 +104,17 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_input(n: int, seed: int):
+# ------------------------------------------------------------ input generation
+# (module-level so that spawned pool workers can run them)
+
+def make_headline(n: int, seed: int):
     from paper_2603_26968_b300 import synth as S
     return S.make_field(S.spec_3d_f32(seed=seed, n=n))
+
+
+def make_batch_field(spec):
+    from paper_2603_26968_b300 import synth as S
+    return S.make_field(spec)
 
 
 def cpu_oracle_sample(x: np.ndarray, eb: float, sub: int):
@@ -113,7 +132,7 @@ def cpu_oracle_sample(x: np.ndarray, eb: float, sub: int):
 def run_reference(args, rank):
     if rank != 0:
         return
-    x = make_input(args.size, seed=1)
+    x = make_headline(args.size, seed=1)
     sub = args.cpu_sample
     for _ in range(args.warmup):
         cpu_oracle_sample(x, args.eb, sub)
@@ -136,6 +155,88 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ legs
+
+def batch_leg(torch, lopc, fields_np, specs, flush, args):
+    """64 mixed fields: one launch sequence per field vs one batched launch."""
+    from paper_2603_26968_b300 import autotune
+    dev = flush.device
+    xs = [torch.from_numpy(a).to(dev) for a in fields_np]
+    ebs = [float(s.eb) for s in specs]
+    nbytes = sum(a.nbytes for a in fields_np)
+    default = lopc.tune_get()
+    singles = [lopc.BatchCompress([x], [e]) for x, e in zip(xs, ebs)]
+    batch = lopc.BatchCompress(xs, ebs)
+    st = torch.cuda.current_stream()
+
+    def run_singles():
+        for b in singles:
+            b.launch()
+
+    def timed(run, reps):
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            run()
+            b.record(st)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return float(np.median(out))
+
+    run_singles()
+    batch.launch()
+    torch.cuda.synchronize()
+    per_field_ms = timed(run_singles, args.batch_reps)
+    batch_default_ms = timed(batch.launch, args.batch_reps)
+    key = autotune.device_key(batch.descs)
+    tuned = autotune.load(key) if not args.retune else None
+    if tuned is None:
+        tuned = autotune.tune(batch.launch, autotune.classes_of(batch.descs), reps=args.batch_reps)
+        try:
+            autotune.save(key, {k: v for k, v in tuned.items() if k != "trials"})
+        except OSError:
+            pass
+    lopc.tune_set(tuned["rerun_blocks_per_sm"])
+    batch.launch()
+    torch.cuda.synchronize()
+    batch_ms = timed(batch.launch, args.batch_reps)
+    # identical output: every field's batched stream equals its own launch's stream
+    bs, bst = batch.results()
+    identical = all(s == 0 for s in bst)
+    for b, s in zip(singles, bs):
+        o, ss = b.results()
+        identical = identical and ss[0] == 0 and torch.equal(o[0], s)
+    lopc.tune_set(default)
+    del singles, batch, xs
+    torch.cuda.empty_cache()
+    classes = autotune.signature([lopc.make_desc(s.shape, s.dtype, lopc.NOA, s.eb) for s in specs])
+    return {"fields": len(specs), "bytes": int(nbytes), "class_signature": classes,
+            "per_field_ms": per_field_ms, "per_field_gbs": nbytes / (per_field_ms * 1e-3) / 1e9,
+            "batched_default_ms": batch_default_ms, "batched_ms": batch_ms,
+            "batched_gbs": nbytes / (batch_ms * 1e-3) / 1e9, "speedup": per_field_ms / batch_ms,
+            "tuned_rerun_blocks_per_sm": tuned["rerun_blocks_per_sm"], "default_rerun_blocks_per_sm": list(default),
+            "identical_output": bool(identical),
+            "timing": f"median of {args.batch_reps}, L2 flushed before each; per-field = one async launch "
+                      f"sequence (cached graph) per field back to back on one stream"}
+
+
+def serve_leg(torch, lopc, args):
+    from paper_2603_26968_b300 import serve, synth_gpu as SG
+    specs = SG.serve_requests(args.seed, args.serve_rate, args.serve_seconds)
+    offered = SG.offered_load(specs, args.serve_seconds) / 1e9
+    srv = serve.Server(serve.default_budget(), max_fields=1024, rounds_per_step=args.serve_rounds)
+    # warm the engine's kernels on one small request (not counted)
+    srv.run(SG.serve_requests(args.seed + 99, 1000.0, 0.01, min_bytes=1e6, max_bytes=4e6)[:2])
+    rep = srv.run(specs)
+    srv.close()
+    out = serve.summary(rep, offered)
+    out.update({"rate_per_s": args.serve_rate, "seconds": args.serve_seconds,
+                "rounds_per_step": args.serve_rounds})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -144,9 +245,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=512)
     ap.add_argument("--eb", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--extra-ebs", default="1e-2,1e-4")
     ap.add_argument("--cpu-sample", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--retune", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rounds", type=int, default=1)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -156,6 +266,13 @@ def main():
         run_reference(args, rank)
         return
 
+    # host generators run in a spawned pool, started before any CUDA call
+    from paper_2603_26968_b300 import synth as S
+    specs = [] if args.no_batch else S.spec_batch(args.seed, args.batch_count)
+    pool = mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2) - 1)))
+    head_async = pool.apply_async(make_headline, (args.size, args.seed + rank))
+    batch_async = pool.map_async(make_batch_field, specs) if specs else None
+
     import torch
     from paper_2603_26968_b300 import lopc
     torch.cuda.set_device(local)
@@ -164,7 +281,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    x_np = make_input(args.size, seed=1 + rank)
+    x_np = head_async.get()
     nbytes = x_np.nbytes
     dev = torch.device("cuda", local)
     x = torch.from_numpy(x_np).to(dev)
@@ -176,21 +293,14 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (126 MB)
     stream = torch.cuda.current_stream()
 
-    def step(eb):
-        st = lopc.compress(x, eb, lopc.NOA, out=out, workspace=ws)
-        lopc.decompress(st, out=xhat, desc=d, workspace=dws)
-        return st
-
-    def timed(eb, k, w, profile=False):
+    def timed(eb, k, w):
         for _ in range(w):
-            step(eb)
+            st = lopc.compress(x, eb, lopc.NOA, out=out, workspace=ws)
+            lopc.decompress(st, out=xhat, desc=d, workspace=dws)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         times, tc, td = [], [], []
-        if profile:
-            lopc.profile_reset()
-            lopc.profile_enable(True)
         size = 0
         for _ in range(k):
             flush.zero_()                       # L2 flush between timed steps
@@ -205,16 +315,26 @@ def main():
             tc.append(e0.elapsed_time(e1))
             td.append(e1.elapsed_time(e2))
             times.append(e0.elapsed_time(e2))
-        prof = lopc.profile_read() if profile else {}
-        if profile:
-            lopc.profile_enable(False)
         if dist:
             dist.barrier()
-        return np.array(times), np.array(tc), np.array(td), size, prof
+        return np.array(times), np.array(tc), np.array(td), size
 
-    # headline: the configured bound, with clocks and per-kernel events
+    def profiled(eb, k):
+        """Per-kernel CUDA-event timings (direct launches, host-driven rounds)."""
+        lopc.profile_reset()
+        lopc.profile_enable(True)
+        for _ in range(k):
+            flush.zero_()
+            st = lopc.compress(x, eb, lopc.NOA, out=out, workspace=ws)
+            lopc.decompress(st, out=xhat, desc=d, workspace=dws)
+        torch.cuda.synchronize()
+        prof = lopc.profile_read()
+        lopc.profile_enable(False)
+        return prof
+
+    # headline: the configured bound as the library runs it (graphs), with clocks
     with ClockSampler(local) as clk:
-        times, tc, td, ssize, prof = timed(args.eb, args.steps, args.warmup, profile=True)
+        times, tc, td, ssize = timed(args.eb, args.steps, args.warmup)
     ms_step = float(times.mean())
     if dist:
         t = torch.tensor([ms_step], device=dev)
@@ -222,51 +342,63 @@ def main():
         ms_step = float(t.item())
     rounds, runs = lopc.last_stats()
     sweeps, sweeps_max = lopc.last_fixpoint_stats()
+    work = lopc.last_fixpoint_work()
     phases = dict(zip(["pass_load", "pass_flags", "pass_fixpoint", "pass_writeback", "pass_bin_record",
                        "rerun_load", "rerun_fixpoint", "unused"], lopc.last_phase_cycles()))
     hbm, peak_kind = peaks()
     cr = nbytes / ssize
-    w = 4
     algo_comp = nbytes * 2 + ssize                 # NOA: range pass + tile pass read x; write stream
     algo_dec = ssize + nbytes
     comp_gbs = nbytes / (tc.mean() * 1e-3) / 1e9
     dec_gbs = nbytes / (td.mean() * 1e-3) / 1e9
 
-    # per-kernel table and the dominant kernel's roofline
+    # per-kernel split, and the dominant kernel's roofline (separate pass, same workload)
+    prof_steps = 2
+    prof = profiled(args.eb, prof_steps)
+    w = 4
     npts = nbytes // w
     # algorithmic bytes per step of each kernel: what the method must move (range and
     # tile pass read x; the subbin encoder writes its records; decode reads the stream
-    # and writes x_hat); a rerun must read the subbins and masks of the tiles it reruns
+    # and writes x_hat; pack reads and writes the records)
     algo_bytes = {"range": nbytes, "tile_pass": nbytes, "encode_subbins": ssize, "decode": ssize + nbytes,
                   "pack": 2 * ssize}
     kern = {}
     for name, (launches, total_ms) in prof.items():
-        kern[name] = {"launches": launches, "total_ms": total_ms, "ms_per_launch": total_ms / max(1, launches)}
-    dom = max(kern.items(), key=lambda kv: kv[1]["total_ms"])[0] if kern else None
+        kern[name] = {"launches_per_step": launches / prof_steps, "ms_per_step": total_ms / prof_steps,
+                      "ms_per_launch": total_ms / max(1, launches)}
+    tot_ms = sum(v["ms_per_step"] for v in kern.values())
+    for v in kern.values():
+        v["share"] = v["ms_per_step"] / tot_ms if tot_ms else None
+    dom = max(kern.items(), key=lambda kv: kv[1]["ms_per_step"])[0] if kern else None
     roof = None
     if dom:
-        per_step_launches = kern[dom]["launches"] / args.steps
+        per_step = kern[dom]["launches_per_step"]
         if dom in algo_bytes:
-            bytes_per_launch = algo_bytes[dom] / per_step_launches
+            bytes_per_launch = algo_bytes[dom] / per_step
         elif dom == "tile_rerun":
             # a rerun reads the subbins (4 B) and lower masks (2 B) of its tiles' points
-            bytes_per_launch = (runs - npts / 4096) * 4096 * 6 / max(1, rounds)
+            bytes_per_launch = max(0, runs - npts / 4096) * 4096 * 6 / max(1, per_step)
         else:
             bytes_per_launch = 0
         achieved = bytes_per_launch / (kern[dom]["ms_per_launch"] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_kind": f"{peak_kind} (copy)"}
-    gpu_launches = int(sum(v["launches"] for v in kern.values()))
+                "frac": achieved / hbm, "traffic": PASS_TRAFFIC if dom == "tile_pass" else None,
+                "peak_kind": f"{peak_kind} (copy)", "algorithmic_bytes_per_launch": bytes_per_launch,
+                "timing": "CUDA events around each launch on its stream, in a second pass of the same workload"}
+    launches_per_step = sum(v["launches_per_step"] for v in kern.values())
+    gpu_launches = int(round(launches_per_step * args.steps))
 
-    # other bounds of the same config
+    # other bounds of the same field
     extra = {}
     for eb in [float(v) for v in args.extra_ebs.split(",") if v]:
-        t2, c2, d2, s2, _ = timed(eb, max(1, args.steps // 2), 1)
+        t2, c2, d2, s2 = timed(eb, max(2, args.steps // 2), 2)
         r2, n2 = lopc.last_stats()
         f2 = lopc.last_fixpoint_stats()
-        extra[f"{eb:g}"] = {"fixpoint_sweeps": f2[0], "fixpoint_sweeps_max": f2[1], "ms_per_step": float(t2.mean()), "compress_gbs": nbytes / (c2.mean() * 1e-3) / 1e9,
+        extra[f"{eb:g}"] = {"ms_per_step": float(t2.mean()), "compress_ms": float(c2.mean()),
+                            "compress_gbs": nbytes / (c2.mean() * 1e-3) / 1e9,
                             "decompress_gbs": nbytes / (d2.mean() * 1e-3) / 1e9, "cr": nbytes / s2,
-                            "repair_rounds": r2, "tile_runs": n2}
+                            "repair_rounds": r2, "tile_runs": n2, "fixpoint_sweeps": f2[0],
+                            "fixpoint_sweeps_max": f2[1], "fixpoint_work": lopc.last_fixpoint_work()}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     hx = torch.from_numpy(x_np).pin_memory()
@@ -289,6 +421,17 @@ def main():
             e2e_t.append(time.perf_counter() - t0)
         h2d, d2h = nbytes + n, n + nbytes
     e2e_gbs = nbytes / float(np.mean(e2e_t)) / 1e9
+    del ws, dws, out, xhat
+
+    batch = None
+    if batch_async is not None:
+        torch.cuda.empty_cache()
+        batch = batch_leg(torch, lopc, batch_async.get(), specs, flush, args)
+    pool.close()
+    serving = None
+    if not args.no_serve:
+        torch.cuda.empty_cache()
+        serving = serve_leg(torch, lopc, args)
 
     # aggregate over ranks (replicas): total bytes / max time
     value = world * nbytes / (ms_step * 1e-3) / 1e9
@@ -303,17 +446,23 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"3d_f32_{args.size}^3 (256 Gaussian bumps + 3-octave value noise), NOA eb "
-                                   f"{args.eb:g}; step = compress + decompress", "field_bytes": nbytes,
-                       "parallelism": "replicas" if world > 1 else "single", "l2": "flushed between steps (256 MB write); input 512 MB > L2"},
-            "compress": {"gbs": comp_gbs, "ms": float(tc.mean()), "hbm_frac_algorithmic": algo_comp / (tc.mean() * 1e-3) / 1e9 / hbm,
+                                   f"{args.eb:g}; step = compress + decompress (GB/s of uncompressed input)",
+                       "field_bytes": nbytes, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed between steps (256 MB write); input 512 MB > L2"},
+            "compress": {"gbs": comp_gbs, "ms": float(tc.mean()),
+                         "hbm_frac_algorithmic": algo_comp / (tc.mean() * 1e-3) / 1e9 / hbm,
                          "input_frac": comp_gbs / hbm, "cr": cr, "repair_rounds": rounds, "tile_runs": runs,
-                         "fixpoint_sweeps": sweeps, "fixpoint_sweeps_max": sweeps_max, "phase_cycles": phases},
-            "decompress": {"gbs": dec_gbs, "ms": float(td.mean()), "hbm_frac_algorithmic": algo_dec / (td.mean() * 1e-3) / 1e9 / hbm},
+                         "fixpoint_sweeps": sweeps, "fixpoint_sweeps_max": sweeps_max, "fixpoint_work": work,
+                         "phase_cycles": phases},
+            "decompress": {"gbs": dec_gbs, "ms": float(td.mean()),
+                           "hbm_frac_algorithmic": algo_dec / (td.mean() * 1e-3) / 1e9 / hbm},
             "other_bounds": extra,
             "kernels": kern,
             "roofline": roof,
             "gpu_launches": gpu_launches,
             "e2e": {"value": e2e_gbs, "unit": "GB/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "batched": batch,
+            "serving": serving,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
         }
