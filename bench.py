@@ -320,9 +320,12 @@ def main():
         return np.array(times), np.array(tc), np.array(td), size
 
     def profiled(eb, k):
-        """Per-kernel CUDA-event timings (direct launches, host-driven rounds)."""
+        """Per-kernel CUDA-event timings (direct launches, host-driven rounds) and
+        decode phase cycles."""
         lopc.profile_reset()
         lopc.profile_enable(True)
+        lopc.decode_phase_enable(True)
+        lopc.decode_phase_read()
         for _ in range(k):
             flush.zero_()
             st = lopc.compress(x, eb, lopc.NOA, out=out, workspace=ws)
@@ -330,7 +333,9 @@ def main():
         torch.cuda.synchronize()
         prof = lopc.profile_read()
         lopc.profile_enable(False)
-        return prof
+        dph = {a: v // k for a, v in lopc.decode_phase_read().items()}
+        lopc.decode_phase_enable(False)
+        return prof, dph
 
     # headline: the configured bound as the library runs it (graphs), with clocks
     with ClockSampler(local) as clk:
@@ -354,7 +359,7 @@ def main():
 
     # per-kernel split, and the dominant kernel's roofline (separate pass, same workload)
     prof_steps = 2
-    prof = profiled(args.eb, prof_steps)
+    prof, dec_phases = profiled(args.eb, prof_steps)
     w = 4
     npts = nbytes // w
     # algorithmic bytes per step of each kernel: what the method must move (range and
@@ -455,7 +460,8 @@ def main():
                          "fixpoint_sweeps": sweeps, "fixpoint_sweeps_max": sweeps_max, "fixpoint_work": work,
                          "phase_cycles": phases},
             "decompress": {"gbs": dec_gbs, "ms": float(td.mean()),
-                           "hbm_frac_algorithmic": algo_dec / (td.mean() * 1e-3) / 1e9 / hbm},
+                           "hbm_frac_algorithmic": algo_dec / (td.mean() * 1e-3) / 1e9 / hbm,
+                           "phase_cycles": dec_phases},
             "other_bounds": extra,
             "kernels": kern,
             "roofline": roof,

@@ -182,6 +182,14 @@ LOPC_API int lopc_last_phase_cycles(int64_t* cycles, int n);
  * the reruns.  Copies min(n, 4) values and returns 4. */
 LOPC_API int lopc_last_fixpoint_work(int64_t* out, int n);
 
+/* Measurement aid: while enabled, the decoder adds up SM cycles per phase over all
+ * blocks of the current device: 0 bin record RZE, 1 bin planes + prefix sum, 2 bin
+ * range and lowest-value cache, 3 subbin RZE_1, 4 subbin RZE_w, 5 planes + values.
+ * lopc_decode_phase_read synchronises the device, copies min(n, 8) sums, resets them
+ * and returns 8 (or a negative status). */
+LOPC_API int lopc_decode_phase_enable(int on);
+LOPC_API int lopc_decode_phase_read(int64_t* out, int n);
+
 /* Per-kernel timing for measurement: while enabled, every kernel the library
  * launches is bracketed by CUDA events recorded on the launching stream, and the
  * elapsed times are added up per kernel when the call returns.  Off by default;

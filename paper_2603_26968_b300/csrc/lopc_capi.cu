@@ -1188,6 +1188,22 @@ int lopc_last_phase_cycles(int64_t* cycles, int n) {
   return 8;
 }
 
+int lopc_decode_phase_enable(int on) {
+  const int v = on != 0;
+  CK(cudaMemcpyToSymbol(g_dec_phase_on, &v, sizeof(int)));
+  return LOPC_OK;
+}
+
+int lopc_decode_phase_read(int64_t* out, int n) {
+  unsigned long long h[8] = {};
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpyFromSymbol(h, g_dec_phase, sizeof(h)));
+  for (int k = 0; k < n && k < 8; ++k) out[k] = (int64_t)h[k];
+  const unsigned long long z[8] = {};
+  CK(cudaMemcpyToSymbol(g_dec_phase, z, sizeof(z)));
+  return 8;
+}
+
 int lopc_last_fixpoint_work(int64_t* out, int n) {
   for (int k = 0; k < n && k < 4; ++k) out[k] = g_last_work[k];
   return 4;

@@ -25,11 +25,28 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
 
 // Bit-plane transpose of n32 words (a multiple of 32): plane k (k = 0 least
 // significant) is n32/32 u32 words, bit j of word g being bit k of word 32g+j.
-// `word(i)` supplies input word i (zero for padding).  One warp per group of 32.
+// `word(i)` supplies input word i (zero for padding).  One warp per group of 32
+// words; with a plane length that is a multiple of 4 a warp takes four groups at a
+// time and each lane stores its four plane words in one 16-byte access (the lanes'
+// words lie a plane apart, on the same banks, so this cuts the conflicts by four).
 template <int NT, int W, typename WordFn>
 __device__ __forceinline__ void bit_transpose(int n32, WordFn word, uint32_t* planes) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int G = n32 >> 5;
+  if ((G & 3) == 0) {
+    for (int g = 4 * wid; g < G; g += 4 * (NT / 32)) {
+      uint32_t lo[4], hi[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint64_t v = word(32 * (g + u) + lane);
+        lo[u] = warp_transpose32((uint32_t)v);
+        hi[u] = W == 8 ? warp_transpose32((uint32_t)(v >> 32)) : 0u;
+      }
+      *reinterpret_cast<uint4*>(&planes[lane * G + g]) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      if (W == 8) *reinterpret_cast<uint4*>(&planes[(32 + lane) * G + g]) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    }
+    return;
+  }
   for (int g = wid; g < G; g += NT / 32) {
     const uint64_t v = word(32 * g + lane);
     planes[lane * G + g] = warp_transpose32((uint32_t)v);
@@ -42,6 +59,21 @@ template <int NT, int W, typename EmitFn>
 __device__ __forceinline__ void bit_untranspose(int n32, const uint32_t* planes, EmitFn emit) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int G = n32 >> 5;
+  if ((G & 3) == 0) {
+    for (int g = 4 * wid; g < G; g += 4 * (NT / 32)) {
+      const uint4 a = *reinterpret_cast<const uint4*>(&planes[lane * G + g]);
+      uint4 b = make_uint4(0u, 0u, 0u, 0u);
+      if (W == 8) b = *reinterpret_cast<const uint4*>(&planes[(32 + lane) * G + g]);
+      const uint32_t la[4] = {a.x, a.y, a.z, a.w}, lb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t lo = warp_transpose32(la[u]);
+        const uint32_t hi = W == 8 ? warp_transpose32(lb[u]) : 0u;
+        emit(32 * (g + u) + lane, (uint64_t)lo | ((uint64_t)hi << 32));
+      }
+    }
+    return;
+  }
   for (int g = wid; g < G; g += NT / 32) {
     const uint32_t lo = warp_transpose32(planes[lane * G + g]);
     const uint32_t hi = W == 8 ? warp_transpose32(planes[(32 + lane) * G + g]) : 0u;
@@ -254,16 +286,27 @@ __device__ bool rze_decode(const uint8_t* in, uint32_t in_len, uint32_t L, uint8
   const int t = threadIdx.x, lane = t & 31;
   if (in_len < l2) return false;  // uniform
   const uint8_t* m2 = in;
-  // level-1 bitmap from level 2 (each thread ranks its bytes from scratch: l2 is small)
-  uint32_t nk1 = 0;
-  for (uint32_t i = 0; i < l2; ++i) nk1 += __popc((uint32_t)m2[i]);
+  // level-1 bitmap from level 2: warp 0 ranks the level-2 bytes (prefix popcounts,
+  // 32 bytes per step), then every level-1 byte is one lookup
+  if (t < 32) {
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < l2; base += 32) {
+      const uint32_t i = base + t;
+      const uint32_t c = i < l2 ? __popc((uint32_t)m2[i]) : 0u;
+      uint32_t tot;
+      const uint32_t ex = warp_exclusive_scan(c, &tot);
+      if (i < l2) w.pre[i] = carry + ex;
+      carry += tot;
+    }
+    if (t == 0) w.pre[l2] = carry;
+  }
+  __syncthreads();
+  const uint32_t nk1 = w.pre[l2];
   if (!tail_clear(m2, l1) || l2 + nk1 > in_len) return false;  // uniform
   for (uint32_t j = t; j < ((l1 + 3) & ~3u); j += NT) {
     uint8_t v = 0;
     if (j < l1) {
-      uint32_t r = 0;
-      for (uint32_t i = 0; i < (j >> 3); ++i) r += __popc((uint32_t)m2[i]);
-      r += __popc((uint32_t)m2[j >> 3] & ((2u << (j & 7)) - 1u));
+      const uint32_t r = w.pre[j >> 3] + __popc((uint32_t)m2[j >> 3] & ((2u << (j & 7)) - 1u));
       v = r ? in[l2 + r - 1] : 0;
     }
     w.m1[j] = v;

@@ -188,6 +188,9 @@ struct TileGeom {
   static_assert(TX >= 16, "a half warp spans one x-run");
   __device__ static constexpr int off(int dz, int dy, int dx) { return dz * PP + dy * BXP + dx; }
   __device__ static constexpr int entry(int lz, int ly, int lx) { return (lz + HZ) * PP + (ly + 1) * BXP + lx + 1; }
+  // linear index of a tile point (masks are kept for the tile's own points only)
+  __device__ static constexpr int lin(int lz, int ly, int lx) { return (lz * TY + ly) * TX + lx; }
+  __device__ static constexpr int loff(int dz, int dy, int dx) { return (dz * TY + dy) * TX + dx; }
   // owner thread of a point, and the point's bit in the frontier (thread-major)
   __device__ static constexpr int owner(int lz, int ly, int lx) { return (lz * SEGY + ly / kSegment) * TX + lx; }
   __device__ static constexpr int fbit(int lz, int ly, int lx) { return owner(lz, ly, lx) * kSegment + ly % kSegment; }
@@ -225,6 +228,89 @@ __device__ __forceinline__ uint32_t ld_acquire_u8(const uint8_t* p) {
   return v;
 }
 
+// Asynchronous global -> shared copies (cp.async); a false predicate writes zeros and
+// reads nothing (the source must still be a valid address).
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool pred) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(pred ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool pred) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(pred ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Asynchronous copy of a tile's box (the tile and a one-point halo; 2D tiles have no
+// z halo) of `src` (row-major field of nz x ny x nx elements of `Word`) into shared
+// memory at `dst` (entry layout of G).  Rows are walked as (row, column) with one
+// row base per row: the 16 interior columns go to 16 lanes, the two halo columns
+// are a second loop.  Absent points read nothing and are zero.  The caller waits.
+template <typename G, typename Word>
+__device__ __forceinline__ void load_box_async(Word* dst, const Word* __restrict__ src, const Geometry& g,
+                                               const TileBox& tb) {
+  static_assert(G::TX == 16 || G::TX == 64, "interior columns are whole lane groups");
+  constexpr int NT = G::NT, ROWS = G::BZ * G::BY;
+  constexpr int CW = G::TX < 32 ? G::TX : 32;  // lanes per row
+  constexpr int RPP = NT / CW;                 // rows per pass
+  const int64_t plane = g.ny * g.nx;
+  const int c = threadIdx.x % CW;
+  for (int r = threadIdx.x / CW; r < ROWS; r += RPP) {
+    const int ly = r % G::BY, lz = r / G::BY;
+    const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1;
+    const bool row_in = gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny;
+    const Word* row = src + (row_in ? gz * plane + gy * g.nx : 0);
+    Word* drow = dst + lz * G::PP + ly * G::BXP;
+#pragma unroll
+    for (int lx = c; lx < G::TX; lx += CW) {
+      const int64_t gx = tb.x0 + lx;
+      const bool in = row_in && gx < g.nx;
+      if (sizeof(Word) == 4)
+        cp_async4(&drow[lx + 1], in ? row + gx : src, in);
+      else
+        cp_async8(&drow[lx + 1], in ? row + gx : src, in);
+    }
+  }
+  // the halo columns x0 - 1 and x0 + TX
+  for (int i = threadIdx.x; i < 2 * ROWS; i += NT) {
+    const int r = i >> 1, side = i & 1;
+    const int ly = r % G::BY, lz = r / G::BY;
+    const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1;
+    const int64_t gx = side ? tb.x0 + G::TX : tb.x0 - 1;
+    const bool in = gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx >= 0 && gx < g.nx;
+    Word* d = dst + lz * G::PP + ly * G::BXP + (side ? G::TX + 1 : 0);
+    if (sizeof(Word) == 4)
+      cp_async4(d, in ? src + gz * plane + gy * g.nx + gx : src, in);
+    else
+      cp_async8(d, in ? src + gz * plane + gy * g.nx + gx : src, in);
+  }
+}
+
+// Calls fn(e, in) for every entry e of a tile's box (in: the point is in the field),
+// walking rows as load_box_async does.
+template <typename G, typename Fn>
+__device__ __forceinline__ void for_box(const Geometry& g, const TileBox& tb, Fn fn) {
+  constexpr int NT = G::NT, ROWS = G::BZ * G::BY;
+  constexpr int CW = G::TX < 32 ? G::TX : 32;
+  constexpr int RPP = NT / CW;
+  const int c = threadIdx.x % CW;
+  for (int r = threadIdx.x / CW; r < ROWS; r += RPP) {
+    const int ly = r % G::BY, lz = r / G::BY;
+    const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1;
+    const bool row_in = gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny;
+    const int e0 = lz * G::PP + ly * G::BXP;
+#pragma unroll
+    for (int lx = c; lx < G::TX; lx += CW) fn(e0 + lx + 1, row_in && tb.x0 + lx < g.nx);
+  }
+  for (int i = threadIdx.x; i < 2 * ROWS; i += NT) {
+    const int r = i >> 1, side = i & 1;
+    const int ly = r % G::BY, lz = r / G::BY;
+    const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1;
+    const int64_t gx = side ? tb.x0 + G::TX : tb.x0 - 1;
+    fn(lz * G::PP + ly * G::BXP + (side ? G::TX + 1 : 0),
+       gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx >= 0 && gx < g.nx);
+  }
+}
+
 // Decodes a frontier bit (fbit order) into local coordinates.
 template <typename G>
 __device__ __forceinline__ void point_of_bit(int q, int& lz, int& ly, int& lx) {
@@ -252,8 +338,8 @@ struct FixSmem {
 // sweep costs about one evaluation per thread.  Raised subbins are visible to the
 // rest of the sweep at once; a neighbour read before it rose is queued again by
 // that rise.  Chaotic relaxation from lower bounds reaches the unique least fixpoint
-// (Sec. III-E) whatever the schedule.  `cml[e]` holds the lower-neighbour bits of
-// entry e; `fa` holds the first frontier, `fb` and `rb` must be clear; `rb` receives
+// (Sec. III-E) whatever the schedule.  `cml[o]` holds the lower-neighbour bits of
+// tile point o (linear order); `fa` holds the first frontier, `fb` and `rb` must be clear; `rb` receives
 // the points that rose.  Returns the number of sweeps.
 template <typename G>
 __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint16_t* cml, uint32_t* fa, uint32_t* fb,
@@ -299,7 +385,8 @@ __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint16_t* c
       int lz, ly, lx;
       point_of_bit<G>(q, lz, ly, lx);
       const int e = G::entry(lz, ly, lx);
-      const uint32_t m = cml[e];
+      const int o = G::lin(lz, ly, lx);
+      const uint32_t m = cml[o];
       const uint32_t before = vs[e];
       ++evals;
       uint32_t best = before;
@@ -321,7 +408,7 @@ __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint16_t* c
         const int nz = lz + dz_of(k), ny = ly + dy_of(k), nx = lx + dx_of(k);
         if (nz < 0 || nz >= G::TZ || ny < 0 || ny >= G::TY || nx < 0 || nx >= G::TX) continue;
         const int kop = k < 7 ? k + 7 : k - 7;
-        if (!((cml[e + G::off(dz_of(k), dy_of(k), dx_of(k))] >> kop) & 1u)) continue;
+        if (!((cml[o + G::loff(dz_of(k), dy_of(k), dx_of(k))] >> kop) & 1u)) continue;
         const int qn = G::fbit(nz, ny, nx);
         atomicOr(&fb[qn >> 5], 1u << (qn & 31));
       }
@@ -359,7 +446,7 @@ struct PassSmem {
   static constexpr size_t RAb = (size_t)L + RzeWork::bytes(L);
   static constexpr size_t RA = up16(RAa > RAb ? RAa : RAb);
   static constexpr size_t RB = up16((size_t)G::E * sizeof(B) > L ? (size_t)G::E * sizeof(B) : L);
-  static constexpr size_t RC = up16((size_t)G::E * 2);                  // lower masks
+  static constexpr size_t RC = up16((size_t)G::NP * 2);                 // lower masks of the tile's points
   static constexpr size_t RD = up16(FixSmem<G>::bits_bytes());         // frontiers, risen bits, counters
   static_assert(FixSmem<G>::list_bytes() <= RB, "the frontier list reuses the bins");
   static constexpr size_t bytes() { return RA + RB + RC + RD; }
@@ -413,18 +500,21 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   const int64_t plane = g.ny * g.nx;
   long long t0 = clock64();
 
-  // 1. load, quantize, keys (absent points get a bin no value has)
+  // 1. load x on the box with asynchronous copies (absent points read nothing), then
+  //    quantize and take order keys in place (absent points get a bin no value has)
+  using Raw = typename Traits<T>::Bits;
+  Raw* raw = reinterpret_cast<Raw*>(smem);  // the keys' region holds the raw values first
+  constexpr int NBOX = G::BZ * G::BY * G::BX;  // entries of the box (the rare error path walks them)
+  load_box_async<G, Raw>(raw, reinterpret_cast<const Raw*>(x), g, tb);
+  for (int i = threadIdx.x; i < 3 * (G::NP / 32); i += NT) fa[i] = 0;  // both frontiers, risen bits
+  cp_async_wait_all();
+  __syncthreads();
   bool bad = false;
-  constexpr int NBOX = G::BZ * G::BY * G::BX;
-#pragma unroll 4
-  for (int i = threadIdx.x; i < NBOX; i += NT) {
-    const int lx = i % G::BX, ly = (i / G::BX) % G::BY, lz = i / (G::BX * G::BY);
-    const int e = lz * G::PP + ly * G::BXP + lx;
-    const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1, gx = tb.x0 + lx - 1;
+  for_box<G>(g, tb, [&](int e, bool in) {
     B b = Traits<T>::kAbsent;
     K k = 0;
-    if (gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx >= 0 && gx < g.nx) {
-      const T v = __ldg(&x[gz * plane + gy * g.nx + gx]);
+    if (in) {
+      const T v = Traits<T>::from_bits(raw[e]);
       long long q;
       if (is_finite_bits<T>(v) && quantize_fast<T>(v, inv_f, fast_ok, inv_m, inv_e, q) &&
           q < Traits<T>::kBinLimit && q > -Traits<T>::kBinLimit) {
@@ -436,9 +526,8 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
     }
     key[e] = k;
     bin[e] = b;
-  }
-  for (int i = threadIdx.x; i < 3 * (G::NP / 32); i += NT) fa[i] = 0;  // both frontiers, risen bits
-  if (bad) {  // tell non-finite from out-of-range, off the fast path
+  });
+  if (__syncthreads_or(bad)) {  // tell non-finite from out-of-range, off the fast path (whole block)
     for (int i = threadIdx.x; i < NBOX; i += NT) {
       const int lx = i % G::BX, ly = (i / G::BX) % G::BY, lz = i / (G::BX * G::BY);
       const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1, gx = tb.x0 + lx - 1;
@@ -479,7 +568,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
         }
       }
     }
-    cml[e] = (uint16_t)lo;
+    cml[G::lin(sp.lz, sp.ly0 + j, sp.lx)] = (uint16_t)lo;
     active |= ((lo >> 7) != 0) << j;
   }
   if (active) atomicOr(&fa[sp.b0 >> 5], active << (sp.b0 & 31));
@@ -556,7 +645,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
       const int e = sp.e0 + j * G::BXP;
       const int64_t gi = gz * plane + (tb.y0 + sp.ly0 + j) * g.nx + gx;
       s_glob[gi] = sv[e];
-      cm_glob[gi] = cml[e];
+      cm_glob[gi] = cml[G::lin(sp.lz, sp.ly0 + j, sp.lx)];
     }
   }
   phase_mark(P, 3, t0);
@@ -569,7 +658,7 @@ struct RerunSmem {
   static constexpr int QMAX = 2 * (G::TY * G::TX + (G::HZ ? G::TZ * G::TX + G::TZ * G::TY : G::TX + G::TY));
   static constexpr size_t up16(size_t v) { return (v + 15) & ~(size_t)15; }
   static constexpr size_t CM = (size_t)G::E * 4;                      // subbins, then lower masks
-  static constexpr size_t BITS = CM + up16((size_t)G::E * 2);         // frontiers, risen bits, counters
+  static constexpr size_t BITS = CM + up16((size_t)G::NP * 2);        // frontiers, risen bits, counters
   static constexpr size_t LIST = BITS + up16(FixSmem<G>::bits_bytes());
   static constexpr size_t QUEUE = LIST + FixSmem<G>::list_bytes();
   static constexpr size_t bytes() { return QUEUE + (size_t)QMAX * 4 + 16; }
@@ -618,35 +707,27 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
     const TileBox tb = tile_box(g, tid);
     const int64_t plane = g.ny * g.nx;
     long long t0 = clock64();
-    constexpr int NBOX = G::BZ * G::BY * G::BX;
-    constexpr int BATCH = 4;
-    for (int i0 = threadIdx.x; i0 < NBOX; i0 += BATCH * NT) {
-      uint32_t sb[BATCH], mb[BATCH];
-#pragma unroll
-      for (int u = 0; u < BATCH; ++u) {  // issue every load of the batch first
-        const int i = i0 + u * NT;
-        const int lx = i % G::BX, ly = (i / G::BX) % G::BY, lz = i / (G::BX * G::BY);
-        const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1, gx = tb.x0 + lx - 1;
-        sb[u] = 0;
-        mb[u] = 0;
-        if (i < NBOX && gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx >= 0 && gx < g.nx) {
-          const int64_t gi = gz * plane + gy * g.nx + gx;
-          sb[u] = s_glob[gi];
-          mb[u] = __ldg(&cm_glob[gi]);
-        }
+    // subbins of the box and lower masks of the tile's own points, by asynchronous
+    // copies (absent points read nothing and are zero)
+    load_box_async<G, uint32_t>(sv, s_glob, g, tb);
+    if ((g.nx & 1) == 0) {  // pairs of points along x are 4-byte aligned in memory
+      for (int i = threadIdx.x; i < G::NP / 2; i += NT) {
+        const int o = 2 * i;
+        const int lx = o % G::TX, ly = (o / G::TX) % G::TY, lz = o / (G::TX * G::TY);
+        const bool in = lz < tb.cz && ly < tb.cy && lx < tb.cx;
+        const int64_t gi = (tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx;
+        cp_async4(&cm[o], in ? &cm_glob[gi] : cm_glob, in);
       }
-#pragma unroll
-      for (int u = 0; u < BATCH; ++u) {
-        const int i = i0 + u * NT;
-        if (i >= NBOX) break;
-        const int lx = i % G::BX, ly = (i / G::BX) % G::BY, lz = i / (G::BX * G::BY);
-        const int e = lz * G::PP + ly * G::BXP + lx;
-        sv[e] = sb[u];
-        cm[e] = (uint16_t)mb[u];
+    } else {
+      for (int o = threadIdx.x; o < G::NP; o += NT) {
+        const int lx = o % G::TX, ly = (o / G::TX) % G::TY, lz = o / (G::TX * G::TY);
+        const bool in = lz < tb.cz && ly < tb.cy && lx < tb.cx;
+        cm[o] = in ? __ldg(&cm_glob[(tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx]) : (uint16_t)0;
       }
     }
     for (int i = threadIdx.x; i < 3 * (G::NP / 32); i += NT) fa0[i] = 0;  // frontiers, risen bits
     if (threadIdx.x == 0) qn = 0;
+    cp_async_wait_all();
     __syncthreads();
     const SegPos sp = seg_pos<G>();
     const bool col_in = sp.lz < tb.cz && sp.lx < tb.cx;
@@ -658,7 +739,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
 #pragma unroll 1
       for (int j = 0; j < kSegment; ++j) {
         const int e = sp.e0 + j * G::BXP;
-        const uint32_t mo = cm[e] & out_of_box_bits<G>(sp.lz, sp.ly0 + j, sp.lx);
+        const uint32_t mo = cm[G::lin(sp.lz, sp.ly0 + j, sp.lx)] & out_of_box_bits<G>(sp.lz, sp.ly0 + j, sp.lx);
         if (!mo) continue;
         const uint32_t sp_ = sv[e];
 #pragma unroll
@@ -712,9 +793,13 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
       for (int k = 0; k < 14; ++k) {
         if (!((ob >> k) & 1u)) continue;
         const int kop = k < 7 ? k + 7 : k - 7;
-        if (!((cm[e + G::off(dz_of(k), dy_of(k), dx_of(k))] >> kop) & 1u)) continue;
         const int64_t qz = pz + dz_of(k), qy = py + dy_of(k), qx = px + dx_of(k);
-        if (*(volatile const uint32_t*)&s_glob[qz * plane + qy * g.nx + qx] >= sf + (k < 7 ? 1u : 0u)) continue;
+        if (qz < 0 || qz >= g.nz || qy < 0 || qy >= g.ny || qx < 0 || qx >= g.nx) continue;
+        const int64_t qi = qz * plane + qy * g.nx + qx;
+        const uint32_t qm = __ldg(&cm_glob[qi]);                   // both loads in flight together
+        const uint32_t qs = *(volatile const uint32_t*)&s_glob[qi];
+        if (!((qm >> kop) & 1u)) continue;  // the neighbour is not constrained by p
+        if (qs >= sf + (k < 7 ? 1u : 0u)) continue;
         // a plain byte store: every writer stores the same value
         reinterpret_cast<volatile uint8_t*>(fi.dirty)[((qz / g.tz) * g.nty + qy / g.ty) * g.ntx + qx / g.tx] = 1;
       }

@@ -24,6 +24,18 @@ struct DecField {
   int64_t tile_base;
 };
 
+// Measurement aid: SM cycles per decode phase, summed over blocks, while enabled.
+__device__ unsigned long long g_dec_phase[8];
+__device__ int g_dec_phase_on;
+
+__device__ __forceinline__ void dec_mark(int k, long long& t0) {
+  if (threadIdx.x == 0 && g_dec_phase_on) {
+    const long long t = clock64();
+    atomicAdd(&g_dec_phase[k], (unsigned long long)(t - t0));
+    t0 = t;
+  }
+}
+
 // Reads each stream's header on the device: the decoder's parameters, and a check
 // that the header matches the descriptor the launch was planned for.
 __global__ void k_dec_setup(DecField* F, int nf) {
@@ -105,6 +117,11 @@ struct DecSmem {
   static constexpr size_t bytes() { return (size_t)L + LR + CACHE + (size_t)NP * W + RzeWork::bytes(LR) + 16; }
 };
 
+__device__ __forceinline__ uint32_t shfl_up_w(uint32_t v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ uint64_t shfl_up_w(uint64_t v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ uint32_t shfl_idx_w(uint32_t v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ uint64_t shfl_idx_w(uint64_t v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+
 // One block per chunk: bins (RZE_1, BIT_w, DIFFNB_w inverses), then the lowest value
 // of every bin of the tile's bin range (when it is small enough to cache), then
 // subbins (RZE_1, RZE_w, BIT_w inverses) and x_hat = the subbin-th value above the
@@ -169,6 +186,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_decode(const DecField* _
   const uint8_t* rb = in + offs[tid];
   const uint8_t* rs = in + offs[g.ntiles + tid];
   if (threadIdx.x == 0) bad = 0;
+  long long t0 = clock64();
   __syncthreads();
 
   // bins
@@ -185,6 +203,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_decode(const DecField* _
       if (!rze_decode<NT, 1>(A, sb, (uint32_t)W * n32, Bf, w)) bad = 1;
       __syncthreads();
     }
+    dec_mark(0, t0);
     if (!bad) {
       constexpr W_t M = (W_t)0xAAAAAAAAAAAAAAAAULL;
       bit_untranspose<NT, W>(n32, reinterpret_cast<const uint32_t*>(Bf), [&](int i, uint64_t u) {
@@ -194,17 +213,33 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_decode(const DecField* _
           bad = 1;
       });
       __syncthreads();
-      // prefix sum of the deltas (mod 2^(8W)), contiguous ranges per thread
-      const int per = (n + NT - 1) / NT;
-      const int a = min(n, (int)threadIdx.x * per), b = min(n, a + per);
-      W_t loc = 0;
-      for (int i = a; i < b; ++i) loc += wb[i];
-      __shared__ W_t scan_tmp[NT / 32 + 1];
-      W_t run = block_exclusive_scan<NT, W_t>(loc, scan_tmp, (W_t*)nullptr);
-      for (int i = a; i < b; ++i) {
-        run += wb[i];
-        wb[i] = run;
+      // prefix sum of the deltas (mod 2^(8W)): warp w scans words [w*per, (w+1)*per)
+      // in rows of 32 (one word per lane, shuffle scan, running carry), then adds
+      // the totals of the warps before it
+      constexpr int NWARP = NT / 32;
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      const int per = ((n + NWARP - 1) / NWARP + 31) & ~31;
+      const int a = min(n, wid * per), b = min(n, a + per);
+      W_t carry = 0;
+      for (int r = a; r < b; r += 32) {
+        const int i = r + lane;
+        W_t v = i < b ? wb[i] : (W_t)0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const W_t y = shfl_up_w(v, o);
+          if (lane >= o) v += y;
+        }
+        v += carry;
+        if (i < b) wb[i] = v;
+        carry = shfl_idx_w(v, 31);
       }
+      __shared__ W_t warp_tot[NWARP];
+      if (lane == 0) warp_tot[wid] = carry;
+      __syncthreads();
+      W_t before = 0;
+      for (int k = 0; k < wid; ++k) before += warp_tot[k];
+      if (before != (W_t)0)
+        for (int i = a + lane; i < b; i += 32) wb[i] += before;
     }
     __syncthreads();
   }
@@ -212,6 +247,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_decode(const DecField* _
     if (threadIdx.x == 0) atomicOr(status, kErrCorrupt);
     return;
   }
+  dec_mark(1, t0);
 
   // the lowest value of every bin in [bmin, bmax], when that range is small
   B lo_b = (B)(Traits<T>::kAbsent == INT32_MIN ? INT32_MAX : INT64_MAX), hi_b = (B)Traits<T>::kAbsent;
@@ -244,6 +280,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_decode(const DecField* _
     }
   }
   __syncthreads();
+  dec_mark(2, t0);
 
   const int64_t plane = g.ny * g.nx;
   bool fail = false;
@@ -294,8 +331,10 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_decode(const DecField* _
     }
     if (!bad && !rze_decode<NT, 1>(A + 4, ss - 4, l2, Bf, w)) bad = 1;
     __syncthreads();
+    dec_mark(3, t0);
     if (!bad && !rze_decode<NT, W>(Bf, l2, (uint32_t)W * n32, A, w)) bad = 1;
     __syncthreads();
+    dec_mark(4, t0);
     if (!bad) {
       bit_untranspose<NT, W>(n32, reinterpret_cast<const uint32_t*>(A), [&](int i, uint64_t u) {
         if (i < n)
@@ -306,6 +345,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_decode(const DecField* _
     }
   }
   if ((__syncthreads_or(fail) || bad) && threadIdx.x == 0) atomicOr(status, kErrCorrupt);
+  dec_mark(5, t0);
 }
 
 }  // namespace lopc

@@ -79,6 +79,8 @@ def lib():
         L.lopc_last_fixpoint_stats.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.lopc_last_phase_cycles.argtypes = [C.POINTER(C.c_int64), C.c_int]
         L.lopc_last_fixpoint_work.argtypes = [C.POINTER(C.c_int64), C.c_int]
+        L.lopc_decode_phase_enable.argtypes = [C.c_int]
+        L.lopc_decode_phase_read.argtypes = [C.POINTER(C.c_int64), C.c_int]
         L.lopc_profile_enable.argtypes = [C.c_int]
         L.lopc_profile_reset.argtypes = []
         L.lopc_profile_read.argtypes = [C.POINTER(C.c_char_p), C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int]
@@ -243,6 +245,20 @@ def last_fixpoint_work() -> dict:
     v = (C.c_int64 * 4)()
     lib().lopc_last_fixpoint_work(v, 4)
     return {"pass_evals": v[0], "pass_raises": v[1], "rerun_evals": v[2], "rerun_raises": v[3]}
+
+
+def decode_phase_enable(on: bool = True) -> None:
+    _check(lib().lopc_decode_phase_enable(1 if on else 0), "lopc_decode_phase_enable")
+
+
+def decode_phase_read() -> dict:
+    """SM cycles per decode phase since the last read (summed over blocks)."""
+    v = (C.c_int64 * 8)()
+    rc = lib().lopc_decode_phase_read(v, 8)
+    if rc < 0:
+        _check(rc, "lopc_decode_phase_read")
+    names = ["bin_rze", "bin_planes_scan", "bin_range_cache", "sub_rze1", "sub_rzew", "sub_planes_values"]
+    return dict(zip(names, [int(a) for a in v[:6]]))
 
 
 def compress_status(x: torch.Tensor, eb: float, mode: int = NOA, out_cap: Optional[int] = None,
