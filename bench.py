@@ -335,7 +335,7 @@ def main():
         lopc.profile_enable(False)
         dph = {a: v // k for a, v in lopc.decode_phase_read().items()}
         lopc.decode_phase_enable(False)
-        return prof, dph
+        return prof, dph, lopc.last_round_tiles()
 
     # headline: the configured bound as the library runs it (graphs), with clocks
     with ClockSampler(local) as clk:
@@ -349,7 +349,7 @@ def main():
     sweeps, sweeps_max = lopc.last_fixpoint_stats()
     work = lopc.last_fixpoint_work()
     phases = dict(zip(["pass_load", "pass_flags", "pass_fixpoint", "pass_writeback", "pass_bin_record",
-                       "rerun_load", "rerun_fixpoint", "unused"], lopc.last_phase_cycles()))
+                       "rerun_load", "rerun_fixpoint", "rerun_check_only"], lopc.last_phase_cycles()))
     hbm, peak_kind = peaks()
     cr = nbytes / ssize
     algo_comp = nbytes * 2 + ssize                 # NOA: range pass + tile pass read x; write stream
@@ -359,7 +359,7 @@ def main():
 
     # per-kernel split, and the dominant kernel's roofline (separate pass, same workload)
     prof_steps = 2
-    prof, dec_phases = profiled(args.eb, prof_steps)
+    prof, dec_phases, round_tiles = profiled(args.eb, prof_steps)
     w = 4
     npts = nbytes // w
     # algorithmic bytes per step of each kernel: what the method must move (range and
@@ -458,6 +458,7 @@ def main():
                          "hbm_frac_algorithmic": algo_comp / (tc.mean() * 1e-3) / 1e9 / hbm,
                          "input_frac": comp_gbs / hbm, "cr": cr, "repair_rounds": rounds, "tile_runs": runs,
                          "fixpoint_sweeps": sweeps, "fixpoint_sweeps_max": sweeps_max, "fixpoint_work": work,
+                         "round_tiles": round_tiles,
                          "phase_cycles": phases},
             "decompress": {"gbs": dec_gbs, "ms": float(td.mean()),
                            "hbm_frac_algorithmic": algo_dec / (td.mean() * 1e-3) / 1e9 / hbm,

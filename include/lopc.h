@@ -173,9 +173,16 @@ LOPC_API void lopc_last_fixpoint_stats(int64_t* sweeps_total, int64_t* sweeps_ma
 
 /* Measurement aid: SM cycles of the last compression on this thread, summed over
  * blocks, per phase: 0 tile load + quantization, 1 flags, 2 tile fixpoint, 3 state
- * write-back + marking, 4 bin record, 5 rerun load, 6 rerun fixpoint, 7 unused.
+ * write-back, 4 bin record, 5 rerun load and check, 6 rerun fixpoint, 7 rerun load and check of
+ * tiles whose constraints all held.
  * Copies min(n, 8) values and returns 8. */
 LOPC_API int lopc_last_phase_cycles(int64_t* cycles, int n);
+
+/* Measurement aid: tiles listed for each repair round after the first (all-tile)
+ * round, in the last compression on this thread that ran with per-kernel timing on
+ * (the host-driven loop); the last entry is the empty list that ended the repair.
+ * Copies min(n, rounds) values and returns the number of rounds. */
+LOPC_API int lopc_last_round_tiles(int64_t* out, int n);
 
 /* Measurement aid: work of the tile-local fixpoint in the last compression on this
  * thread: point evaluations and subbin raises in the tile pass, then the same in

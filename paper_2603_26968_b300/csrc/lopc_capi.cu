@@ -92,6 +92,7 @@ thread_local Profiler g_prof;
 thread_local int64_t g_last_rounds = 0, g_last_tile_runs = 0, g_last_fix_iters = 0, g_last_fix_iters_max = 0;
 thread_local int64_t g_last_phase[8] = {};
 thread_local int64_t g_last_work[4] = {};
+thread_local std::vector<int64_t> g_round_tiles;  // tiles listed per round (host-driven loop only)
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -219,7 +220,7 @@ FieldPart field_part(const Geometry& g) {
   L.s = o;
   o = align256(o + 4 * n);
   L.cm = o;
-  o = align256(o + 2 * n);
+  o = align256(o + 4 * n);
   L.sizes = o;
   o = align256(o + 8 * (size_t)g.ntiles);
   L.offs = o;
@@ -253,7 +254,7 @@ FieldInfo field_entry(const lopc_field_desc* d, const void* x, void* out, size_t
   f.out_cap = (uint64_t)cap;
   f.P = reinterpret_cast<Params*>(base + L.params);
   f.s = reinterpret_cast<uint32_t*>(base + L.s);
-  f.cm = reinterpret_cast<uint16_t*>(base + L.cm);
+  f.cm = reinterpret_cast<uint32_t*>(base + L.cm);
   f.sizes = reinterpret_cast<uint32_t*>(base + L.sizes);
   f.offs = reinterpret_cast<uint64_t*>(base + L.offs);
   f.dirty = reinterpret_cast<uint32_t*>(base + L.dirty);
@@ -329,7 +330,7 @@ int launch_class_rerun(const Table& t, int c, const FieldInfo* dF, const BatchSt
   using C = TileCfg<T, ND>;
   if (!t.cls_nf[c]) return LOPC_OK;
   const unsigned grid = (unsigned)imin64(t.cls_nt[c], rerun_blocks(c));
-  LAUNCH("tile_rerun", st,
+  LAUNCH(list ? "tile_rerun" : "tile_rerun_all", st,
          k_rerun<T, ND><<<grid, C::NT, RerunSmem<T, ND>::bytes(), st>>>(dF, t.cls_f0[c], t.cls_nf[c], t.cls_t0[c],
                                                                        t.cls_nt[c], c, dB, list));
   CK(cudaGetLastError());
@@ -482,11 +483,14 @@ int upload_plan(const CompressPlan& p, const Ptrs& q, cudaStream_t st) {
 int run_host_loop(const CompressPlan& p, const Ptrs& q, cudaStream_t st) {
   int rc = enqueue_prologue(p, q, st, cudaGraphConditionalHandle{}, 0);
   if (rc) return rc;
+  g_round_tiles.clear();
   while (true) {
     BatchState hb;
     CK(cudaMemcpyAsync(&hb, q.B, sizeof(BatchState), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (hb.count[0] + hb.count[1] + hb.count[2] + hb.count[3] == 0) break;
+    const int64_t listed = (int64_t)hb.count[0] + hb.count[1] + hb.count[2] + hb.count[3];
+    g_round_tiles.push_back(listed);
+    if (listed == 0) break;
     if ((rc = enqueue_loop_body(p, q, st, cudaGraphConditionalHandle{}, 0))) return rc;
   }
   return launch_epilogue(p.t, q.F, st);
@@ -1202,6 +1206,12 @@ int lopc_decode_phase_read(int64_t* out, int n) {
   const unsigned long long z[8] = {};
   CK(cudaMemcpyToSymbol(g_dec_phase, z, sizeof(z)));
   return 8;
+}
+
+int lopc_last_round_tiles(int64_t* out, int n) {
+  const int m = (int)g_round_tiles.size();
+  for (int k = 0; k < n && k < m; ++k) out[k] = g_round_tiles[k];
+  return m;
 }
 
 int lopc_last_fixpoint_work(int64_t* out, int n) {

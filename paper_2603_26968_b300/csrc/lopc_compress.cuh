@@ -191,15 +191,12 @@ struct TileGeom {
   // linear index of a tile point (masks are kept for the tile's own points only)
   __device__ static constexpr int lin(int lz, int ly, int lx) { return (lz * TY + ly) * TX + lx; }
   __device__ static constexpr int loff(int dz, int dy, int dx) { return (dz * TY + dy) * TX + dx; }
-  // owner thread of a point, and the point's bit in the frontier (thread-major)
-  __device__ static constexpr int owner(int lz, int ly, int lx) { return (lz * SEGY + ly / kSegment) * TX + lx; }
-  __device__ static constexpr int fbit(int lz, int ly, int lx) { return owner(lz, ly, lx) * kSegment + ly % kSegment; }
 };
 
 struct SegPos {
   int lz, ly0, lx;  // local coordinates of the thread's first point
   int e0;           // its shared-memory entry; point j is at e0 + j * BXP
-  int b0;           // its frontier bit; point j is bit b0 + j
+  int o0;           // its linear index (and frontier bit); point j is o0 + j * TX
 };
 
 template <typename G>
@@ -211,7 +208,7 @@ __device__ __forceinline__ SegPos seg_pos() {
   s.lz = r / G::SEGY;
   s.ly0 = (r % G::SEGY) * kSegment;
   s.e0 = G::entry(s.lz, s.ly0, s.lx);
-  s.b0 = t * kSegment;
+  s.o0 = G::lin(s.lz, s.ly0, s.lx);
   return s;
 }
 
@@ -311,18 +308,16 @@ __device__ __forceinline__ void for_box(const Geometry& g, const TileBox& tb, Fn
   }
 }
 
-// Decodes a frontier bit (fbit order) into local coordinates.
+// Local coordinates of tile point o (linear order: x fastest).
 template <typename G>
-__device__ __forceinline__ void point_of_bit(int q, int& lz, int& ly, int& lx) {
-  const int owner = q / kSegment;
-  lx = owner % G::TX;
-  const int r = owner / G::TX;
-  lz = r / G::SEGY;
-  ly = (r % G::SEGY) * kSegment + q % kSegment;
+__device__ __forceinline__ void point_of_lin(int o, int& lz, int& ly, int& lx) {
+  lx = o % G::TX;
+  ly = (o / G::TX) % G::TY;
+  lz = o / (G::TX * G::TY);
 }
 
 // Shared state of the list-driven fixpoint: two frontiers and the risen points (one
-// bit per tile point, fbit order), two list counters, the frontier list.
+// bit per tile point, linear order), two list counters, the frontier list.
 template <typename G>
 struct FixSmem {
   static constexpr int NW = G::NP / 32;
@@ -338,11 +333,13 @@ struct FixSmem {
 // sweep costs about one evaluation per thread.  Raised subbins are visible to the
 // rest of the sweep at once; a neighbour read before it rose is queued again by
 // that rise.  Chaotic relaxation from lower bounds reaches the unique least fixpoint
-// (Sec. III-E) whatever the schedule.  `cml[o]` holds the lower-neighbour bits of
-// tile point o (linear order); `fa` holds the first frontier, `fb` and `rb` must be clear; `rb` receives
-// the points that rose.  Returns the number of sweeps.
+// (Sec. III-E) whatever the schedule.  `cml[o]` holds, for tile point o (linear
+// order), its lower same-bin neighbours in bits 0-13 and its same-bin upper
+// neighbours inside the tile in bits 16-29 (no bounds checks, no neighbour reads).  `fa`
+// holds the first frontier, `fb` and `rb` must be clear; `rb` receives the points
+// that rose.  Returns the number of sweeps.
 template <typename G>
-__device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint16_t* cml, uint32_t* fa, uint32_t* fb,
+__device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint32_t* cml, uint32_t* fa, uint32_t* fb,
                                                  uint32_t* rb, unsigned* cnt, uint16_t* list, int limit, bool& over,
                                                  unsigned& evals, unsigned& raises) {
   constexpr int NW = G::NP / 32, NT = G::NT;
@@ -381,17 +378,16 @@ __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint16_t* c
     }
     if (threadIdx.x == 0) cnt[iter & 1] = 0;  // the counter of the next sweep
     for (unsigned i = threadIdx.x; i < n; i += NT) {
-      const int q = list[i];
+      const int o = list[i];
       int lz, ly, lx;
-      point_of_bit<G>(q, lz, ly, lx);
+      point_of_lin<G>(o, lz, ly, lx);
       const int e = G::entry(lz, ly, lx);
-      const int o = G::lin(lz, ly, lx);
       const uint32_t m = cml[o];
       const uint32_t before = vs[e];
       ++evals;
       uint32_t best = before;
 #pragma unroll
-      for (int k = 0; k < 14; ++k) {
+      for (int k = 0; k < 14; ++k) {  // predicated loads at constant offsets, all in flight together
         if (!G::HZ && dz_of(k) != 0) continue;
         if (m & (1u << k)) {
           const uint32_t cand = vs[e + G::off(dz_of(k), dy_of(k), dx_of(k))] + (k >= 7 ? 1u : 0u);
@@ -401,16 +397,14 @@ __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint16_t* c
       if (best == before) continue;
       vs[e] = best;
       ++raises;
-      atomicOr(&rb[q >> 5], 1u << (q & 31));
+      atomicOr(&rb[o >> 5], 1u << (o & 31));
 #pragma unroll
       for (int k = 0; k < 14; ++k) {
         if (!G::HZ && dz_of(k) != 0) continue;
-        const int nz = lz + dz_of(k), ny = ly + dy_of(k), nx = lx + dx_of(k);
-        if (nz < 0 || nz >= G::TZ || ny < 0 || ny >= G::TY || nx < 0 || nx >= G::TX) continue;
-        const int kop = k < 7 ? k + 7 : k - 7;
-        if (!((cml[o + G::loff(dz_of(k), dy_of(k), dx_of(k))] >> kop) & 1u)) continue;
-        const int qn = G::fbit(nz, ny, nx);
-        atomicOr(&fb[qn >> 5], 1u << (qn & 31));
+        if (m & (1u << (16 + k))) {
+          const int qn = o + G::loff(dz_of(k), dy_of(k), dx_of(k));
+          atomicOr(&fb[qn >> 5], 1u << (qn & 31));
+        }
       }
     }
     __syncthreads();
@@ -421,16 +415,24 @@ __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint16_t* c
   return iter;
 }
 
-// Bits of the directions that leave the tile box, for a point at local (lz, ly, lx).
+// Direction bits whose offset along an axis is -1 (lo) or +1 (hi).
+__host__ __device__ constexpr uint32_t dir_mask(int axis, int sign) {
+  uint32_t r = 0;
+  for (int k = 0; k < 14; ++k) {
+    const int d = axis == 0 ? dz_of(k) : axis == 1 ? dy_of(k) : dx_of(k);
+    if (d == sign) r |= 1u << k;
+  }
+  return r;
+}
+
+// Bits of the directions that leave the tile box, for a point at local (lz, ly, lx):
+// the directions stepping below a face the point lies on, or above one.
 template <typename G>
 __device__ __forceinline__ uint32_t out_of_box_bits(int lz, int ly, int lx) {
-  uint32_t r = 0;
-#pragma unroll
-  for (int k = 0; k < 14; ++k) {
-    if (!G::HZ && dz_of(k) != 0) continue;
-    const int nz = lz + dz_of(k), ny = ly + dy_of(k), nx = lx + dx_of(k);
-    if (nz < 0 || nz >= G::TZ || ny < 0 || ny >= G::TY || nx < 0 || nx >= G::TX) r |= 1u << k;
-  }
+  constexpr uint32_t zl = dir_mask(0, -1), zh = dir_mask(0, 1), yl = dir_mask(1, -1), yh = dir_mask(1, 1);
+  constexpr uint32_t xl = dir_mask(2, -1), xh = dir_mask(2, 1);
+  uint32_t r = (ly == 0 ? yl : 0u) | (ly == G::TY - 1 ? yh : 0u) | (lx == 0 ? xl : 0u) | (lx == G::TX - 1 ? xh : 0u);
+  if (G::HZ) r |= (lz == 0 ? zl : 0u) | (lz == G::TZ - 1 ? zh : 0u);
   return r;
 }
 
@@ -446,7 +448,7 @@ struct PassSmem {
   static constexpr size_t RAb = (size_t)L + RzeWork::bytes(L);
   static constexpr size_t RA = up16(RAa > RAb ? RAa : RAb);
   static constexpr size_t RB = up16((size_t)G::E * sizeof(B) > L ? (size_t)G::E * sizeof(B) : L);
-  static constexpr size_t RC = up16((size_t)G::NP * 2);                 // lower masks of the tile's points
+  static constexpr size_t RC = up16((size_t)G::NP * 4);                 // neighbour masks of the tile's points
   static constexpr size_t RD = up16(FixSmem<G>::bits_bytes());         // frontiers, risen bits, counters
   static_assert(FixSmem<G>::list_bytes() <= RB, "the frontier list reuses the bins");
   static constexpr size_t bytes() { return RA + RB + RC + RD; }
@@ -475,7 +477,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   const Geometry g = fi.g;
   const T* __restrict__ x = reinterpret_cast<const T*>(fi.x);
   uint32_t* __restrict__ s_glob = fi.s;
-  uint16_t* __restrict__ cm_glob = fi.cm;
+  uint32_t* __restrict__ cm_glob = fi.cm;
   int64_t* __restrict__ bins_out = fi.bins_out;
   uint8_t* __restrict__ slots = fi.slots;
   uint32_t* __restrict__ sizes = fi.sizes;
@@ -483,7 +485,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   K* key = reinterpret_cast<K*>(smem);
   uint32_t* sv = reinterpret_cast<uint32_t*>(smem);
   B* bin = reinterpret_cast<B*>(smem + PS::RA);
-  uint16_t* cml = reinterpret_cast<uint16_t*>(smem + PS::RA + PS::RB);
+  uint32_t* cml = reinterpret_cast<uint32_t*>(smem + PS::RA + PS::RB);
   uint32_t* fa = reinterpret_cast<uint32_t*>(smem + PS::RA + PS::RB + PS::RC);
   uint32_t* fb = fa + G::NP / 32;
   uint32_t* rb = fb + G::NP / 32;
@@ -548,14 +550,17 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   //    +1 constraint (a lower same-bin neighbour at a higher index, k >= 7) can rise
   //    in the first sweep: those points are the first frontier, and the others are
   //    queued when a lower neighbour rises.
+  //    A same-bin neighbour that is not lower is upper: inside the tile, those are
+  //    the points a rise must requeue.
   const SegPos sp = seg_pos<G>();
   const bool col_in = sp.lz < tb.cz && sp.lx < tb.cx;
-  uint32_t active = 0;
+  const int lane = threadIdx.x & 31;
 #pragma unroll 1
   for (int j = 0; j < kSegment; ++j) {
-    uint32_t lo = 0;
+    uint32_t same = 0, lo = 0;
     const int e = sp.e0 + j * G::BXP;
-    if (col_in && sp.ly0 + j < tb.cy) {
+    const int ly = sp.ly0 + j;
+    if (col_in && ly < tb.cy) {
       const B bp = bin[e];
       const K kp = key[e];
 #pragma unroll
@@ -563,15 +568,24 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
         if (!G::HZ && dz_of(k) != 0) continue;
         const int e2 = e + G::off(dz_of(k), dy_of(k), dx_of(k));
         if (bin[e2] == bp) {
+          same |= 1u << k;
           const K kn = key[e2];
           if (kn < kp || (kn == kp && k < 7)) lo |= 1u << k;
         }
       }
     }
-    cml[G::lin(sp.lz, sp.ly0 + j, sp.lx)] = (uint16_t)lo;
-    active |= ((lo >> 7) != 0) << j;
+    const uint32_t up = same & ~lo & ~out_of_box_bits<G>(sp.lz, ly, sp.lx);
+    const int o = sp.o0 + j * G::TX;
+    cml[o] = lo | (up << 16);
+    // first-frontier bits, one ballot per warp: a row of lanes holds consecutive points
+    const uint32_t bal = __ballot_sync(0xffffffffu, (lo >> 7) != 0);
+    if (G::TX >= 32) {
+      if (lane == 0 && bal) atomicOr(&fa[o >> 5], bal);
+    } else if ((lane & 15) == 0) {
+      const uint32_t half = (bal >> (lane & 16)) & 0xFFFFu;
+      if (half) atomicOr(&fa[o >> 5], half << (o & 31));
+    }
   }
-  if (active) atomicOr(&fa[sp.b0 >> 5], active << (sp.b0 & 31));
   const int64_t gz = tb.z0 + sp.lz, gx = tb.x0 + sp.lx;
   if (bins_out && col_in) {
     for (int j = 0; j < kSegment && sp.ly0 + j < tb.cy; ++j)
@@ -645,7 +659,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
       const int e = sp.e0 + j * G::BXP;
       const int64_t gi = gz * plane + (tb.y0 + sp.ly0 + j) * g.nx + gx;
       s_glob[gi] = sv[e];
-      cm_glob[gi] = cml[G::lin(sp.lz, sp.ly0 + j, sp.lx)];
+      cm_glob[gi] = cml[sp.o0 + j * G::TX];
     }
   }
   phase_mark(P, 3, t0);
@@ -658,7 +672,7 @@ struct RerunSmem {
   static constexpr int QMAX = 2 * (G::TY * G::TX + (G::HZ ? G::TZ * G::TX + G::TZ * G::TY : G::TX + G::TY));
   static constexpr size_t up16(size_t v) { return (v + 15) & ~(size_t)15; }
   static constexpr size_t CM = (size_t)G::E * 4;                      // subbins, then lower masks
-  static constexpr size_t BITS = CM + up16((size_t)G::NP * 2);        // frontiers, risen bits, counters
+  static constexpr size_t BITS = CM + up16((size_t)G::NP * 4);        // frontiers, risen bits, counters
   static constexpr size_t LIST = BITS + up16(FixSmem<G>::bits_bytes());
   static constexpr size_t QUEUE = LIST + FixSmem<G>::list_bytes();
   static constexpr size_t bytes() { return QUEUE + (size_t)QMAX * 4 + 16; }
@@ -681,7 +695,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
   constexpr int NT = G::NT;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* sv = reinterpret_cast<uint32_t*>(smem);
-  uint16_t* cm = reinterpret_cast<uint16_t*>(smem + RS::CM);
+  uint32_t* cm = reinterpret_cast<uint32_t*>(smem + RS::CM);
   uint32_t* fa0 = reinterpret_cast<uint32_t*>(smem + RS::BITS);
   uint32_t* rb = fa0 + 2 * (G::NP / 32);
   unsigned* cnt = rb + G::NP / 32;
@@ -699,7 +713,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
     if ((P->status & kErrNonfinite) || P->constant) continue;  // uniform per block
     const Geometry g = fi.g;
     uint32_t* __restrict__ s_glob = fi.s;
-    const uint16_t* __restrict__ cm_glob = fi.cm;
+    const uint32_t* __restrict__ cm_glob = fi.cm;
     uint32_t* fa = fa0;
     uint32_t* fb = fa0 + G::NP / 32;
     const int64_t tid = gt - fi.tile_base;
@@ -710,20 +724,11 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
     // subbins of the box and lower masks of the tile's own points, by asynchronous
     // copies (absent points read nothing and are zero)
     load_box_async<G, uint32_t>(sv, s_glob, g, tb);
-    if ((g.nx & 1) == 0) {  // pairs of points along x are 4-byte aligned in memory
-      for (int i = threadIdx.x; i < G::NP / 2; i += NT) {
-        const int o = 2 * i;
-        const int lx = o % G::TX, ly = (o / G::TX) % G::TY, lz = o / (G::TX * G::TY);
-        const bool in = lz < tb.cz && ly < tb.cy && lx < tb.cx;
-        const int64_t gi = (tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx;
-        cp_async4(&cm[o], in ? &cm_glob[gi] : cm_glob, in);
-      }
-    } else {
-      for (int o = threadIdx.x; o < G::NP; o += NT) {
-        const int lx = o % G::TX, ly = (o / G::TX) % G::TY, lz = o / (G::TX * G::TY);
-        const bool in = lz < tb.cz && ly < tb.cy && lx < tb.cx;
-        cm[o] = in ? __ldg(&cm_glob[(tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx]) : (uint16_t)0;
-      }
+    for (int o = threadIdx.x; o < G::NP; o += NT) {
+      const int lx = o % G::TX, ly = (o / G::TX) % G::TY, lz = o / (G::TX * G::TY);
+      const bool in = lz < tb.cz && ly < tb.cy && lx < tb.cx;
+      const int64_t gi = (tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx;
+      cp_async4(&cm[o], in ? &cm_glob[gi] : cm_glob, in);
     }
     for (int i = threadIdx.x; i < 3 * (G::NP / 32); i += NT) fa0[i] = 0;  // frontiers, risen bits
     if (threadIdx.x == 0) qn = 0;
@@ -734,29 +739,41 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
     // the first frontier: boundary points whose constraint from a lower same-bin
     // neighbour outside the tile is violated by the current subbins (points outside
     // a clipped tile are out of the domain: their masks were loaded as 0)
-    uint32_t first = 0;
+    bool first = false;
     if (col_in) {
 #pragma unroll 1
       for (int j = 0; j < kSegment; ++j) {
         const int e = sp.e0 + j * G::BXP;
-        const uint32_t mo = cm[G::lin(sp.lz, sp.ly0 + j, sp.lx)] & out_of_box_bits<G>(sp.lz, sp.ly0 + j, sp.lx);
+        const int o = sp.o0 + j * G::TX;
+        const uint32_t mo = cm[o] & out_of_box_bits<G>(sp.lz, sp.ly0 + j, sp.lx);
         if (!mo) continue;
         const uint32_t sp_ = sv[e];
+        bool viol = false;
 #pragma unroll
         for (int k = 0; k < 14; ++k) {
           if ((mo >> k) & 1u) {
-            if (sv[e + G::off(dz_of(k), dy_of(k), dx_of(k))] + (k >= 7 ? 1u : 0u) > sp_) first |= 1u << j;
+            if (sv[e + G::off(dz_of(k), dy_of(k), dx_of(k))] + (k >= 7 ? 1u : 0u) > sp_) viol = true;
           }
+        }
+        if (viol) {
+          atomicOr(&fa[o >> 5], 1u << (o & 31));
+          first = true;
         }
       }
     }
-    if (first) atomicOr(&fa[sp.b0 >> 5], first << (sp.b0 & 31));
-    if (!__syncthreads_or(first != 0)) continue;  // every constraint into this tile holds
+    if (!__syncthreads_or(first)) {  // every constraint into this tile holds
+      phase_mark(P, 7, t0);
+      continue;
+    }
     phase_mark(P, 5, t0);
     bool over = false;
     unsigned evals = 0, raises = 0;
     const int iters = frontier_fixpoint<G>(sv, cm, fa, fb, rb, cnt, flist, 4 * G::NP + 64, over, evals, raises);
-    const uint32_t risen = (rb[sp.b0 >> 5] >> (sp.b0 & 31)) & ((1u << kSegment) - 1u);
+    uint32_t risen = 0;  // the thread's segment points that rose
+    for (int j = 0; j < kSegment; ++j) {
+      const int o = sp.o0 + j * G::TX;
+      risen |= ((rb[o >> 5] >> (o & 31)) & 1u) << j;
+    }
     if (threadIdx.x == 0) {
       if (over) atomicOr(&P->status, kErrNotConverged);
       atomicAdd(&P->fix_iters, (unsigned long long)iters);

@@ -380,7 +380,7 @@ struct FieldInfo {
   uint64_t out_cap;
   Params* P;              // per-field state (in the workspace)
   uint32_t* s;            // subbins, one per point
-  uint16_t* cm;           // lower-neighbour masks, one per point
+  uint32_t* cm;           // per point: lower same-bin neighbours (bits 0-13), in-tile upper ones (16-29)
   uint8_t* slots;         // 2 x ntiles record slots of 16 KiB
   uint32_t* sizes;        // 2 x ntiles record sizes
   uint64_t* offs;         // 2 x ntiles record offsets

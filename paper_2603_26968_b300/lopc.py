@@ -79,6 +79,7 @@ def lib():
         L.lopc_last_fixpoint_stats.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.lopc_last_phase_cycles.argtypes = [C.POINTER(C.c_int64), C.c_int]
         L.lopc_last_fixpoint_work.argtypes = [C.POINTER(C.c_int64), C.c_int]
+        L.lopc_last_round_tiles.argtypes = [C.POINTER(C.c_int64), C.c_int]
         L.lopc_decode_phase_enable.argtypes = [C.c_int]
         L.lopc_decode_phase_read.argtypes = [C.POINTER(C.c_int64), C.c_int]
         L.lopc_profile_enable.argtypes = [C.c_int]
@@ -245,6 +246,13 @@ def last_fixpoint_work() -> dict:
     v = (C.c_int64 * 4)()
     lib().lopc_last_fixpoint_work(v, 4)
     return {"pass_evals": v[0], "pass_raises": v[1], "rerun_evals": v[2], "rerun_raises": v[3]}
+
+
+def last_round_tiles() -> list:
+    """Tiles listed per repair round of the last profiled compression."""
+    v = (C.c_int64 * 4096)()
+    n = lib().lopc_last_round_tiles(v, 4096)
+    return [int(v[k]) for k in range(min(n, 4096))]
 
 
 def decode_phase_enable(on: bool = True) -> None:
