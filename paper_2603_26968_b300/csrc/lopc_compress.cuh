@@ -308,6 +308,27 @@ __device__ __forceinline__ void for_box(const Geometry& g, const TileBox& tb, Fn
   }
 }
 
+// Direction bits whose offset along an axis is -1 (lo) or +1 (hi).
+__host__ __device__ constexpr uint32_t dir_mask(int axis, int sign) {
+  uint32_t r = 0;
+  for (int k = 0; k < 14; ++k) {
+    const int d = axis == 0 ? dz_of(k) : axis == 1 ? dy_of(k) : dx_of(k);
+    if (d == sign) r |= 1u << k;
+  }
+  return r;
+}
+
+// Bits of the directions that leave the tile box, for a point at local (lz, ly, lx):
+// the directions stepping below a face the point lies on, or above one.
+template <typename G>
+__device__ __forceinline__ uint32_t out_of_box_bits(int lz, int ly, int lx) {
+  constexpr uint32_t zl = dir_mask(0, -1), zh = dir_mask(0, 1), yl = dir_mask(1, -1), yh = dir_mask(1, 1);
+  constexpr uint32_t xl = dir_mask(2, -1), xh = dir_mask(2, 1);
+  uint32_t r = (ly == 0 ? yl : 0u) | (ly == G::TY - 1 ? yh : 0u) | (lx == 0 ? xl : 0u) | (lx == G::TX - 1 ? xh : 0u);
+  if (G::HZ) r |= (lz == 0 ? zl : 0u) | (lz == G::TZ - 1 ? zh : 0u);
+  return r;
+}
+
 // Local coordinates of tile point o (linear order: x fastest).
 template <typename G>
 __device__ __forceinline__ void point_of_lin(int o, int& lz, int& ly, int& lx) {
@@ -334,11 +355,12 @@ struct FixSmem {
 // rest of the sweep at once; a neighbour read before it rose is queued again by
 // that rise.  Chaotic relaxation from lower bounds reaches the unique least fixpoint
 // (Sec. III-E) whatever the schedule.  `cml[o]` holds, for tile point o (linear
-// order), its lower same-bin neighbours in bits 0-13 and its same-bin upper
-// neighbours inside the tile in bits 16-29 (no bounds checks, no neighbour reads).  `fa`
+// order), its lower same-bin neighbours in bits 0-13, and in bits 16-29 its same-bin
+// upper neighbours inside the tile (SAME = false) or all its same-bin neighbours
+// (SAME = true; the in-tile upper ones are derived).  `fa`
 // holds the first frontier, `fb` and `rb` must be clear; `rb` receives the points
 // that rose.  Returns the number of sweeps.
-template <typename G>
+template <typename G, bool SAME>
 __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint32_t* cml, uint32_t* fa, uint32_t* fb,
                                                  uint32_t* rb, unsigned* cnt, uint16_t* list, int limit, bool& over,
                                                  unsigned& evals, unsigned& raises) {
@@ -398,10 +420,12 @@ __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint32_t* c
       vs[e] = best;
       ++raises;
       atomicOr(&rb[o >> 5], 1u << (o & 31));
+      // in-tile upper neighbours: stored as such, or derived from the same-bin bits
+      const uint32_t um = SAME ? ((m >> 16) & ~m & ~out_of_box_bits<G>(lz, ly, lx)) : (m >> 16);
 #pragma unroll
       for (int k = 0; k < 14; ++k) {
         if (!G::HZ && dz_of(k) != 0) continue;
-        if (m & (1u << (16 + k))) {
+        if (um & (1u << k)) {
           const int qn = o + G::loff(dz_of(k), dy_of(k), dx_of(k));
           atomicOr(&fb[qn >> 5], 1u << (qn & 31));
         }
@@ -415,26 +439,6 @@ __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint32_t* c
   return iter;
 }
 
-// Direction bits whose offset along an axis is -1 (lo) or +1 (hi).
-__host__ __device__ constexpr uint32_t dir_mask(int axis, int sign) {
-  uint32_t r = 0;
-  for (int k = 0; k < 14; ++k) {
-    const int d = axis == 0 ? dz_of(k) : axis == 1 ? dy_of(k) : dx_of(k);
-    if (d == sign) r |= 1u << k;
-  }
-  return r;
-}
-
-// Bits of the directions that leave the tile box, for a point at local (lz, ly, lx):
-// the directions stepping below a face the point lies on, or above one.
-template <typename G>
-__device__ __forceinline__ uint32_t out_of_box_bits(int lz, int ly, int lx) {
-  constexpr uint32_t zl = dir_mask(0, -1), zh = dir_mask(0, 1), yl = dir_mask(1, -1), yh = dir_mask(1, 1);
-  constexpr uint32_t xl = dir_mask(2, -1), xh = dir_mask(2, 1);
-  uint32_t r = (ly == 0 ? yl : 0u) | (ly == G::TY - 1 ? yh : 0u) | (lx == 0 ? xl : 0u) | (lx == G::TX - 1 ? xh : 0u);
-  if (G::HZ) r |= (lz == 0 ? zl : 0u) | (lz == G::TZ - 1 ? zh : 0u);
-  return r;
-}
 
 template <typename T, int ND>
 struct PassSmem {
@@ -555,6 +559,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   const SegPos sp = seg_pos<G>();
   const bool col_in = sp.lz < tb.cz && sp.lx < tb.cx;
   const int lane = threadIdx.x & 31;
+  const int64_t gz = tb.z0 + sp.lz, gx = tb.x0 + sp.lx;
 #pragma unroll 1
   for (int j = 0; j < kSegment; ++j) {
     uint32_t same = 0, lo = 0;
@@ -577,6 +582,8 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
     const uint32_t up = same & ~lo & ~out_of_box_bits<G>(sp.lz, ly, sp.lx);
     const int o = sp.o0 + j * G::TX;
     cml[o] = lo | (up << 16);
+    // the global copy (for reruns) keeps the lower and all the same-bin bits
+    if (col_in && ly < tb.cy) cm_glob[gz * plane + (tb.y0 + ly) * g.nx + gx] = lo | (same << 16);
     // first-frontier bits, one ballot per warp: a row of lanes holds consecutive points
     const uint32_t bal = __ballot_sync(0xffffffffu, (lo >> 7) != 0);
     if (G::TX >= 32) {
@@ -586,7 +593,6 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
       if (half) atomicOr(&fa[o >> 5], half << (o & 31));
     }
   }
-  const int64_t gz = tb.z0 + sp.lz, gx = tb.x0 + sp.lx;
   if (bins_out && col_in) {
     for (int j = 0; j < kSegment && sp.ly0 + j < tb.cy; ++j)
       bins_out[gz * plane + (tb.y0 + sp.ly0 + j) * g.nx + gx] = (int64_t)bin[sp.e0 + j * G::BXP];
@@ -642,7 +648,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   __syncthreads();
   bool over = false;
   unsigned evals = 0, raises = 0;
-  const int iters = frontier_fixpoint<G>(sv, cml, fa, fb, rb, cnt, list, 4 * G::NP + 64, over, evals, raises);
+  const int iters = frontier_fixpoint<G, false>(sv, cml, fa, fb, rb, cnt, list, 4 * G::NP + 64, over, evals, raises);
   if (threadIdx.x == 0) {
     if (over) atomicOr(&P->status, kErrNotConverged);
     atomicAdd(&P->fix_iters, (unsigned long long)iters);
@@ -651,7 +657,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   block_add2(evals, raises, &P->work[0]);
   phase_mark(P, 2, t0);
 
-  // 5. write the state reruns need (cross-tile constraints are checked afterwards)
+  // 5. write the subbins reruns start from (cross-tile constraints are checked afterwards)
   if (col_in) {
 #pragma unroll 4
     for (int j = 0; j < kSegment; ++j) {
@@ -659,7 +665,6 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
       const int e = sp.e0 + j * G::BXP;
       const int64_t gi = gz * plane + (tb.y0 + sp.ly0 + j) * g.nx + gx;
       s_glob[gi] = sv[e];
-      cm_glob[gi] = cml[sp.o0 + j * G::TX];
     }
   }
   phase_mark(P, 3, t0);
@@ -768,7 +773,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
     phase_mark(P, 5, t0);
     bool over = false;
     unsigned evals = 0, raises = 0;
-    const int iters = frontier_fixpoint<G>(sv, cm, fa, fb, rb, cnt, flist, 4 * G::NP + 64, over, evals, raises);
+    const int iters = frontier_fixpoint<G, true>(sv, cm, fa, fb, rb, cnt, flist, 4 * G::NP + 64, over, evals, raises);
     uint32_t risen = 0;  // the thread's segment points that rose
     for (int j = 0; j < kSegment; ++j) {
       const int o = sp.o0 + j * G::TX;
@@ -796,27 +801,26 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
       }
     }
     __syncthreads();
-    // mark, in parallel over the queue: tiles whose constraints from risen boundary
-    // points are now violated (the neighbour's mask says whether it is constrained)
+    // mark, in parallel over the queue: tiles holding an upper same-bin neighbour q of
+    // a risen boundary point p whose constraint s(q) >= s(p) + [p after q] no longer
+    // holds.  q's subbin is read from the halo loaded at the start: it can only have
+    // risen since, so a tile is sometimes marked when it need not be (its rerun then
+    // finds every constraint held) but never missed.
     const uint32_t nq = min(qn, (uint32_t)RS::QMAX);
     for (uint32_t qi = threadIdx.x; qi < nq; qi += NT) {
       const uint32_t v = queue[qi];
       const int lz = (int)(v >> 20), ly = (int)((v >> 10) & 1023u), lx = (int)(v & 1023u);
       const int e = G::entry(lz, ly, lx);
       const uint32_t sf = sv[e];
-      const uint32_t ob = out_of_box_bits<G>(lz, ly, lx);
+      const uint32_t pm = cm[G::lin(lz, ly, lx)];
+      const uint32_t up = (pm >> 16) & ~pm & out_of_box_bits<G>(lz, ly, lx);  // upper, outside the tile
       const int64_t pz = tb.z0 + lz, py = tb.y0 + ly, px = tb.x0 + lx;
 #pragma unroll
       for (int k = 0; k < 14; ++k) {
-        if (!((ob >> k) & 1u)) continue;
-        const int kop = k < 7 ? k + 7 : k - 7;
+        if (!G::HZ && dz_of(k) != 0) continue;
+        if (!((up >> k) & 1u)) continue;
+        if (sv[e + G::off(dz_of(k), dy_of(k), dx_of(k))] >= sf + (k < 7 ? 1u : 0u)) continue;
         const int64_t qz = pz + dz_of(k), qy = py + dy_of(k), qx = px + dx_of(k);
-        if (qz < 0 || qz >= g.nz || qy < 0 || qy >= g.ny || qx < 0 || qx >= g.nx) continue;
-        const int64_t qi = qz * plane + qy * g.nx + qx;
-        const uint32_t qm = __ldg(&cm_glob[qi]);                   // both loads in flight together
-        const uint32_t qs = *(volatile const uint32_t*)&s_glob[qi];
-        if (!((qm >> kop) & 1u)) continue;  // the neighbour is not constrained by p
-        if (qs >= sf + (k < 7 ? 1u : 0u)) continue;
         // a plain byte store: every writer stores the same value
         reinterpret_cast<volatile uint8_t*>(fi.dirty)[((qz / g.tz) * g.nty + qy / g.ty) * g.ntx + qx / g.tx] = 1;
       }
