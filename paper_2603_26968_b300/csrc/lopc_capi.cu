@@ -342,7 +342,7 @@ int launch_class_encode(const Table& t, int c, const FieldInfo* dF, cudaStream_t
   using C = TileCfg<T, ND>;
   if (!t.cls_nf[c]) return LOPC_OK;
   LAUNCH("encode_subbins", st,
-         k_encode_sub<T, ND><<<(unsigned)t.cls_nt[c], C::NT, EncSmem<T, ND>::bytes(), st>>>(dF, t.cls_f0[c],
+         k_encode_sub<T, ND><<<(unsigned)t.cls_nt[c], C::NTC, EncSmem<T, ND>::bytes(), st>>>(dF, t.cls_f0[c],
                                                                                            t.cls_nf[c], t.cls_t0[c]));
   CK(cudaGetLastError());
   return LOPC_OK;
@@ -775,7 +775,7 @@ int launch_class_decode(const DecompressPlan& p, int c, const DecField* dF, cuda
   int rc = set_smem_attrs<T, ND>();
   if (rc) return rc;
   LAUNCH("decode", st,
-         k_decode<T, ND><<<(unsigned)p.cls_nt[c], C::NT, DecSmem<T, ND>::bytes(), st>>>(dF, p.cls_f0[c], p.cls_nf[c],
+         k_decode<T, ND><<<(unsigned)p.cls_nt[c], C::NTC, DecSmem<T, ND>::bytes(), st>>>(dF, p.cls_f0[c], p.cls_nf[c],
                                                                                        p.cls_t0[c]));
   CK(cudaGetLastError());
   return LOPC_OK;

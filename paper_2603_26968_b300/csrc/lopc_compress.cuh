@@ -9,21 +9,24 @@ namespace lopc {
 // Compile-time tile configuration (Sec. II-C chunk of 16 KiB of words, as a tile).
 template <typename T, int ND>
 struct TileCfg;
+// TZ x TY x TX: the chunk tile; HZ: z halo (0 for 2D); NT threads and SEG y-points per
+// thread in the tile pass and reruns (NT = TZ * (TY / SEG) * TX); MINB, MINB_RERUN:
+// blocks per SM those kernels are built for; NTC: threads of the chunk codecs.
 template <>
 struct TileCfg<float, 3> {
-  static constexpr int TZ = 16, TY = 16, TX = 16, HZ = 1, NT = 256, MINB = 3, MINB_RERUN = 3;
+  static constexpr int TZ = 16, TY = 16, TX = 16, HZ = 1, NT = 256, SEG = 16, MINB = 3, MINB_RERUN = 3, NTC = 256;
 };
 template <>
 struct TileCfg<double, 3> {
-  static constexpr int TZ = 8, TY = 16, TX = 16, HZ = 1, NT = 128, MINB = 3, MINB_RERUN = 6;
+  static constexpr int TZ = 8, TY = 16, TX = 16, HZ = 1, NT = 128, SEG = 16, MINB = 3, MINB_RERUN = 6, NTC = 128;
 };
 template <>
 struct TileCfg<float, 2> {
-  static constexpr int TZ = 1, TY = 64, TX = 64, HZ = 0, NT = 256, MINB = 3, MINB_RERUN = 3;
+  static constexpr int TZ = 1, TY = 64, TX = 64, HZ = 0, NT = 256, SEG = 16, MINB = 3, MINB_RERUN = 3, NTC = 256;
 };
 template <>
 struct TileCfg<double, 2> {
-  static constexpr int TZ = 1, TY = 32, TX = 64, HZ = 0, NT = 128, MINB = 5, MINB_RERUN = 6;
+  static constexpr int TZ = 1, TY = 32, TX = 64, HZ = 0, NT = 128, SEG = 16, MINB = 5, MINB_RERUN = 6, NTC = 128;
 };
 
 // Freudenthal neighbourhood (Sec. II): offsets +-d, d in {0,1}^3 \ {0}.  Direction
@@ -177,13 +180,13 @@ constexpr uint32_t kSlotBytes = 16384;  // a record never exceeds the raw chunk 
 template <typename T, int ND>
 struct TileGeom {
   using C = TileCfg<T, ND>;
-  static constexpr int TZ = C::TZ, TY = C::TY, TX = C::TX, HZ = C::HZ, NT = C::NT;
+  static constexpr int TZ = C::TZ, TY = C::TY, TX = C::TX, HZ = C::HZ, NT = C::NT, SEG = C::SEG;
   static constexpr int BZ = TZ + 2 * HZ, BY = TY + 2, BX = TX + 2;
   static constexpr int BXP = (BX % 2) ? BX : BX + 1;
   static constexpr int PP = HZ ? ((BY * BXP + 15) / 32) * 32 + 16 : BY * BXP;
   static constexpr int E = BZ * PP;               // shared-memory entries
   static constexpr int NP = TZ * TY * TX;         // points of a full tile
-  static constexpr int SEGY = TY / kSegment;      // y-segments per column
+  static constexpr int SEGY = TY / SEG;           // y-segments per column
   static_assert(TZ * SEGY * TX == NT, "one y-segment per thread");
   static_assert(TX >= 16, "a half warp spans one x-run");
   __device__ static constexpr int off(int dz, int dy, int dx) { return dz * PP + dy * BXP + dx; }
@@ -206,7 +209,7 @@ __device__ __forceinline__ SegPos seg_pos() {
   s.lx = t % G::TX;
   const int r = t / G::TX;
   s.lz = r / G::SEGY;
-  s.ly0 = (r % G::SEGY) * kSegment;
+  s.ly0 = (r % G::SEGY) * G::SEG;
   s.e0 = G::entry(s.lz, s.ly0, s.lx);
   s.o0 = G::lin(s.lz, s.ly0, s.lx);
   return s;
@@ -561,7 +564,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   const int lane = threadIdx.x & 31;
   const int64_t gz = tb.z0 + sp.lz, gx = tb.x0 + sp.lx;
 #pragma unroll 1
-  for (int j = 0; j < kSegment; ++j) {
+  for (int j = 0; j < G::SEG; ++j) {
     uint32_t same = 0, lo = 0;
     const int e = sp.e0 + j * G::BXP;
     const int ly = sp.ly0 + j;
@@ -594,7 +597,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
     }
   }
   if (bins_out && col_in) {
-    for (int j = 0; j < kSegment && sp.ly0 + j < tb.cy; ++j)
+    for (int j = 0; j < G::SEG && sp.ly0 + j < tb.cy; ++j)
       bins_out[gz * plane + (tb.y0 + sp.ly0 + j) * g.nx + gx] = (int64_t)bin[sp.e0 + j * G::BXP];
   }
   __syncthreads();  // keys are dead from here on
@@ -660,7 +663,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   // 5. write the subbins reruns start from (cross-tile constraints are checked afterwards)
   if (col_in) {
 #pragma unroll 4
-    for (int j = 0; j < kSegment; ++j) {
+    for (int j = 0; j < G::SEG; ++j) {
       if (sp.ly0 + j >= tb.cy) break;
       const int e = sp.e0 + j * G::BXP;
       const int64_t gi = gz * plane + (tb.y0 + sp.ly0 + j) * g.nx + gx;
@@ -747,7 +750,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
     bool first = false;
     if (col_in) {
 #pragma unroll 1
-      for (int j = 0; j < kSegment; ++j) {
+      for (int j = 0; j < G::SEG; ++j) {
         const int e = sp.e0 + j * G::BXP;
         const int o = sp.o0 + j * G::TX;
         const uint32_t mo = cm[o] & out_of_box_bits<G>(sp.lz, sp.ly0 + j, sp.lx);
@@ -775,7 +778,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
     unsigned evals = 0, raises = 0;
     const int iters = frontier_fixpoint<G, true>(sv, cm, fa, fb, rb, cnt, flist, 4 * G::NP + 64, over, evals, raises);
     uint32_t risen = 0;  // the thread's segment points that rose
-    for (int j = 0; j < kSegment; ++j) {
+    for (int j = 0; j < G::SEG; ++j) {
       const int o = sp.o0 + j * G::TX;
       risen |= ((rb[o >> 5] >> (o & 31)) & 1u) << j;
     }
@@ -790,7 +793,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
     const int64_t gz = tb.z0 + sp.lz, gx = tb.x0 + sp.lx;
     if (col_in && risen) {
 #pragma unroll 1
-      for (int j = 0; j < kSegment; ++j) {
+      for (int j = 0; j < G::SEG; ++j) {
         if (!((risen >> j) & 1u)) continue;
         const int ly = sp.ly0 + j;
         s_glob[gz * plane + (tb.y0 + ly) * g.nx + gx] = sv[sp.e0 + j * G::BXP];
@@ -912,12 +915,12 @@ struct EncSmem {
 // Subbin record of each chunk (Sec. III-C, LC-generated pipeline): BIT_w, RZE_w,
 // RZE_1, prefixed by the u32 length of the RZE_w output; raw if not shorter.
 template <typename T, int ND>
-__global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_encode_sub(const FieldInfo* __restrict__ F, int f0, int nf,
+__global__ void __launch_bounds__(TileCfg<T, ND>::NTC) k_encode_sub(const FieldInfo* __restrict__ F, int f0, int nf,
                                                                    int64_t tile0) {
   using G = TileGeom<T, ND>;
   using ES = EncSmem<T, ND>;
   using W_t = typename Traits<T>::Bits;
-  constexpr int NT = G::NT, W = Traits<T>::W;
+  constexpr int NT = TileCfg<T, ND>::NTC, W = Traits<T>::W;
   const int64_t gt = tile0 + blockIdx.x;
   const FieldInfo& fi = F[field_of_tile(F, f0, nf, gt)];
   const Params* P = fi.P;

@@ -127,14 +127,14 @@ __device__ __forceinline__ uint64_t shfl_idx_w(uint64_t v, int l) { return __shf
 // subbins (RZE_1, RZE_w, BIT_w inverses) and x_hat = the subbin-th value above the
 // bin's lowest value (Sec. III-E), written as the subbin words come out.
 template <typename T, int ND>
-__global__ void __launch_bounds__(TileCfg<T, ND>::NT) k_decode(const DecField* __restrict__ F, int f0, int nf,
+__global__ void __launch_bounds__(TileCfg<T, ND>::NTC) k_decode(const DecField* __restrict__ F, int f0, int nf,
                                                                int64_t tile0) {
   using G = TileGeom<T, ND>;
   using DS = DecSmem<T, ND>;
   using W_t = typename Traits<T>::Bits;
   using K = typename Traits<T>::Key;
   using B = typename Traits<T>::Bin;
-  constexpr int NT = G::NT, W = Traits<T>::W;
+  constexpr int NT = TileCfg<T, ND>::NTC, W = Traits<T>::W;
   constexpr int CAPN = DS::CACHE / sizeof(K);
   constexpr K kNone = (K)(-Traits<T>::kMaxKey - 1);  // never a valid key
   extern __shared__ __align__(16) unsigned char smem[];

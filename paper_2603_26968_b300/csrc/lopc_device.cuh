@@ -14,7 +14,6 @@ namespace lopc {
 constexpr int kHeaderBytes = 128;
 constexpr uint32_t kMagic = 0x43504F4Cu;  // "LOPC"
 constexpr uint32_t kRawFlag = 0x80000000u;
-constexpr int kSegment = 16;  // points a thread owns along x in a tile
 
 // Status bits collected on the device and mapped to a return code on the host.
 enum : uint32_t {
