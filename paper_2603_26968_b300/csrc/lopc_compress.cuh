@@ -94,17 +94,37 @@ __global__ void k_range(const FieldInfo* F, int f0) {
   Params* P = fi.P;
   K lo = Traits<T>::kMaxKey, hi = -Traits<T>::kMaxKey;
   bool bad = false;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const T v = x[i];
+  auto take = [&](T v) {
     if (!is_finite_bits<T>(v)) {
       bad = true;
-      continue;
+      return;
     }
     const K k = order_key<T>(v);
     lo = min(lo, k);
     hi = max(hi, k);
+  };
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // 16-byte loads over the aligned body, single values over the head and tail
+  constexpr int V = 16 / (int)sizeof(T);
+  const int64_t head = (int64_t)(((16 - (reinterpret_cast<uintptr_t>(x) & 15)) & 15) / sizeof(T));
+  const int64_t h = head < n ? head : n;
+  const int64_t nv = (n - h) / V;
+  const uint4* xv = reinterpret_cast<const uint4*>(x + h);
+  for (int64_t i = t0; i < nv; i += stride) {
+    const uint4 u = __ldg(&xv[i]);
+    if constexpr (sizeof(T) == 4) {
+      take(__uint_as_float(u.x));
+      take(__uint_as_float(u.y));
+      take(__uint_as_float(u.z));
+      take(__uint_as_float(u.w));
+    } else {
+      take(Traits<T>::from_bits(((uint64_t)u.y << 32) | u.x));
+      take(Traits<T>::from_bits(((uint64_t)u.w << 32) | u.z));
+    }
   }
+  for (int64_t i = t0; i < h; i += stride) take(x[i]);
+  for (int64_t i = h + nv * V + t0; i < n; i += stride) take(x[i]);
   unsigned long long blo = biased<T>(lo), bhi = biased<T>(hi);
   for (int o = 16; o; o >>= 1) {
     blo = min(blo, __shfl_xor_sync(0xffffffffu, blo, o));
@@ -942,7 +962,14 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC) k_encode_sub(const FieldI
   const TileBox tb = tile_box(g, tid);
   const int n = tb.n, n32 = (n + 31) & ~31;
   const int64_t plane = g.ny * g.nx;
-  if (n == G::NP) {
+  if (n == G::NP && W == 4) {  // subbins are already words: asynchronous copies
+    for (int i = threadIdx.x; i < n; i += NT) {
+      const int lx = i % G::TX, ly = (i / G::TX) % G::TY, lz = i / (G::TX * G::TY);
+      cp_async4(&ws[i], &s_glob[(tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx], true);
+    }
+    cp_async_wait_all();
+  } else if (n == G::NP) {
+#pragma unroll 4
     for (int i = threadIdx.x; i < n; i += NT) {
       const int lx = i % G::TX, ly = (i / G::TX) % G::TY, lz = i / (G::TX * G::TY);
       ws[i] = (W_t)s_glob[(tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx];
