@@ -325,7 +325,7 @@ int launch_class_pre(const Table& t, int c, const FieldInfo* dF, cudaStream_t st
 }
 
 template <typename T, int ND>
-int launch_class_rerun(const Table& t, int c, const FieldInfo* dF, const BatchState* dB, const uint32_t* list,
+int launch_class_rerun(const Table& t, int c, const FieldInfo* dF, BatchState* dB, const uint32_t* list,
                        cudaStream_t st) {
   using C = TileCfg<T, ND>;
   if (!t.cls_nf[c]) return LOPC_OK;
@@ -359,8 +359,9 @@ int launch_pre(const Table& t, const FieldInfo* dF, cudaStream_t st) {
 }
 
 // One rerun round: of every tile (list == null, the first round) or of the listed ones.
-int launch_reruns(const Table& t, const FieldInfo* dF, const BatchState* dB, const uint32_t* list, cudaStream_t st) {
+int launch_reruns(const Table& t, const FieldInfo* dF, BatchState* dB, const uint32_t* list, cudaStream_t st) {
   int rc;
+  if (!list) CK(cudaMemsetAsync(dB->next_all, 0, sizeof(dB->next_all), st));  // the all-tile round's counters
   if ((rc = launch_class_rerun<float, 2>(t, 0, dF, dB, list, st))) return rc;
   if ((rc = launch_class_rerun<float, 3>(t, 1, dF, dB, list, st))) return rc;
   if ((rc = launch_class_rerun<double, 2>(t, 2, dF, dB, list, st))) return rc;

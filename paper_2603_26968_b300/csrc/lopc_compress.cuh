@@ -717,7 +717,7 @@ struct RerunSmem {
 template <typename T, int ND>
 __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN)
     k_rerun(const FieldInfo* __restrict__ F, int f0, int nf, int64_t tile0, int64_t ntile_cls, int cls,
-            const BatchState* __restrict__ B, const uint32_t* __restrict__ list) {
+            BatchState* __restrict__ B, const uint32_t* __restrict__ list) {
   using G = TileGeom<T, ND>;
   using RS = RerunSmem<T, ND>;
   constexpr int NT = G::NT;
@@ -730,11 +730,19 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
   uint16_t* flist = reinterpret_cast<uint16_t*>(smem + RS::LIST);
   uint32_t* queue = reinterpret_cast<uint32_t*>(smem + RS::QUEUE);
   __shared__ uint32_t qn;
-  // the first round (list == nullptr) visits every tile of the class
+  __shared__ unsigned s_item;
+  // the first round (list == nullptr) visits every tile of the class; blocks take
+  // items from a counter, so a slow tile holds up only its own block
   const int64_t count = list ? (int64_t)B->count[cls] : ntile_cls;
   const uint32_t* lst = list ? list + B->off[cls] : nullptr;
+  unsigned* next = list ? &B->next[cls] : &B->next_all[cls];
 #pragma unroll 1
-  for (int64_t item = blockIdx.x; item < count; item += gridDim.x) {
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(next, 1u);
+    __syncthreads();
+    const int64_t item = (int64_t)s_item;
+    __syncthreads();  // s_item is rewritten for the next item
+    if (item >= count) break;
     const int64_t gt = lst ? (int64_t)lst[item] : tile0 + item;
     const FieldInfo& fi = F[field_of_tile(F, f0, nf, gt)];
     Params* P = fi.P;
@@ -910,6 +918,7 @@ __global__ void __launch_bounds__(NT) k_compact(const FieldInfo* __restrict__ F,
     for (int c = 0; c < 4; ++c) {
       B->count[c] = cnt[c];
       B->off[c] = o;
+      B->next[c] = 0;
       o += cnt[c];
     }
     B->rounds += 1;

@@ -403,6 +403,8 @@ __host__ __device__ inline int class_of_geometry(const Geometry& g) {
 struct BatchState {
   unsigned int count[4];      // tiles to rerun per class this round
   unsigned int off[4];        // their first position in the list
+  unsigned int next[4];       // per class: the next listed item a rerun block takes
+  unsigned int next_all[4];   // per class: the next tile of the all-tile round
   unsigned long long rounds;  // repair rounds done
   unsigned long long runs;    // tile runs launched (first round included)
   unsigned int cap_hit;
