@@ -113,8 +113,10 @@ struct DecSmem {
   static constexpr uint32_t L = (uint32_t)NP * W;                                   // planes of a full tile
   static constexpr uint32_t LR = (L + L / 8 + L / 64 + L / 512 + 16 + 15) & ~15u;  // largest legal RZE_w output
   static constexpr uint32_t CACHE = 16384;                                          // bytes of bin-lowest keys
-  // A: staged record / subbin planes; B: bin planes / RZE_w bytes; C: key cache; WB: bins
-  static constexpr size_t bytes() { return (size_t)L + LR + CACHE + (size_t)NP * W + RzeWork::bytes(LR) + 16; }
+  static constexpr uint32_t BB = LR > CACHE ? LR : CACHE;
+  // A: staged record / subbin planes; B: RZE output, or the key cache between the two
+  // halves; WB: bins, then each point's bin-lowest key
+  static constexpr size_t bytes() { return (size_t)L + BB + (size_t)NP * W + RzeWork::bytes(LR) + 16; }
 };
 
 __device__ __forceinline__ uint32_t shfl_up_w(uint32_t v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
@@ -127,7 +129,7 @@ __device__ __forceinline__ uint64_t shfl_idx_w(uint64_t v, int l) { return __shf
 // subbins (RZE_1, RZE_w, BIT_w inverses) and x_hat = the subbin-th value above the
 // bin's lowest value (Sec. III-E), written as the subbin words come out.
 template <typename T, int ND>
-__global__ void __launch_bounds__(TileCfg<T, ND>::NTC) k_decode(const DecField* __restrict__ F, int f0, int nf,
+__global__ void __launch_bounds__(TileCfg<T, ND>::NTC, 4) k_decode(const DecField* __restrict__ F, int f0, int nf,
                                                                int64_t tile0) {
   using G = TileGeom<T, ND>;
   using DS = DecSmem<T, ND>;
@@ -140,8 +142,8 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC) k_decode(const DecField* 
   extern __shared__ __align__(16) unsigned char smem[];
   uint8_t* A = smem;
   uint8_t* Bf = smem + DS::L;
-  K* cache = reinterpret_cast<K*>(smem + DS::L + DS::LR);
-  W_t* wb = reinterpret_cast<W_t*>(smem + DS::L + DS::LR + DS::CACHE);
+  K* cache = reinterpret_cast<K*>(Bf);  // between the halves, B holds the key cache
+  W_t* wb = reinterpret_cast<W_t*>(smem + DS::L + DS::BB);
   const RzeWork w = rze_work_at(reinterpret_cast<uint8_t*>(wb + DS::NP), DS::LR);
   __shared__ int bad;
   __shared__ B red_min[NT / 32], red_max[NT / 32];
@@ -280,23 +282,25 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC) k_decode(const DecField* 
     }
   }
   __syncthreads();
-  dec_mark(2, t0);
-
-  const int64_t plane = g.ny * g.nx;
+  // every point's bin becomes its bin's lowest key, in place; the cache is then dead
   bool fail = false;
-  auto put = [&](int i, uint64_t s) {
+  for (int i = threadIdx.x; i < n; i += NT) {
     const long long b = (long long)(B)wb[i];
     K k;
     if (cached) {
       k = cache[b - (long long)bmin];
-      if (k == kNone) {
-        fail = true;
-        return;
-      }
     } else if (!lowest_key_in_bin<T>(b, di.eps_q, di.inv_m, di.inv_e, k)) {
-      fail = true;
-      return;
+      k = kNone;
     }
+    if (k == kNone) fail = true;
+    wb[i] = (W_t)k;
+  }
+  __syncthreads();
+  dec_mark(2, t0);
+
+  const int64_t plane = g.ny * g.nx;
+  auto put = [&](int i, uint64_t s) {
+    const K k = (K)wb[i];
     if (s > (uint64_t)(long long)Traits<T>::kMaxKey - (uint64_t)(long long)k) {
       fail = true;
       return;
