@@ -173,6 +173,38 @@ struct WarpRange {
   }
 };
 
+// Exclusive block scan of three counters at once, with one barrier: a[j] receives the
+// sum of v[j] over the threads before this one, tot[j] the block's sum.  `tmp` holds
+// 3 * NT/32 words and must not be reused before the next barrier.
+template <int NT>
+__device__ __forceinline__ void block_exclusive_scan3(const uint32_t v[3], uint32_t* tmp, uint32_t a[3],
+                                                      uint32_t tot[3]) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t x[3] = {v[0], v[1], v[2]};
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x[j], o);
+      if (lane >= o) x[j] += y;
+    }
+  }
+  if (lane == 31)
+    for (int j = 0; j < 3; ++j) tmp[3 * wid + j] = x[j];
+  __syncthreads();
+  for (int j = 0; j < 3; ++j) {
+    uint32_t base = 0, all = 0;
+    for (int k = 0; k < NW; ++k) {
+      const uint32_t t = tmp[3 * k + j];
+      base += k < wid ? t : 0u;
+      all += t;
+    }
+    a[j] = base + x[j] - v[j];
+    tot[j] = all;
+  }
+}
+
 // RZE_g encode of `in` (L bytes, shared memory, 16-byte aligned) into `out` (shared
 // memory): [level-2 bitmap][level-1 kept][level-0 kept][non-zero units].  Nothing is
 // written when the result would not be shorter than `limit`.  Returns its length.
@@ -207,13 +239,7 @@ __device__ uint32_t rze_encode(const uint8_t* in, uint32_t L, uint8_t* out, uint
     w.m1[jj] = (uint8_t)byte;
     c1 += __popc(byte);
   }
-  // per-warp payload totals, then the block-wide order of warps
-  uint32_t wtot;
-  warp_exclusive_scan(c0, &wtot);
-  uint32_t np, nk0;
-  const uint32_t wbase = block_exclusive_scan<NT, uint32_t>(lane == 0 ? wtot : 0u, w.tmp, &np);
-  const uint32_t warp_base = __shfl_sync(0xffffffffu, wbase, 0);
-  const uint32_t k0_off = block_exclusive_scan<NT, uint32_t>(c1, w.tmp, &nk0);
+  __syncthreads();  // level 1 complete
   // level 2: each thread owns one level-2 byte (8 level-1 bytes)
   uint32_t c2 = 0;
   if ((uint32_t)t < l2) {
@@ -227,8 +253,15 @@ __device__ uint32_t rze_encode(const uint8_t* in, uint32_t L, uint8_t* out, uint
     w.m2[t] = (uint8_t)byte;
     c2 = __popc(byte);
   }
-  uint32_t nk1;
-  const uint32_t k1_off = block_exclusive_scan<NT, uint32_t>(c2, w.tmp, &nk1);
+  // one scan: warps' payload bases, level-0 kept offsets, level-1 kept offsets
+  uint32_t wtot;
+  warp_exclusive_scan(c0, &wtot);
+  const uint32_t sv3[3] = {lane == 0 ? wtot : 0u, c1, c2};
+  uint32_t ex3[3], tot3[3];
+  block_exclusive_scan3<NT>(sv3, w.tmp, ex3, tot3);
+  const uint32_t warp_base = __shfl_sync(0xffffffffu, ex3[0], 0);
+  const uint32_t k0_off = ex3[1], k1_off = ex3[2];
+  const uint32_t np = tot3[0], nk0 = tot3[1], nk1 = tot3[2];
   const uint32_t total = l2 + nk1 + nk0 + np * G;
   if (total >= limit) return total;
   if ((uint32_t)t < l2) {
