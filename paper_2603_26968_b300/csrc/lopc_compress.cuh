@@ -193,16 +193,19 @@ __global__ void k_resolve_eps(const FieldInfo* F, int f0, int nf) {
 constexpr uint32_t kSlotBytes = 16384;  // a record never exceeds the raw chunk (16 KiB)
 
 // Shared-memory geometry of a tile with its 1-point halo, and the thread mapping:
-// thread t owns the 16 points (lz, 16*sy + j, lx), j = 0..15, of one y-segment, with
-// t = (lz * SEGY + sy) * TX + lx, so the lanes of a warp walk consecutive x.  Rows
-// are padded to an odd pitch and z-planes to a pitch = 16 (mod 32) so that the two
-// x-runs of 16 lanes a warp touches fall in distinct banks.
-template <typename T, int ND>
+// thread t owns the SEG points (lz, SEG*sy + j, lx), j = 0..SEG-1, of one y-segment,
+// with t = (lz * SEGY + sy) * TX + lx, so the lanes of a warp walk consecutive x.
+// Z-planes have a pitch = 16 (mod 32) so that the two x-runs of 16 lanes a warp
+// touches fall in distinct banks.  Rows have an odd pitch (A16 = false, the tightest
+// layout), or a pitch that is a multiple of 4 words with the first interior point
+// at entry 4 (A16 = true), so that interior rows start on 16-byte boundaries.
+template <typename T, int ND, bool A16 = false>
 struct TileGeom {
   using C = TileCfg<T, ND>;
   static constexpr int TZ = C::TZ, TY = C::TY, TX = C::TX, HZ = C::HZ, NT = C::NT, SEG = C::SEG;
   static constexpr int BZ = TZ + 2 * HZ, BY = TY + 2, BX = TX + 2;
-  static constexpr int BXP = (BX % 2) ? BX : BX + 1;
+  static constexpr int XO = A16 ? 4 : 1;  // entry of interior column 0 within a row
+  static constexpr int BXP = A16 ? ((TX + 8 + 3) & ~3) : ((BX % 2) ? BX : BX + 1);
   static constexpr int PP = HZ ? ((BY * BXP + 15) / 32) * 32 + 16 : BY * BXP;
   static constexpr int E = BZ * PP;               // shared-memory entries
   static constexpr int NP = TZ * TY * TX;         // points of a full tile
@@ -210,7 +213,7 @@ struct TileGeom {
   static_assert(TZ * SEGY * TX == NT, "one y-segment per thread");
   static_assert(TX >= 16, "a half warp spans one x-run");
   __device__ static constexpr int off(int dz, int dy, int dx) { return dz * PP + dy * BXP + dx; }
-  __device__ static constexpr int entry(int lz, int ly, int lx) { return (lz + HZ) * PP + (ly + 1) * BXP + lx + 1; }
+  __device__ static constexpr int entry(int lz, int ly, int lx) { return (lz + HZ) * PP + (ly + 1) * BXP + lx + XO; }
   // linear index of a tile point (masks are kept for the tile's own points only)
   __device__ static constexpr int lin(int lz, int ly, int lx) { return (lz * TY + ly) * TX + lx; }
   __device__ static constexpr int loff(int dz, int dy, int dx) { return (dz * TY + dy) * TX + dx; }
@@ -263,31 +266,50 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Asynchronous copy of a tile's box (the tile and a one-point halo; 2D tiles have no
 // z halo) of `src` (row-major field of nz x ny x nx elements of `Word`) into shared
 // memory at `dst` (entry layout of G).  Rows are walked as (row, column) with one
-// row base per row: the 16 interior columns go to 16 lanes, the two halo columns
-// are a second loop.  Absent points read nothing and are zero.  The caller waits.
+// row base per row: the interior columns go to lanes (16-byte copies of four words
+// when the layout and the field allow it), the two halo columns are a second loop.
+// Absent points read nothing and are zero.  The caller waits.
 template <typename G, typename Word>
 __device__ __forceinline__ void load_box_async(Word* dst, const Word* __restrict__ src, const Geometry& g,
                                                const TileBox& tb) {
   static_assert(G::TX == 16 || G::TX == 64, "interior columns are whole lane groups");
   constexpr int NT = G::NT, ROWS = G::BZ * G::BY;
-  constexpr int CW = G::TX < 32 ? G::TX : 32;  // lanes per row
-  constexpr int RPP = NT / CW;                 // rows per pass
   const int64_t plane = g.ny * g.nx;
-  const int c = threadIdx.x % CW;
-  for (int r = threadIdx.x / CW; r < ROWS; r += RPP) {
-    const int ly = r % G::BY, lz = r / G::BY;
-    const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1;
-    const bool row_in = gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny;
-    const Word* row = src + (row_in ? gz * plane + gy * g.nx : 0);
-    Word* drow = dst + lz * G::PP + ly * G::BXP;
+  constexpr int V = 16 / (int)sizeof(Word);  // words per 16-byte copy
+  if (G::XO % V == 0 && G::BXP % V == 0 && G::PP % V == 0 && g.nx % V == 0) {
+    // every interior row starts on a 16-byte boundary in shared and global memory,
+    // and a copy of V words is either wholly inside the field or wholly outside
+    constexpr int CW = G::TX / V;  // copies per row
+    constexpr int RPP = NT / CW;
+    const int c = threadIdx.x % CW;
+    for (int r = threadIdx.x / CW; r < ROWS; r += RPP) {
+      const int ly = r % G::BY, lz = r / G::BY;
+      const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1;
+      const int64_t gx = tb.x0 + (int64_t)c * V;
+      const bool in = gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx < g.nx;
+      const unsigned d = (unsigned)__cvta_generic_to_shared(dst + lz * G::PP + ly * G::BXP + G::XO + c * V);
+      const Word* sp = in ? src + gz * plane + gy * g.nx + gx : src;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(sp), "r"(in ? 16 : 0) : "memory");
+    }
+  } else {
+    constexpr int CW = G::TX < 32 ? G::TX : 32;  // lanes per row
+    constexpr int RPP = NT / CW;                 // rows per pass
+    const int c = threadIdx.x % CW;
+    for (int r = threadIdx.x / CW; r < ROWS; r += RPP) {
+      const int ly = r % G::BY, lz = r / G::BY;
+      const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1;
+      const bool row_in = gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny;
+      const Word* row = src + (row_in ? gz * plane + gy * g.nx : 0);
+      Word* drow = dst + lz * G::PP + ly * G::BXP + G::XO;
 #pragma unroll
-    for (int lx = c; lx < G::TX; lx += CW) {
-      const int64_t gx = tb.x0 + lx;
-      const bool in = row_in && gx < g.nx;
-      if (sizeof(Word) == 4)
-        cp_async4(&drow[lx + 1], in ? row + gx : src, in);
-      else
-        cp_async8(&drow[lx + 1], in ? row + gx : src, in);
+      for (int lx = c; lx < G::TX; lx += CW) {
+        const int64_t gx = tb.x0 + lx;
+        const bool in = row_in && gx < g.nx;
+        if (sizeof(Word) == 4)
+          cp_async4(&drow[lx], in ? row + gx : src, in);
+        else
+          cp_async8(&drow[lx], in ? row + gx : src, in);
+      }
     }
   }
   // the halo columns x0 - 1 and x0 + TX
@@ -297,7 +319,7 @@ __device__ __forceinline__ void load_box_async(Word* dst, const Word* __restrict
     const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1;
     const int64_t gx = side ? tb.x0 + G::TX : tb.x0 - 1;
     const bool in = gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx >= 0 && gx < g.nx;
-    Word* d = dst + lz * G::PP + ly * G::BXP + (side ? G::TX + 1 : 0);
+    Word* d = dst + lz * G::PP + ly * G::BXP + (side ? G::XO + G::TX : G::XO - 1);
     if (sizeof(Word) == 4)
       cp_async4(d, in ? src + gz * plane + gy * g.nx + gx : src, in);
     else
@@ -319,14 +341,14 @@ __device__ __forceinline__ void for_box(const Geometry& g, const TileBox& tb, Fn
     const bool row_in = gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny;
     const int e0 = lz * G::PP + ly * G::BXP;
 #pragma unroll
-    for (int lx = c; lx < G::TX; lx += CW) fn(e0 + lx + 1, row_in && tb.x0 + lx < g.nx);
+    for (int lx = c; lx < G::TX; lx += CW) fn(e0 + G::XO + lx, row_in && tb.x0 + lx < g.nx);
   }
   for (int i = threadIdx.x; i < 2 * ROWS; i += NT) {
     const int r = i >> 1, side = i & 1;
     const int ly = r % G::BY, lz = r / G::BY;
     const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1;
     const int64_t gx = side ? tb.x0 + G::TX : tb.x0 - 1;
-    fn(lz * G::PP + ly * G::BXP + (side ? G::TX + 1 : 0),
+    fn(lz * G::PP + ly * G::BXP + (side ? G::XO + G::TX : G::XO - 1),
        gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx >= 0 && gx < g.nx);
   }
 }
@@ -695,9 +717,9 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
 
 template <typename T, int ND>
 struct RerunSmem {
-  using G = TileGeom<T, ND>;
+  using G = TileGeom<T, ND, true>;
   // boundary points of a tile: an upper bound for the queue of risen boundary points
-  static constexpr int QMAX = 2 * (G::TY * G::TX + (G::HZ ? G::TZ * G::TX + G::TZ * G::TY : G::TX + G::TY));
+  static constexpr int QMAX = G::HZ ? 2 * (G::TY * G::TX + G::TZ * G::TX + G::TZ * G::TY) : 2 * (G::TX + G::TY);
   static constexpr size_t up16(size_t v) { return (v + 15) & ~(size_t)15; }
   static constexpr size_t CM = (size_t)G::E * 4;                      // subbins, then lower masks
   static constexpr size_t BITS = CM + up16((size_t)G::NP * 4);        // frontiers, risen bits, counters
@@ -718,7 +740,7 @@ template <typename T, int ND>
 __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN)
     k_rerun(const FieldInfo* __restrict__ F, int f0, int nf, int64_t tile0, int64_t ntile_cls, int cls,
             BatchState* __restrict__ B, const uint32_t* __restrict__ list) {
-  using G = TileGeom<T, ND>;
+  using G = TileGeom<T, ND, true>;  // interior rows on 16-byte boundaries
   using RS = RerunSmem<T, ND>;
   constexpr int NT = G::NT;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -760,11 +782,24 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
     // subbins of the box and lower masks of the tile's own points, by asynchronous
     // copies (absent points read nothing and are zero)
     load_box_async<G, uint32_t>(sv, s_glob, g, tb);
-    for (int o = threadIdx.x; o < G::NP; o += NT) {
-      const int lx = o % G::TX, ly = (o / G::TX) % G::TY, lz = o / (G::TX * G::TY);
-      const bool in = lz < tb.cz && ly < tb.cy && lx < tb.cx;
-      const int64_t gi = (tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx;
-      cp_async4(&cm[o], in ? &cm_glob[gi] : cm_glob, in);
+    if ((g.nx & 3) == 0) {  // four masks per 16-byte copy (a copy is wholly inside or outside)
+      for (int i = threadIdx.x; i < G::NP / 4; i += NT) {
+        const int o = 4 * i;
+        const int lx = o % G::TX, ly = (o / G::TX) % G::TY, lz = o / (G::TX * G::TY);
+        const bool in = lz < tb.cz && ly < tb.cy && lx < tb.cx;
+        const int64_t gi = (tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx;
+        const unsigned d = (unsigned)__cvta_generic_to_shared(&cm[o]);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(in ? &cm_glob[gi] : cm_glob),
+                     "r"(in ? 16 : 0)
+                     : "memory");
+      }
+    } else {
+      for (int o = threadIdx.x; o < G::NP; o += NT) {
+        const int lx = o % G::TX, ly = (o / G::TX) % G::TY, lz = o / (G::TX * G::TY);
+        const bool in = lz < tb.cz && ly < tb.cy && lx < tb.cx;
+        const int64_t gi = (tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx;
+        cp_async4(&cm[o], in ? &cm_glob[gi] : cm_glob, in);
+      }
     }
     for (int i = threadIdx.x; i < 3 * (G::NP / 32); i += NT) fa0[i] = 0;  // frontiers, risen bits
     if (threadIdx.x == 0) qn = 0;
