@@ -224,18 +224,23 @@ def batch_leg(torch, lopc, fields_np, specs, flush, args):
 
 
 def serve_leg(torch, lopc, args):
+    """Poisson serving at the configured rate, then at half of it (below saturation)."""
     from paper_2603_26968_b300 import serve, synth_gpu as SG
-    specs = SG.serve_requests(args.seed, args.serve_rate, args.serve_seconds)
-    offered = SG.offered_load(specs, args.serve_seconds) / 1e9
     srv = serve.Server(serve.default_budget(), max_fields=1024, rounds_per_step=args.serve_rounds)
     # warm the engine's kernels on one small request (not counted)
     srv.run(SG.serve_requests(args.seed + 99, 1000.0, 0.01, min_bytes=1e6, max_bytes=4e6)[:2])
-    rep = srv.run(specs)
+    runs = []
+    for rate in (args.serve_rate, args.serve_rate / 2):
+        specs = SG.serve_requests(args.seed, rate, args.serve_seconds)
+        offered = SG.offered_load(specs, args.serve_seconds) / 1e9
+        rep = srv.run(specs)
+        out = serve.summary(rep, offered)
+        out.update({"rate_per_s": rate, "seconds": args.serve_seconds, "rounds_per_step": args.serve_rounds})
+        runs.append(out)
     srv.close()
-    out = serve.summary(rep, offered)
-    out.update({"rate_per_s": args.serve_rate, "seconds": args.serve_seconds,
-                "rounds_per_step": args.serve_rounds})
-    return out
+    res = dict(runs[0])
+    res["half_rate"] = runs[1]
+    return res
 
 
 def main():

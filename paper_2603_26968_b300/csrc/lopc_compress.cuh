@@ -917,35 +917,39 @@ __global__ void __launch_bounds__(NT) k_compact(const FieldInfo* __restrict__ F,
     if (field_counts) field_counts[f] = 0;
   }
   __syncthreads();
-  unsigned int run = 0;
-  for (int64_t base = 0; base < total_words; base += NT) {
-    const int64_t w = base + threadIdx.x;
-    uint32_t bits = 0;
-    int k = 0;
-    if (w < total_words) {
-      k = field_of_word(F, nf, w);
-      uint32_t* dw = F[k].dirty + (w - F[k].word_base);
-      const uint32_t v = *dw;  // four byte flags
-      if (v) {
-        *dw = 0u;
-        bits = (v & 0xffu ? 1u : 0u) | (v & 0xff00u ? 2u : 0u) | (v & 0xff0000u ? 4u : 0u) | (v & 0xff000000u ? 8u : 0u);
-        if ((long long)F[k].P->rounds > F[k].round_cap) {
-          atomicOr(&F[k].P->status, kErrNotConverged);
-          capped = 1;
-          bits = 0;
-        }
-      }
+  // each thread owns a contiguous range of flag words: count, one scan, then list
+  const int64_t per = (total_words + NT - 1) / NT;
+  const int64_t a = min(total_words, (int64_t)threadIdx.x * per), b = min(total_words, a + per);
+  auto bits_of = [](uint32_t v) {  // four byte flags -> four bits
+    return (v & 0xffu ? 1u : 0u) | (v & 0xff00u ? 2u : 0u) | (v & 0xff0000u ? 4u : 0u) | (v & 0xff000000u ? 8u : 0u);
+  };
+  unsigned int n = 0;
+  int k = a < b ? field_of_word(F, nf, a) : 0;
+  for (int64_t w = a; w < b; ++w) {
+    while (k + 1 < nf && F[k + 1].word_base <= w) ++k;
+    const uint32_t v = F[k].dirty[w - F[k].word_base];
+    if (v && (long long)F[k].P->rounds <= F[k].round_cap) n += __popc(bits_of(v));
+  }
+  unsigned int tot;
+  unsigned int pos = block_exclusive_scan<NT, unsigned int>(n, tmp, &tot);
+  k = a < b ? field_of_word(F, nf, a) : 0;
+  for (int64_t w = a; w < b; ++w) {
+    while (k + 1 < nf && F[k + 1].word_base <= w) ++k;
+    uint32_t* dw = F[k].dirty + (w - F[k].word_base);
+    const uint32_t v = *dw;
+    if (!v) continue;
+    *dw = 0u;
+    if ((long long)F[k].P->rounds > F[k].round_cap) {  // past the cap: drop the tiles, fail the field
+      atomicOr(&F[k].P->status, kErrNotConverged);
+      capped = 1;
+      continue;
     }
-    const unsigned int n = __popc(bits);
-    unsigned int tot;
-    unsigned int pos = block_exclusive_scan<NT, unsigned int>(n, tmp, &tot) + run;
-    if (n) {
-      const int64_t t0 = F[k].tile_base + 4 * (w - F[k].word_base);
-      for (uint32_t b = bits; b; b &= b - 1) list[pos++] = (uint32_t)(t0 + __ffs(b) - 1);
-      atomicAdd(&cnt[class_of_geometry(F[k].g)], n);
-      if (field_counts) atomicAdd(&field_counts[k], n);
-    }
-    run += tot;
+    const uint32_t bits = bits_of(v);
+    const int64_t t0 = F[k].tile_base + 4 * (w - F[k].word_base);
+    for (uint32_t bb = bits; bb; bb &= bb - 1) list[pos++] = (uint32_t)(t0 + __ffs(bb) - 1);
+    const unsigned int c = __popc(bits);
+    atomicAdd(&cnt[class_of_geometry(F[k].g)], c);
+    if (field_counts) atomicAdd(&field_counts[k], c);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -957,9 +961,9 @@ __global__ void __launch_bounds__(NT) k_compact(const FieldInfo* __restrict__ F,
       o += cnt[c];
     }
     B->rounds += 1;
-    B->runs += run;
+    B->runs += tot;
     B->cap_hit |= (unsigned int)capped;
-    if (use_handle) cudaGraphSetConditional(handle, run ? 1u : 0u);
+    if (use_handle) cudaGraphSetConditional(handle, tot ? 1u : 0u);
   }
 }
 
