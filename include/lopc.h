@@ -258,6 +258,17 @@ LOPC_API int lopc_engine_sync(lopc_engine* e);
 LOPC_API void lopc_tune_set(const int* rerun_blocks_per_sm);
 LOPC_API void lopc_tune_get(int* rerun_blocks_per_sm);
 
+/* Launch tuning of the tile pass's fixpoint, per field class; later calls on this
+ * thread use it and output bytes never depend on it.  A tile whose same-bin
+ * neighbour pairs exceed dense/16 of a full tile's pairs is solved in topological
+ * order at once (default 8; 17 = never; clamped to [0, 17]); any other tile runs
+ * frontier sweeps until they have spent budget/16 evaluations per point (default 64;
+ * clamped to [1, 4096]) and then finishes in topological order. */
+LOPC_API void lopc_tune_set_budget(const int* sixteenths);
+LOPC_API void lopc_tune_get_budget(int* sixteenths);
+LOPC_API void lopc_tune_set_dense(const int* sixteenths);
+LOPC_API void lopc_tune_get_dense(int* sixteenths);
+
 /* Human-readable text of a status code (static storage). */
 LOPC_API const char* lopc_strerror(int status);
 

@@ -299,6 +299,12 @@ int sm_count() {
 
 // Persistent rerun blocks per SM, per class (set by lopc_tune_set).
 thread_local int g_rerun_per_sm[4] = {3, 3, 6, 6};
+// Frontier evaluations of a tile pass before it switches to the topological order,
+// in sixteenths of the tile's points, per class (set by lopc_tune_set_budget).
+thread_local int g_pass_budget16[4] = {64, 64, 64, 64};
+// Same-bin neighbour pairs, in sixteenths of a full tile's pairs, above which a tile
+// pass goes straight to the topological order (set by lopc_tune_set_dense; 17 = never).
+thread_local int g_pass_dense16[4] = {8, 8, 8, 8};
 
 int rerun_blocks(int c) { return sm_count() * g_rerun_per_sm[c]; }
 
@@ -318,8 +324,8 @@ int launch_class_pre(const Table& t, int c, const FieldInfo* dF, cudaStream_t st
   LAUNCH("range", st, k_range<T><<<dim3(sm_count() * 4, t.cls_nf[c]), 256, 0, st>>>(dF, t.cls_f0[c]));
   LAUNCH("resolve_eps", st, k_resolve_eps<T><<<(t.cls_nf[c] + 63) / 64, 64, 0, st>>>(dF, t.cls_f0[c], t.cls_nf[c]));
   LAUNCH("tile_pass", st,
-         k_pass<T, ND><<<(unsigned)t.cls_nt[c], C::NT, PassSmem<T, ND>::bytes(), st>>>(dF, t.cls_f0[c], t.cls_nf[c],
-                                                                                      t.cls_t0[c]));
+         k_pass<T, ND><<<(unsigned)t.cls_nt[c], C::NT, PassSmem<T, ND>::bytes(), st>>>(
+             dF, t.cls_f0[c], t.cls_nf[c], t.cls_t0[c], (unsigned)g_pass_budget16[c], (unsigned)g_pass_dense16[c]));
   CK(cudaGetLastError());
   return LOPC_OK;
 }
@@ -588,7 +594,8 @@ std::vector<uint64_t> plan_key(const CompressPlan& p, const uint8_t* ws) {
   k.push_back((uint64_t)dev);
   k.push_back((uint64_t)(uintptr_t)ws);
   k.push_back((uint64_t)p.t.n());
-  for (int c = 0; c < 4; ++c) k.push_back((uint64_t)rerun_blocks(c));
+  for (int c = 0; c < 4; ++c)
+    k.push_back((uint64_t)rerun_blocks(c) | ((uint64_t)g_pass_budget16[c] << 20) | ((uint64_t)g_pass_dense16[c] << 40));
   for (const FieldInfo& f : p.t.F) {
     const uint64_t* w = reinterpret_cast<const uint64_t*>(&f);
     for (size_t i = 0; i < sizeof(FieldInfo) / 8; ++i) k.push_back(w[i]);
@@ -1265,6 +1272,26 @@ void lopc_tune_set(const int* v) {
 void lopc_tune_get(int* v) {
   if (!v) return;
   for (int c = 0; c < 4; ++c) v[c] = g_rerun_per_sm[c];
+}
+
+void lopc_tune_set_budget(const int* v) {
+  if (!v) return;
+  for (int c = 0; c < 4; ++c) g_pass_budget16[c] = v[c] < 1 ? 1 : (v[c] > 4096 ? 4096 : v[c]);
+}
+
+void lopc_tune_get_budget(int* v) {
+  if (!v) return;
+  for (int c = 0; c < 4; ++c) v[c] = g_pass_budget16[c];
+}
+
+void lopc_tune_set_dense(const int* v) {
+  if (!v) return;
+  for (int c = 0; c < 4; ++c) g_pass_dense16[c] = v[c] < 0 ? 0 : (v[c] > 17 ? 17 : v[c]);
+}
+
+void lopc_tune_get_dense(int* v) {
+  if (!v) return;
+  for (int c = 0; c < 4; ++c) v[c] = g_pass_dense16[c];
 }
 
 // ------------------------------------------------------------ serving engine ABI

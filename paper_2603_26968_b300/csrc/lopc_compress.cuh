@@ -398,7 +398,8 @@ struct FixSmem {
 // sweep compacts the frontier bitmap into a list that all threads share evenly, so a
 // sweep costs about one evaluation per thread.  Raised subbins are visible to the
 // rest of the sweep at once; a neighbour read before it rose is queued again by
-// that rise.  Chaotic relaxation from lower bounds reaches the unique least fixpoint
+// that rise.  `over` is set, with the last frontier not evaluated, after `limit`
+// sweeps or before the evaluations would exceed `eval_budget`.  Chaotic relaxation from lower bounds reaches the unique least fixpoint
 // (Sec. III-E) whatever the schedule.  `cml[o]` holds, for tile point o (linear
 // order), its lower same-bin neighbours in bits 0-13, and in bits 16-29 its same-bin
 // upper neighbours inside the tile (SAME = false) or all its same-bin neighbours
@@ -408,7 +409,8 @@ struct FixSmem {
 template <typename G, bool SAME>
 __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint32_t* cml, uint32_t* fa, uint32_t* fb,
                                                  uint32_t* rb, unsigned* cnt, uint16_t* list, int limit, bool& over,
-                                                 unsigned& evals, unsigned& raises) {
+                                                 unsigned& evals, unsigned& raises,
+                                                 unsigned eval_budget = 0xffffffffu) {
   constexpr int NW = G::NP / 32, NT = G::NT;
   static_assert(NW <= NT, "one frontier word per thread");
   volatile uint32_t* vs = sv;
@@ -416,6 +418,7 @@ __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint32_t* c
   if (threadIdx.x == 0) cnt[0] = cnt[1] = 0;
   __syncthreads();
   int iter = 0;
+  unsigned spent = 0;  // evaluations so far (the same value in every thread)
   while (true) {
     // compact the frontier into the list; clear it for reuse two sweeps later
     uint32_t word = 0;
@@ -439,10 +442,11 @@ __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint32_t* c
     __syncthreads();
     const unsigned n = cnt[iter & 1];
     if (n == 0) break;
-    if (++iter > limit) {
+    if (++iter > limit || spent + n > eval_budget) {
       over = true;
       break;
     }
+    spent += n;
     if (threadIdx.x == 0) cnt[iter & 1] = 0;  // the counter of the next sweep
     for (unsigned i = threadIdx.x; i < n; i += NT) {
       const int o = list[i];
@@ -485,6 +489,128 @@ __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint32_t* c
 }
 
 
+// Tile-local least fixpoint in topological order (Kahn's algorithm), for the tile pass
+// where every point must be computed: a point is evaluated once, when all its
+// lower same-bin neighbours inside the tile are final, as
+//   s(p) = max over lower same-bin n of s(n) + [n after p]
+// (halo neighbours hold constants).  Each wave takes the ready list; a point's
+// evaluation releases its in-tile upper neighbours, and those whose last lower
+// neighbour it was form the next list.  The constraint graph is acyclic, so this is
+// the unique least fixpoint.  `cml[o]`: lower bits 0-13, in-tile upper bits 16-29;
+// `indeg`: NP bytes of scratch (read as words); `la`, `lb`: two lists of NP entries;
+// `cnt`: two counters.  Returns the number of waves.
+template <typename G, bool SAME>
+__device__ __forceinline__ int topo_fixpoint(uint32_t* sv, const uint32_t* cml, uint32_t* indeg, uint16_t* la,
+                                             uint16_t* lb, unsigned* cnt, const TileBox& tb, uint32_t* rb,
+                                             unsigned& evals, unsigned& raises) {
+  constexpr int NT = G::NT;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) cnt[0] = cnt[1] = 0;
+  __syncthreads();
+  // in-degrees (in-tile lower same-bin neighbours) and the first ready list
+  static_assert(G::NP % NT == 0, "a whole number of points per thread");
+  for (int o4 = threadIdx.x; o4 < G::NP / 4; o4 += NT) {
+    uint32_t word = 0;
+    unsigned readym = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int o = 4 * o4 + u;
+      int lz, ly, lx;
+      point_of_lin<G>(o, lz, ly, lx);
+      const bool real = lz < tb.cz && ly < tb.cy && lx < tb.cx;
+      const uint32_t d = real ? (uint32_t)__popc(cml[o] & 0x3FFFu & ~out_of_box_bits<G>(lz, ly, lx)) : 0xFFu;
+      word |= d << (8 * u);
+      readym |= (real && d == 0 ? 1u : 0u) << u;
+    }
+    indeg[o4] = word;
+    const unsigned r = __popc(readym);
+    unsigned incl = r;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += y;
+    }
+    const unsigned wt = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned base = 0;
+    if (lane == 31 && wt) base = atomicAdd(&cnt[0], wt);
+    base = __shfl_sync(0xffffffffu, base, 31) + incl - r;
+    for (unsigned m = readym; m; m &= m - 1) la[base++] = (uint16_t)(4 * o4 + __ffs(m) - 1);
+  }
+  __syncthreads();
+  unsigned n = cnt[0];
+  int cur = 0;
+  int wave = 0;
+  while (n) {
+    ++wave;
+    const uint16_t* lin_ = cur ? lb : la;
+    uint16_t* lout = cur ? la : lb;
+    unsigned* cout = &cnt[cur ^ 1];
+    for (unsigned b0 = 0; b0 < n; b0 += NT) {  // uniform trip count: every lane takes part in the scans
+      const unsigned i = b0 + threadIdx.x;
+      unsigned readym = 0;
+      int o = 0;
+      uint32_t m = 0;
+      if (i < n) {
+        o = lin_[i];
+        int lz, ly, lx;
+        point_of_lin<G>(o, lz, ly, lx);
+        const int e = G::entry(lz, ly, lx);
+        m = cml[o];
+        const uint32_t before = sv[e];
+        uint32_t best = before;
+#pragma unroll
+        for (int k = 0; k < 14; ++k) {
+          if (!G::HZ && dz_of(k) != 0) continue;
+          if (m & (1u << k)) {
+            const uint32_t cand = sv[e + G::off(dz_of(k), dy_of(k), dx_of(k))] + (k >= 7 ? 1u : 0u);
+            best = cand > best ? cand : best;
+          }
+        }
+        if (best != before) {
+          ++raises;
+          sv[e] = best;
+          if (rb) atomicOr(&rb[o >> 5], 1u << (o & 31));
+        }
+        ++evals;
+        // release the in-tile upper neighbours; record those this point made ready
+        const uint32_t um = SAME ? ((m >> 16) & ~m & ~out_of_box_bits<G>(lz, ly, lx)) : (m >> 16);
+#pragma unroll
+        for (int k = 0; k < 14; ++k) {
+          if (!G::HZ && dz_of(k) != 0) continue;
+          if (um & (1u << k)) {
+            const int q = o + G::loff(dz_of(k), dy_of(k), dx_of(k));
+            const uint32_t sh = 8u * (uint32_t)(q & 3);
+            const uint32_t old = atomicSub(&indeg[q >> 2], 1u << sh);
+            if (((old >> sh) & 0xFFu) == 1u) readym |= 1u << k;
+          }
+        }
+      }
+      const unsigned r = __popc(readym);
+      unsigned incl = r;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+      }
+      const unsigned wt = __shfl_sync(0xffffffffu, incl, 31);
+      unsigned base = 0;
+      if (lane == 31 && wt) base = atomicAdd(cout, wt);
+      base = __shfl_sync(0xffffffffu, base, 31) + incl - r;
+#pragma unroll
+      for (int k = 0; k < 14; ++k) {
+        if (!G::HZ && dz_of(k) != 0) continue;
+        if (readym & (1u << k)) lout[base++] = (uint16_t)(o + G::loff(dz_of(k), dy_of(k), dx_of(k)));
+      }
+    }
+    __syncthreads();
+    n = *cout;
+    if (threadIdx.x == 0) cnt[cur] = 0;  // the counter of the wave after next
+    cur ^= 1;
+    __syncthreads();
+  }
+  return wave;
+}
+
 template <typename T, int ND>
 struct PassSmem {
   using G = TileGeom<T, ND>;
@@ -496,10 +622,12 @@ struct PassSmem {
   static constexpr size_t RAa = (size_t)G::E * (sizeof(K) > 4 ? sizeof(K) : 4);
   static constexpr size_t RAb = (size_t)L + RzeWork::bytes(L);
   static constexpr size_t RA = up16(RAa > RAb ? RAa : RAb);
-  static constexpr size_t RB = up16((size_t)G::E * sizeof(B) > L ? (size_t)G::E * sizeof(B) : L);
+  // after the bin record, the bins' region holds the in-degrees and two ready lists
+  static constexpr size_t TOPO = (size_t)G::NP + 2 * FixSmem<G>::list_bytes();
+  static constexpr size_t max3(size_t a, size_t b, size_t c) { return a > b ? (a > c ? a : c) : (b > c ? b : c); }
+  static constexpr size_t RB = up16(max3((size_t)G::E * sizeof(B), (size_t)L, TOPO));
   static constexpr size_t RC = up16((size_t)G::NP * 4);                 // neighbour masks of the tile's points
-  static constexpr size_t RD = up16(FixSmem<G>::bits_bytes());         // frontiers, risen bits, counters
-  static_assert(FixSmem<G>::list_bytes() <= RB, "the frontier list reuses the bins");
+  static constexpr size_t RD = up16(FixSmem<G>::bits_bytes());         // frontier bits, counters
   static constexpr size_t bytes() { return RA + RB + RC + RD; }
 };
 
@@ -511,7 +639,7 @@ struct PassSmem {
 //   5. write subbins and lower masks (what reruns and the boundary check need).
 template <typename T, int ND>
 __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
-    k_pass(const FieldInfo* __restrict__ F, int f0, int nf, int64_t tile0) {
+    k_pass(const FieldInfo* __restrict__ F, int f0, int nf, int64_t tile0, unsigned budget16, unsigned dense16) {
   using G = TileGeom<T, ND>;
   using PS = PassSmem<T, ND>;
   using K = typename Traits<T>::Key;
@@ -539,7 +667,12 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   uint32_t* fb = fa + G::NP / 32;
   uint32_t* rb = fb + G::NP / 32;
   unsigned* cnt = rb + G::NP / 32;
-  uint16_t* list = reinterpret_cast<uint16_t*>(smem + PS::RA + PS::RB - FixSmem<G>::list_bytes());  // bins' region
+  // the fixpoint's lists, in the bins' region once they are dead: the frontier list,
+  // or (for a tile that needs the topological order) in-degrees and two ready lists
+  uint16_t* flist = reinterpret_cast<uint16_t*>(smem + PS::RA);
+  uint32_t* indeg = reinterpret_cast<uint32_t*>(smem + PS::RA);
+  uint16_t* la = reinterpret_cast<uint16_t*>(smem + PS::RA + G::NP);
+  uint16_t* lb = la + FixSmem<G>::list_bytes() / 2;
 
   const int64_t tid = gt - fi.tile_base;
   if (tid < 0 || tid >= g.ntiles) return;  // never for a consistent plan
@@ -558,6 +691,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   constexpr int NBOX = G::BZ * G::BY * G::BX;  // entries of the box (the rare error path walks them)
   load_box_async<G, Raw>(raw, reinterpret_cast<const Raw*>(x), g, tb);
   for (int i = threadIdx.x; i < 3 * (G::NP / 32); i += NT) fa[i] = 0;  // both frontiers, risen bits
+  if (threadIdx.x == 0) cnt[0] = 0;  // the same-bin pair count of the flags
   cp_async_wait_all();
   __syncthreads();
   bool bad = false;
@@ -595,16 +729,13 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   __syncthreads();
   phase_mark(P, 0, t0);
 
-  // 2. flags of the thread's y-segment.  With every subbin at 0, only a point with a
-  //    +1 constraint (a lower same-bin neighbour at a higher index, k >= 7) can rise
-  //    in the first sweep: those points are the first frontier, and the others are
-  //    queued when a lower neighbour rises.
-  //    A same-bin neighbour that is not lower is upper: inside the tile, those are
-  //    the points a rise must requeue.
+  // 2. flags of the thread's y-segment: the lower same-bin neighbours, and the upper
+  //    ones inside the tile (a same-bin neighbour that is not lower is upper), which a
+  //    rise requeues or the topological order releases.
   const SegPos sp = seg_pos<G>();
   const bool col_in = sp.lz < tb.cz && sp.lx < tb.cx;
-  const int lane = threadIdx.x & 31;
   const int64_t gz = tb.z0 + sp.lz, gx = tb.x0 + sp.lx;
+  unsigned same_pairs = 0;  // same-bin neighbour pairs of the thread's points
 #pragma unroll 1
   for (int j = 0; j < G::SEG; ++j) {
     uint32_t same = 0, lo = 0;
@@ -626,15 +757,17 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
     }
     const uint32_t up = same & ~lo & ~out_of_box_bits<G>(sp.lz, ly, sp.lx);
     const int o = sp.o0 + j * G::TX;
+    same_pairs += __popc(same);
     cml[o] = lo | (up << 16);
     // the global copy (for reruns) keeps the lower and all the same-bin bits
     if (col_in && ly < tb.cy) cm_glob[gz * plane + (tb.y0 + ly) * g.nx + gx] = lo | (same << 16);
-    // first-frontier bits, one ballot per warp: a row of lanes holds consecutive points
+    // first-frontier bits (all subbins are 0, so only a point with a +1 constraint can
+    // rise first), one ballot per warp: a row of lanes holds consecutive points
     const uint32_t bal = __ballot_sync(0xffffffffu, (lo >> 7) != 0);
     if (G::TX >= 32) {
-      if (lane == 0 && bal) atomicOr(&fa[o >> 5], bal);
-    } else if ((lane & 15) == 0) {
-      const uint32_t half = (bal >> (lane & 16)) & 0xFFFFu;
+      if ((threadIdx.x & 31) == 0 && bal) atomicOr(&fa[o >> 5], bal);
+    } else if ((threadIdx.x & 15) == 0) {
+      const uint32_t half = (bal >> (threadIdx.x & 16)) & 0xFFFFu;
       if (half) atomicOr(&fa[o >> 5], half << (o & 31));
     }
   }
@@ -642,7 +775,15 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
     for (int j = 0; j < G::SEG && sp.ly0 + j < tb.cy; ++j)
       bins_out[gz * plane + (tb.y0 + sp.ly0 + j) * g.nx + gx] = (int64_t)bin[sp.e0 + j * G::BXP];
   }
+  {
+    const unsigned wsum = __reduce_add_sync(0xffffffffu, same_pairs);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&cnt[0], wsum);
+  }
   __syncthreads();  // keys are dead from here on
+  // same-bin pairs over the tile's points, against 16ths of the neighbour pairs a full
+  // tile has (each pair is seen from both ends)
+  const unsigned pairs_full = (unsigned)G::NP * (G::HZ ? 14u : 6u);
+  const bool dense_tile = (unsigned long long)cnt[0] * 16ull > (unsigned long long)pairs_full * dense16;
   phase_mark(P, 1, t0);
 
   // 3. bin record: DIFFNB_w, BIT_w, RZE_1; raw if that is not shorter
@@ -691,11 +832,24 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   // 4. tile-local least fixpoint, halo subbins 0
   for (int e = threadIdx.x; e < G::E; e += NT) sv[e] = 0;
   __syncthreads();
-  bool over = false;
+  // frontier sweeps (cheaper while chains are short), and for a tile whose chains
+  // outlast the evaluation budget (budget16 / 16 evaluations per point) the
+  // topological order, which evaluates each point once, from the values reached so
+  // far (lower bounds of the result)
   unsigned evals = 0, raises = 0;
-  const int iters = frontier_fixpoint<G, false>(sv, cml, fa, fb, rb, cnt, list, 4 * G::NP + 64, over, evals, raises);
+  bool over = false;
+  int iters = 0;
+  // a tile whose neighbour pairs are mostly same-bin (thick bins, long chains) takes
+  // the topological order at once
+  if (!dense_tile) {
+    iters = frontier_fixpoint<G, false>(sv, cml, fa, fb, rb, cnt, flist, 4 * G::NP + 64, over, evals, raises,
+                                        (unsigned)G::NP * budget16 / 16u);
+  }
+  if (over || dense_tile) {
+    __syncthreads();
+    iters += topo_fixpoint<G, false>(sv, cml, indeg, la, lb, cnt, tb, nullptr, evals, raises);
+  }
   if (threadIdx.x == 0) {
-    if (over) atomicOr(&P->status, kErrNotConverged);
     atomicAdd(&P->fix_iters, (unsigned long long)iters);
     atomicMax(&P->fix_iters_max, (unsigned long long)iters);
   }

@@ -100,6 +100,14 @@ def lib():
         L.lopc_tune_set.restype = None
         L.lopc_tune_get.argtypes = [C.POINTER(C.c_int)]
         L.lopc_tune_get.restype = None
+        L.lopc_tune_set_budget.argtypes = [C.POINTER(C.c_int)]
+        L.lopc_tune_set_budget.restype = None
+        L.lopc_tune_get_budget.argtypes = [C.POINTER(C.c_int)]
+        L.lopc_tune_get_budget.restype = None
+        L.lopc_tune_set_dense.argtypes = [C.POINTER(C.c_int)]
+        L.lopc_tune_set_dense.restype = None
+        L.lopc_tune_get_dense.argtypes = [C.POINTER(C.c_int)]
+        L.lopc_tune_get_dense.restype = None
         L.lopc_strerror.argtypes = [C.c_int]
         L.lopc_strerror.restype = C.c_char_p
         _lib = L
@@ -395,6 +403,28 @@ def tune_set(rerun_blocks_per_sm) -> None:
 def tune_get() -> Tuple[int, int, int, int]:
     v = (C.c_int * 4)()
     lib().lopc_tune_get(v)
+    return tuple(int(a) for a in v)
+
+
+def tune_set_budget(sixteenths) -> None:
+    """Pass frontier-evaluation budget per class, in sixteenths of a tile's points."""
+    lib().lopc_tune_set_budget((C.c_int * 4)(*[int(v) for v in sixteenths]))
+
+
+def tune_get_budget() -> Tuple[int, int, int, int]:
+    v = (C.c_int * 4)()
+    lib().lopc_tune_get_budget(v)
+    return tuple(int(a) for a in v)
+
+
+def tune_set_dense(sixteenths) -> None:
+    """Same-bin pair density (sixteenths) above which a tile pass goes topological."""
+    lib().lopc_tune_set_dense((C.c_int * 4)(*[int(v) for v in sixteenths]))
+
+
+def tune_get_dense() -> Tuple[int, int, int, int]:
+    v = (C.c_int * 4)()
+    lib().lopc_tune_get_dense(v)
     return tuple(int(a) for a in v)
 
 
