@@ -380,11 +380,13 @@ __device__ bool rze_decode(const uint8_t* in, uint32_t in_len, uint32_t L, uint8
   for (uint32_t j = wr.a + lane; j < wr.b; j += 32) c0 += __popc((uint32_t)w.m0[j]);
   uint32_t wtot;
   warp_exclusive_scan(c0, &wtot);
-  uint32_t np;
-  const uint32_t wbase = block_exclusive_scan<NT, uint32_t>(lane == 0 ? wtot : 0u, w.tmp, &np);
+  const uint32_t sv3[3] = {lane == 0 ? wtot : 0u, 0u, 0u};
+  uint32_t ex3[3], tot3[3];
+  block_exclusive_scan3<NT>(sv3, w.tmp, ex3, tot3);  // one barrier
+  const uint32_t np = tot3[0];
   if ((uint64_t)l2 + nk1 + nk0 + (uint64_t)np * G != in_len) return false;  // uniform
   const uint8_t* pay = in + l2 + nk1 + nk0;
-  uint32_t run = __shfl_sync(0xffffffffu, wbase, 0);
+  uint32_t run = __shfl_sync(0xffffffffu, ex3[0], 0);
   for (uint32_t base = wr.a; base < wr.b; base += 32) {
     const uint32_t j = base + lane;
     const uint32_t bits = j < wr.b ? (uint32_t)w.m0[j] : 0u;

@@ -192,7 +192,19 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC, 4) k_decode(const DecFiel
   __syncthreads();
 
   // bins
+  // the subbin record goes to A once A is free, behind the bins' work (raw bins never
+  // use A); the subbin stage waits for it
+  auto prefetch_sub = [&]() {
+    if (!bad && !(ss & kRawFlag) && ss >= 4 && ss < raw) {
+      const uint32_t n16 = (ss + 15) >> 4;
+      for (uint32_t i = threadIdx.x; i < n16; i += NT) {
+        const unsigned d = (unsigned)__cvta_generic_to_shared(A + 16 * i);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(rs + 16 * i) : "memory");
+      }
+    }
+  };
   if (sb & kRawFlag) {
+    prefetch_sub();
     if ((sb & ~kRawFlag) != raw) bad = 1;
     for (int i = threadIdx.x; i < n; i += NT) wb[i] = reinterpret_cast<const W_t*>(rb)[i];
     __syncthreads();
@@ -206,6 +218,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC, 4) k_decode(const DecFiel
       __syncthreads();
     }
     dec_mark(0, t0);
+    prefetch_sub();  // A is free from here on
     if (!bad) {
       constexpr W_t M = (W_t)0xAAAAAAAAAAAAAAAAULL;
       bit_untranspose<NT, W>(n32, reinterpret_cast<const uint32_t*>(Bf), [&](int i, uint64_t u) {
@@ -246,6 +259,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC, 4) k_decode(const DecFiel
     __syncthreads();
   }
   if (bad) {
+    cp_async_wait_all();  // no copy may outlive the block
     if (threadIdx.x == 0) atomicOr(status, kErrCorrupt);
     return;
   }
@@ -328,7 +342,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC, 4) k_decode(const DecFiel
     __syncthreads();
     uint32_t l2 = 0;
     if (!bad) {
-      copy16<NT>(A, rs, ss);
+      cp_async_wait_all();  // the record fetched after the bins' RZE stage
       __syncthreads();
       l2 = *reinterpret_cast<const uint32_t*>(A);
       if (l2 > DS::LR) bad = 1;  // uniform: every thread reads the same word
@@ -348,6 +362,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC, 4) k_decode(const DecFiel
       });
     }
   }
+  cp_async_wait_all();  // no copy may outlive the block (a no-op once the record was consumed)
   if ((__syncthreads_or(fail) || bad) && threadIdx.x == 0) atomicOr(status, kErrCorrupt);
   dec_mark(5, t0);
 }
