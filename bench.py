@@ -223,6 +223,115 @@ def batch_leg(torch, lopc, fields_np, specs, flush, args):
                       f"sequence (cached graph) per field back to back on one stream"}
 
 
+def e2e_leg(torch, lopc, x_np, eb, steps, warmup, dev):
+    """Host to host through the public (asynchronous) batch calls: every step uploads
+    its field from pinned memory, compresses it, downloads the stream, uploads it
+    again, decompresses and downloads the field.  Two buffer sets, a software
+    pipeline on the compute stream (step k+1's compression is enqueued before step
+    k's decompression, which waits for its stream's round trip) and separate copy
+    streams for fields and for streams let the copies overlap the kernels; the host
+    waits only to learn each stream's length."""
+    import ctypes as C
+    NB = 2
+    shape, nbytes = tuple(x_np.shape), x_np.nbytes
+    d = lopc.make_desc(shape, "f32", lopc.NOA, eb)
+    hx = torch.from_numpy(x_np).pin_memory()
+    xs = [torch.empty(shape, dtype=torch.float32, device=dev) for _ in range(NB)]
+    comps = [lopc.BatchCompress([xs[b]], [eb]) for b in range(NB)]
+    cap = comps[0].caps[0]
+    hs = [torch.empty(cap, dtype=torch.uint8).pin_memory() for _ in range(NB)]
+    ins = [torch.empty(cap, dtype=torch.uint8, device=dev) for _ in range(NB)]
+    xh = [torch.empty(shape, dtype=torch.float32, device=dev) for _ in range(NB)]
+    hy = [torch.empty(shape, dtype=torch.float32).pin_memory() for _ in range(NB)]
+    dws = [torch.empty(lopc.decompress_workspace_size(d), dtype=torch.uint8, device=dev) for _ in range(NB)]
+    dst = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in range(NB)]
+    size_h = torch.zeros(NB, dtype=torch.int64).pin_memory()
+    # field upload, field download, stream download, stream upload, compute
+    s_xin, s_xout, s_sout, s_sin, s_comp = (torch.cuda.Stream(device=dev) for _ in range(5))
+    ev = {k: [torch.cuda.Event() for _ in range(NB)] for k in ("x", "c", "so", "si", "d", "y")}
+    used = {k: [False] * NB for k in ev}
+    descs = lopc._descs([d])
+
+    def rec(k, b, st):
+        ev[k][b].record(st)
+        used[k][b] = True
+
+    def wait(st, k, b):
+        if used[k][b]:
+            st.wait_event(ev[k][b])
+
+    def upload_x(k):
+        b = k % NB
+        with torch.cuda.stream(s_xin):
+            wait(s_xin, "c", b)  # the buffer's previous field was compressed
+            xs[b].copy_(hx, non_blocking=True)
+            rec("x", b, s_xin)
+
+    def compress(k):
+        b = k % NB
+        with torch.cuda.stream(s_comp):
+            wait(s_comp, "x", b)
+            wait(s_comp, "so", b)  # the buffer's previous stream was downloaded
+            comps[b].launch(stream=s_comp)
+            size_h[b:b + 1].copy_(comps[b].sizes, non_blocking=True)
+            rec("c", b, s_comp)
+
+    total = warmup + steps
+    h2d = d2h = 0
+    t_start = None
+
+    def start_clock():
+        # the timed region opens before the upload of the first timed step's field
+        # (it also holds the rest of the warm-up steps in flight: a conservative count)
+        nonlocal t_start
+        torch.cuda.synchronize()
+        t_start = time.perf_counter()
+
+    if warmup == 0:
+        start_clock()
+    upload_x(0)
+    compress(0)
+    for k in range(total):
+        b = k % NB
+        if k + 1 < total:
+            if k + 1 == warmup:
+                start_clock()
+            upload_x(k + 1)
+            compress(k + 1)  # runs while step k's stream makes its round trip
+        ev["c"][b].synchronize()
+        n = int(size_h[b])
+        with torch.cuda.stream(s_sout):
+            s_sout.wait_event(ev["c"][b])
+            hs[b][:n].copy_(comps[b].outs[0][:n], non_blocking=True)
+            rec("so", b, s_sout)
+        with torch.cuda.stream(s_sin):
+            s_sin.wait_event(ev["so"][b])
+            ins[b][:n].copy_(hs[b][:n], non_blocking=True)
+            rec("si", b, s_sin)
+        with torch.cuda.stream(s_comp):
+            s_comp.wait_event(ev["si"][b])
+            wait(s_comp, "y", b)  # the buffer's previous field was downloaded
+            rc = lopc.lib().lopc_batch_decompress(
+                1, descs, (C.c_void_p * 1)(ins[b].data_ptr()), (C.c_size_t * 1)(n),
+                (C.c_void_p * 1)(xh[b].data_ptr()), C.c_void_p(dst[b].data_ptr()), C.c_void_p(dws[b].data_ptr()),
+                dws[b].numel(), C.c_void_p(s_comp.cuda_stream))
+            assert rc == 0, rc
+            rec("d", b, s_comp)
+        with torch.cuda.stream(s_xout):
+            s_xout.wait_event(ev["d"][b])
+            hy[b].copy_(xh[b], non_blocking=True)
+            rec("y", b, s_xout)
+        h2d, d2h = nbytes + n, n + nbytes
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t_start
+    ok = all(int(v) == 0 for v in torch.cat(dst).cpu())
+    return {"value": steps * nbytes / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h),
+            "pipelined": "two buffer sets; compute stream runs step k+1's compression before step k's "
+                         "decompression; separate copy streams for fields and streams",
+            "statuses_ok": bool(ok)}
+
+
 def serve_leg(torch, lopc, args):
     """Poisson serving at the configured rate, then at half of it (below saturation)."""
     from paper_2603_26968_b300 import serve, synth_gpu as SG
@@ -338,10 +447,11 @@ def main():
             lopc.decompress(st, out=xhat, desc=d, workspace=dws)
         torch.cuda.synchronize()
         prof = lopc.profile_read()
+        rerun_ms = lopc.profile_read_launches("tile_rerun")[-(len(lopc.last_round_tiles()) - 1):]
         lopc.profile_enable(False)
         dph = {a: v // k for a, v in lopc.decode_phase_read().items()}
         lopc.decode_phase_enable(False)
-        return prof, dph, lopc.last_round_tiles()
+        return prof, dph, lopc.last_round_tiles(), rerun_ms
 
     # headline: the configured bound as the library runs it (graphs), with clocks
     with ClockSampler(local) as clk:
@@ -365,7 +475,7 @@ def main():
 
     # per-kernel split, and the dominant kernel's roofline (separate pass, same workload)
     prof_steps = 2
-    prof, dec_phases, round_tiles = profiled(args.eb, prof_steps)
+    prof, dec_phases, round_tiles, round_ms = profiled(args.eb, prof_steps)
     w = 4
     npts = nbytes // w
     # algorithmic bytes per step of each kernel: what the method must move (range and
@@ -412,26 +522,7 @@ def main():
                             "fixpoint_sweeps_max": f2[1], "fixpoint_work": lopc.last_fixpoint_work()}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    hx = torch.from_numpy(x_np).pin_memory()
-    hs = torch.empty(out.numel(), dtype=torch.uint8).pin_memory()
-    hy = torch.empty_like(hx).pin_memory()
-    e2e_t = []
-    h2d = d2h = 0
-    for i in range(args.warmup + args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        x.copy_(hx, non_blocking=True)
-        st = lopc.compress(x, args.eb, lopc.NOA, out=out, workspace=ws)
-        n = st.numel()
-        hs[:n].copy_(st, non_blocking=True)
-        out[:n].copy_(hs[:n], non_blocking=True)
-        lopc.decompress(out[:n], out=xhat, desc=d, workspace=dws)
-        hy.copy_(xhat, non_blocking=True)
-        torch.cuda.synchronize()
-        if i >= args.warmup:
-            e2e_t.append(time.perf_counter() - t0)
-        h2d, d2h = nbytes + n, n + nbytes
-    e2e_gbs = nbytes / float(np.mean(e2e_t)) / 1e9
+    e2e = e2e_leg(torch, lopc, x_np, args.eb, args.steps, args.warmup, dev)
     del ws, dws, out, xhat
 
     batch = None
@@ -464,7 +555,7 @@ def main():
                          "hbm_frac_algorithmic": algo_comp / (tc.mean() * 1e-3) / 1e9 / hbm,
                          "input_frac": comp_gbs / hbm, "cr": cr, "repair_rounds": rounds, "tile_runs": runs,
                          "fixpoint_sweeps": sweeps, "fixpoint_sweeps_max": sweeps_max, "fixpoint_work": work,
-                         "round_tiles": round_tiles,
+                         "round_tiles": round_tiles, "round_ms": round_ms,
                          "phase_cycles": phases},
             "decompress": {"gbs": dec_gbs, "ms": float(td.mean()),
                            "hbm_frac_algorithmic": algo_dec / (td.mean() * 1e-3) / 1e9 / hbm,
@@ -473,7 +564,7 @@ def main():
             "kernels": kern,
             "roofline": roof,
             "gpu_launches": gpu_launches,
-            "e2e": {"value": e2e_gbs, "unit": "GB/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "e2e": e2e,
             "batched": batch,
             "serving": serving,
             "cpu_baseline": cpu,

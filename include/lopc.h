@@ -205,6 +205,9 @@ LOPC_API int lopc_decode_phase_read(int64_t* out, int n);
 LOPC_API void lopc_profile_enable(int on);
 LOPC_API void lopc_profile_reset(void);
 LOPC_API int lopc_profile_read(const char** names, int64_t* launches, double* total_ms, int cap);
+/* The times of every timed launch of one kernel (by the name lopc_profile_read
+ * reports), in launch order: copies up to `cap` and returns how many there are. */
+LOPC_API int lopc_profile_read_launches(const char* name, double* ms, int cap);
 
 /* ---- serving engine (round-level continuous batching; the paper compresses one
  * field per call and has no counterpart).  Fields are submitted as they arrive and

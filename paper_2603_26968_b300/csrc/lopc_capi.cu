@@ -25,6 +25,7 @@ struct ProfEntry {
   const char* name;
   int64_t launches;
   double ms;
+  std::vector<float> each;  // every launch's time, in order
 };
 struct Pending {
   int entry;
@@ -42,7 +43,10 @@ struct Profiler {
     for (int i = 0; i < n; ++i)
       if (entries[i].name == name) return i;
     if (n == 64) return -1;
-    entries[n] = ProfEntry{name, 0, 0.0};
+    entries[n].name = name;
+    entries[n].launches = 0;
+    entries[n].ms = 0.0;
+    entries[n].each.clear();
     return n++;
   }
   cudaEvent_t event() {
@@ -74,6 +78,7 @@ struct Profiler {
       if (cudaEventSynchronize(pend[i].b) == cudaSuccess && cudaEventElapsedTime(&ms, pend[i].a, pend[i].b) == cudaSuccess) {
         entries[pend[i].entry].launches += 1;
         entries[pend[i].entry].ms += ms;
+        if (entries[pend[i].entry].each.size() < 100000) entries[pend[i].entry].each.push_back(ms);
       }
     }
     npend = 0;
@@ -1245,6 +1250,17 @@ int lopc_profile_read(const char** names, int64_t* launches, double* total_ms, i
     if (total_ms) total_ms[i] = g_prof.entries[i].ms;
   }
   return g_prof.n;
+}
+
+int lopc_profile_read_launches(const char* name, double* ms, int cap) {
+  g_prof.resolve();
+  for (int i = 0; i < g_prof.n; ++i) {
+    if (!name || strcmp(g_prof.entries[i].name, name) != 0) continue;
+    const std::vector<float>& v = g_prof.entries[i].each;
+    for (int k = 0; k < cap && k < (int)v.size(); ++k) ms[k] = v[k];
+    return (int)v.size();
+  }
+  return 0;
 }
 
 const char* lopc_strerror(int s) {

@@ -86,6 +86,8 @@ def lib():
         L.lopc_profile_reset.argtypes = []
         L.lopc_profile_read.argtypes = [C.POINTER(C.c_char_p), C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int]
         L.lopc_profile_read.restype = C.c_int
+        L.lopc_profile_read_launches.argtypes = [C.c_char_p, C.POINTER(C.c_double), C.c_int]
+        L.lopc_profile_read_launches.restype = C.c_int
         E = C.c_void_p
         L.lopc_engine_create.argtypes = [C.c_int, C.c_int64, C.POINTER(E)]
         L.lopc_engine_destroy.argtypes = [E]
@@ -319,6 +321,14 @@ def profile_read() -> dict:
 
 
 # ------------------------------------------------------------------------ batches
+
+def profile_read_launches(name: str) -> list:
+    """Times (ms) of every timed launch of one kernel, in launch order."""
+    cap = 100000
+    v = (C.c_double * cap)()
+    n = lib().lopc_profile_read_launches(name.encode(), v, cap)
+    return [float(v[k]) for k in range(min(n, cap))]
+
 
 def _descs(items):
     arr = (FieldDesc * len(items))()
