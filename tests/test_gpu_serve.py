@@ -55,6 +55,17 @@ def test_tight_budget_serialises_but_still_matches(L):
         assert torch.equal(r.stream, serve.solo_stream(r.spec))
 
 
+def test_several_rounds_per_step_match_solo(L):
+    from paper_2603_26968_b300 import serve
+    specs = _mixed_specs(10, seed=11)
+    srv = serve.Server(budget_bytes=2 << 30, max_fields=32, rounds_per_step=3)
+    rep = srv.run(specs, keep_streams=True)
+    srv.close()
+    for r in rep.served:
+        assert r.status == L.OK
+        assert torch.equal(r.stream, serve.solo_stream(r.spec))
+
+
 def _engine_submit(L, E, x, eb, tag, cap=None):
     d = L.make_desc(tuple(x.shape), x.dtype, L.NOA, eb)
     out = torch.empty(cap if cap is not None else L.compress_bound(d), dtype=torch.uint8, device=x.device)
