@@ -385,7 +385,8 @@ def main():
     from paper_2603_26968_b300 import synth as S
     specs = [] if args.no_batch else S.spec_batch(args.seed, args.batch_count)
     pool = mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2) - 1)))
-    head_async = pool.apply_async(make_headline, (args.size, args.seed + rank))
+    from paper_2603_26968_b300 import replicas
+    head_async = pool.apply_async(make_headline, (args.size, replicas.rank_seed(args.seed, rank)))
     batch_async = pool.map_async(make_batch_field, specs) if specs else None
 
     import torch
@@ -456,11 +457,7 @@ def main():
     # headline: the configured bound as the library runs it (graphs), with clocks
     with ClockSampler(local) as clk:
         times, tc, td, ssize = timed(args.eb, args.steps, args.warmup)
-    ms_step = float(times.mean())
-    if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = replicas.max_over_ranks(float(times.mean()), dist, dev)
     rounds, runs = lopc.last_stats()
     sweeps, sweeps_max = lopc.last_fixpoint_stats()
     work = lopc.last_fixpoint_work()
@@ -536,7 +533,7 @@ def main():
         serving = serve_leg(torch, lopc, args)
 
     # aggregate over ranks (replicas): total bytes / max time
-    value = world * nbytes / (ms_step * 1e-3) / 1e9
+    value = replicas.whole_job_gbs(nbytes, world, ms_step)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         nb, dt, _ = cpu_oracle_sample(x_np, args.eb, args.cpu_sample)
