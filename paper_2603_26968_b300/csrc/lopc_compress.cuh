@@ -29,26 +29,6 @@ struct TileCfg<double, 2> {
   static constexpr int TZ = 1, TY = 32, TX = 64, HZ = 0, NT = 128, SEG = 16, MINB = 5, MINB_RERUN = 6, NTC = 128;
 };
 
-// Freudenthal neighbourhood (Sec. II): offsets +-d, d in {0,1}^3 \ {0}.  Direction
-// k < 7 is -D[k] (lower linear index), k >= 7 is +D[k-7] (higher linear index).
-__device__ __forceinline__ void dir3(int k, int& dz, int& dy, int& dx) {
-  const int d = k % 7;
-  const int s = k < 7 ? -1 : 1;
-  // D = (0,0,1) (0,1,0) (0,1,1) (1,0,0) (1,0,1) (1,1,0) (1,1,1): bits of d+1 = (z,y,x)
-  const int v = d + 1;
-  dz = s * ((v >> 2) & 1);
-  dy = s * ((v >> 1) & 1);
-  dx = s * (v & 1);
-}
-
-template <int HZ>
-__device__ __forceinline__ bool dir_valid(int k) {
-  if (HZ) return true;
-  int dz, dy, dx;
-  dir3(k, dz, dy, dx);
-  return dz == 0;
-}
-
 // ------------------------------------------------------------------ range
 
 // Per-field state reset and cleared dirty flags; blockIdx.y is the field.
@@ -66,7 +46,6 @@ __global__ void k_init_params(const FieldInfo* F, int nf) {
   P->mode = F[f].hdr.mode;
   P->status = 0;
   P->constant = 0;
-  P->dirty_count = 0;
   P->total = 0;
   P->rounds = 0;
   P->fix_iters = 0;
@@ -243,13 +222,6 @@ __device__ __forceinline__ SegPos seg_pos() {
 __host__ __device__ constexpr int dz_of(int k) { return (k < 7 ? -1 : 1) * ((((k % 7) + 1) >> 2) & 1); }
 __host__ __device__ constexpr int dy_of(int k) { return (k < 7 ? -1 : 1) * ((((k % 7) + 1) >> 1) & 1); }
 __host__ __device__ constexpr int dx_of(int k) { return (k < 7 ? -1 : 1) * (((k % 7) + 1) & 1); }
-constexpr int kPlusY = 8;  // direction +D[1] = (0, 1, 0)
-
-__device__ __forceinline__ uint32_t ld_acquire_u8(const uint8_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u8 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 
 // Asynchronous global -> shared copies (cp.async); a false predicate writes zeros and
 // reads nothing (the source must still be a valid address).

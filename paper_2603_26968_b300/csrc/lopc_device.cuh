@@ -35,7 +35,6 @@ struct Params {
   int constant;                   // NOA with a zero range
   unsigned int status;            // kErr* bits
   unsigned long long const_bits;  // the constant's bits (float32: low 32 bits)
-  unsigned int dirty_count;
   int fast_ok;                    // inv_f is a normal float: the fast quantizer path may run
   float inv_f;                    // inv rounded to float
   unsigned int pad0;
