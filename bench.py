@@ -130,6 +130,14 @@ def cpu_oracle_sample(x: np.ndarray, eb: float, sub: int):
     return blk.nbytes, dt, len(st)
 
 
+def workload_config(args, nbytes: int, world: int) -> dict:
+    """The headline workload, the same for both arms."""
+    return {"workload": f"3d_f32_{args.size}^3 (256 Gaussian bumps + 3-octave value noise), NOA eb "
+                        f"{args.eb:g}; step = compress + decompress (GB/s of uncompressed input)",
+            "field_bytes": int(nbytes), "parallelism": "replicas" if world > 1 else "single",
+            "l2": "flushed between steps (256 MB write); input 512 MB > L2"}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -147,8 +155,7 @@ def run_reference(args, rank):
         "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"3d_f32_{args.size}^3 bumps+value-noise, NOA eb {args.eb}; reference arm = CPU oracle "
-                               f"on the central {sub}^3 block per step", "field_bytes": int(x.nbytes)},
+        "config": workload_config(args, x.nbytes, 1),
         "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": f"central {sub}^3 block of the field, compress+decompress, single thread"},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -462,7 +469,8 @@ def main():
     sweeps, sweeps_max = lopc.last_fixpoint_stats()
     work = lopc.last_fixpoint_work()
     phases = dict(zip(["pass_load", "pass_flags", "pass_fixpoint", "pass_writeback", "pass_bin_record",
-                       "rerun_load", "rerun_fixpoint", "rerun_check_only"], lopc.last_phase_cycles()))
+                       "rerun_load", "rerun_fixpoint", "rerun_check_only", "rerun_writeback_mark"],
+                      lopc.last_phase_cycles()))
     hbm, peak_kind = peaks()
     cr = nbytes / ssize
     algo_comp = nbytes * 2 + ssize                 # NOA: range pass + tile pass read x; write stream
@@ -544,10 +552,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"3d_f32_{args.size}^3 (256 Gaussian bumps + 3-octave value noise), NOA eb "
-                                   f"{args.eb:g}; step = compress + decompress (GB/s of uncompressed input)",
-                       "field_bytes": nbytes, "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "flushed between steps (256 MB write); input 512 MB > L2"},
+            "config": workload_config(args, nbytes, world),
             "compress": {"gbs": comp_gbs, "ms": float(tc.mean()),
                          "hbm_frac_algorithmic": algo_comp / (tc.mean() * 1e-3) / 1e9 / hbm,
                          "input_frac": comp_gbs / hbm, "cr": cr, "repair_rounds": rounds, "tile_runs": runs,

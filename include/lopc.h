@@ -174,8 +174,8 @@ LOPC_API void lopc_last_fixpoint_stats(int64_t* sweeps_total, int64_t* sweeps_ma
 /* Measurement aid: SM cycles of the last compression on this thread, summed over
  * blocks, per phase: 0 tile load + quantization, 1 flags, 2 tile fixpoint, 3 state
  * write-back, 4 bin record, 5 rerun load and check, 6 rerun fixpoint, 7 rerun load and check of
- * tiles whose constraints all held.
- * Copies min(n, 8) values and returns 8. */
+ * tiles whose constraints all held, 8 rerun write-back and marking.
+ * Copies min(n, 9) values and returns 9. */
 LOPC_API int lopc_last_phase_cycles(int64_t* cycles, int n);
 
 /* Measurement aid: tiles listed for each repair round after the first (all-tile)

@@ -95,7 +95,7 @@ thread_local Profiler g_prof;
     g_prof.after(st);               \
   } while (0)
 thread_local int64_t g_last_rounds = 0, g_last_tile_runs = 0, g_last_fix_iters = 0, g_last_fix_iters_max = 0;
-thread_local int64_t g_last_phase[8] = {};
+thread_local int64_t g_last_phase[9] = {};
 thread_local int64_t g_last_work[4] = {};
 thread_local std::vector<int64_t> g_round_tiles;  // tiles listed per round (host-driven loop only)
 
@@ -661,7 +661,7 @@ int compress_one(const lopc_field_desc* d, const void* d_x, void* d_out, size_t 
   g_last_tile_runs = (int64_t)(2 * f.g.ntiles + hb.runs);
   g_last_fix_iters = (int64_t)hp.fix_iters;
   g_last_fix_iters_max = (int64_t)hp.fix_iters_max;
-  for (int k = 0; k < 8; ++k) g_last_phase[k] = (int64_t)hp.phase[k];
+  for (int k = 0; k < 9; ++k) g_last_phase[k] = (int64_t)hp.phase[k];
   for (int k = 0; k < 4; ++k) g_last_work[k] = (int64_t)hp.work[k];
   // the repair ran even if the output was too small: report the repair's status first
   if (res.status == LOPC_ERR_CAPACITY && subbins_out) res.status = LOPC_OK;
@@ -1201,8 +1201,8 @@ void lopc_last_fixpoint_stats(int64_t* sweeps_total, int64_t* sweeps_max) {
 }
 
 int lopc_last_phase_cycles(int64_t* cycles, int n) {
-  for (int k = 0; k < n && k < 8; ++k) cycles[k] = g_last_phase[k];
-  return 8;
+  for (int k = 0; k < n && k < 9; ++k) cycles[k] = g_last_phase[k];
+  return 9;
 }
 
 int lopc_decode_phase_enable(int on) {

@@ -50,7 +50,7 @@ __global__ void k_init_params(const FieldInfo* F, int nf) {
   P->rounds = 0;
   P->fix_iters = 0;
   P->fix_iters_max = 0;
-  for (int k = 0; k < 8; ++k) P->phase[k] = 0;
+  for (int k = 0; k < 9; ++k) P->phase[k] = 0;
   for (int k = 0; k < 4; ++k) P->work[k] = 0;
   P->fast_ok = 0;
   P->inv_f = 0.f;
@@ -884,10 +884,17 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
   const int64_t count = list ? (int64_t)B->count[cls] : ntile_cls;
   const uint32_t* lst = list ? list + B->off[cls] : nullptr;
   unsigned* next = list ? &B->next[cls] : &B->next_all[cls];
+  // thread 0 takes the following item while the block works on this one, so the
+  // counter's latency is hidden
+  unsigned ahead = 0;
+  if (threadIdx.x == 0) ahead = atomicAdd(next, 1u);
 #pragma unroll 1
   while (true) {
-    if (threadIdx.x == 0) s_item = atomicAdd(next, 1u);
-    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_item = ahead;
+      if ((int64_t)ahead < count) ahead = atomicAdd(next, 1u);
+    }
+    __syncthreads();  // also: the last item's shared state is no longer read
     const int64_t item = (int64_t)s_item;
     __syncthreads();  // s_item is rewritten for the next item
     if (item >= count) break;
@@ -1017,7 +1024,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
         reinterpret_cast<volatile uint8_t*>(fi.dirty)[((qz / g.tz) * g.nty + qy / g.ty) * g.ntx + qx / g.tx] = 1;
       }
     }
-    __syncthreads();  // shared state is reused by the next item
+    phase_mark(P, 8, t0);  // the next item's first barrier separates this item's reads from its writes
   }
 }
 

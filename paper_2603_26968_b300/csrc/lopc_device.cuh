@@ -42,7 +42,7 @@ struct Params {
   unsigned long long rounds;
   unsigned long long fix_iters;   // sum over tile runs of fixpoint sweeps
   unsigned long long fix_iters_max;
-  unsigned long long phase[8];    // SM cycles spent per kernel phase (block-summed, for measurement)
+  unsigned long long phase[9];    // SM cycles spent per kernel phase (block-summed, for measurement)
   unsigned long long work[4];     // fixpoint point evaluations and raises: tile pass, reruns
 };
 

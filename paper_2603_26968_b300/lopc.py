@@ -246,8 +246,8 @@ def last_fixpoint_stats() -> Tuple[int, int]:
 
 def last_phase_cycles() -> list:
     """SM cycles per kernel phase of the last compression (see include/lopc.h)."""
-    a = (C.c_int64 * 8)()
-    lib().lopc_last_phase_cycles(a, 8)
+    a = (C.c_int64 * 9)()
+    lib().lopc_last_phase_cycles(a, 9)
     return [int(v) for v in a]
 
 
