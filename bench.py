@@ -113,6 +113,13 @@ def make_headline(n: int, seed: int):
     return S.make_field(S.spec_3d_f32(seed=seed, n=n))
 
 
+def make_config_field(name: str):
+    from paper_2603_26968_b300 import synth as S
+    spec = {"C1 2d_f32_256x256 NOA 1e-3": S.spec_2d_small(seed=1),
+            "C3 3d_f64_256x384x384 ties+spikes NOA 5e-4": S.spec_3d_f64_ties(seed=1)}[name]
+    return S.make_field(spec), float(spec.eb)
+
+
 def make_batch_field(spec):
     from paper_2603_26968_b300 import synth as S
     return S.make_field(spec)
@@ -228,6 +235,42 @@ def batch_leg(torch, lopc, fields_np, specs, flush, args):
             "identical_output": bool(identical),
             "timing": f"median of {args.batch_reps}, L2 flushed before each; per-field = one async launch "
                       f"sequence (cached graph) per field back to back on one stream"}
+
+
+def configs_leg(torch, lopc, fields, flush, steps, warmup):
+    """The other single-field configurations: compress + decompress per step, as the
+    library runs them, L2 flushed between steps."""
+    out = {}
+    st = torch.cuda.current_stream()
+    for name, (x_np, eb) in fields.items():
+        x = torch.from_numpy(x_np).to(flush.device)
+        d = lopc.make_desc(tuple(x.shape), x.dtype, lopc.NOA, eb)
+        o = torch.empty(lopc.compress_bound(d), dtype=torch.uint8, device=x.device)
+        ws = torch.empty(lopc.compress_workspace_size(d), dtype=torch.uint8, device=x.device)
+        xh = torch.empty_like(x)
+        dws = torch.empty(lopc.decompress_workspace_size(d), dtype=torch.uint8, device=x.device)
+        tc, td = [], []
+        size = 0
+        for i in range(warmup + steps):
+            flush.zero_()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(st)
+            s_ = lopc.compress(x, eb, lopc.NOA, out=o, workspace=ws)
+            e1.record(st)
+            lopc.decompress(s_, out=xh, desc=d, workspace=dws)
+            e2.record(st)
+            torch.cuda.synchronize()
+            size = s_.numel()
+            if i >= warmup:
+                tc.append(e0.elapsed_time(e1))
+                td.append(e1.elapsed_time(e2))
+        rounds, runs = lopc.last_stats()
+        ms = float(np.mean(tc) + np.mean(td))
+        out[name] = {"field_bytes": int(x_np.nbytes), "ms_per_step": ms, "gbs": x_np.nbytes / (ms * 1e-3) / 1e9,
+                     "compress_ms": float(np.mean(tc)), "decompress_ms": float(np.mean(td)),
+                     "cr": x_np.nbytes / size, "repair_rounds": rounds}
+        del x, o, ws, xh, dws
+    return out
 
 
 def e2e_leg(torch, lopc, x_np, eb, steps, warmup, dev):
@@ -372,6 +415,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--retune", action="store_true")
@@ -395,6 +439,8 @@ def main():
     from paper_2603_26968_b300 import replicas
     head_async = pool.apply_async(make_headline, (args.size, replicas.rank_seed(args.seed, rank)))
     batch_async = pool.map_async(make_batch_field, specs) if specs else None
+    cfg_names = [] if args.no_configs else ["C1 2d_f32_256x256 NOA 1e-3", "C3 3d_f64_256x384x384 ties+spikes NOA 5e-4"]
+    cfg_async = pool.map_async(make_config_field, cfg_names) if cfg_names else None
 
     import torch
     from paper_2603_26968_b300 import lopc
@@ -530,6 +576,9 @@ def main():
     e2e = e2e_leg(torch, lopc, x_np, args.eb, args.steps, args.warmup, dev)
     del ws, dws, out, xhat
 
+    configs = None
+    if cfg_async is not None:
+        configs = configs_leg(torch, lopc, dict(zip(cfg_names, cfg_async.get())), flush, args.steps, args.warmup)
     batch = None
     if batch_async is not None:
         torch.cuda.empty_cache()
@@ -563,6 +612,7 @@ def main():
                            "hbm_frac_algorithmic": algo_dec / (td.mean() * 1e-3) / 1e9 / hbm,
                            "phase_cycles": dec_phases},
             "other_bounds": extra,
+            "other_configs": configs,
             "kernels": kern,
             "roofline": roof,
             "gpu_launches": gpu_launches,
