@@ -319,3 +319,67 @@ def critical_types(x: np.ndarray):
     up = np.empty(x.shape, np.uint8)
     lib().orc_critical_types(C.byref(d), _ptr(x), _ptr(lo), _ptr(up))
     return lo, up
+
+
+# verification summary (Sec. II critical points, Table III, Sec. III-A bound, PSNR) --
+
+CP_MIN, CP_MAX, CP_SADDLE, CP_REGULAR = 0, 1, 2, 3
+
+
+def classify(lower_cc: np.ndarray, upper_cc: np.ndarray) -> np.ndarray:
+    """Sec. II: a point with an empty lower link is a minimum, one with an empty upper
+    link a maximum, one whose lower and upper links are one piece each is regular,
+    any other point a saddle.  (The minimum test comes first, so a point without
+    neighbours counts as a minimum.)"""
+    c = np.full(lower_cc.shape, CP_SADDLE, np.uint8)
+    c[(lower_cc == 1) & (upper_cc == 1)] = CP_REGULAR
+    c[upper_cc == 0] = CP_MAX
+    c[lower_cc == 0] = CP_MIN
+    return c
+
+
+def verify(x: np.ndarray, y: np.ndarray, mode: int = 1, eb: float = 1e-3) -> dict:
+    """What a reconstruction y keeps of x:
+      - order_violations: neighbour pairs whose order (with the index tie-break of
+        Sec. II) differs between x and y, each pair once;
+      - cp_x, cp_y: minima, maxima, saddles, regular points (Sec. II);
+      - false_positives / false_negatives / false_types (Table III): critical in y
+        only / in x only / in both with another type;
+      - link_mismatches: points whose (lower, upper) link component counts differ;
+      - x_min, x_max, max_abs_err = max |x - y|, mse = mean (x - y)^2, all in
+        binary64; psnr = 20 log10(x_max - x_min) - 10 log10(mse) (+inf when mse = 0);
+      - eps: the bound of Sec. III-A (eb, or eb (x_max - x_min) for NOA) and
+        bound_ok = max_abs_err <= eps."""
+    x, y = _c(x), _c(y)
+    assert x.dtype == y.dtype and x.shape == y.shape
+    if not (np.isfinite(x).all() and np.isfinite(y).all()):
+        raise OracleError(NONFINITE, "verify")
+    lx, ux = critical_types(x)
+    ly, uy = critical_types(y)
+    cx, cy = classify(lx, ux), classify(ly, uy)
+    crit_x, crit_y = cx != CP_REGULAR, cy != CP_REGULAR
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    d = np.abs(xd - yd)
+    x_min, x_max = float(xd.min()), float(xd.max())
+    mse = float(np.mean(d * d))
+    r = x_max - x_min
+    if mse == 0.0:
+        psnr = float("inf")
+    elif r == 0.0:
+        psnr = float("-inf")
+    else:
+        psnr = 20.0 * np.log10(r) - 10.0 * np.log10(mse)
+    eps = eb if mode == 0 else eb * r
+    max_err = float(d.max())
+    return {
+        "points": int(x.size),
+        "order_violations": order_violations(x, y),
+        "cp_x": [int((cx == k).sum()) for k in range(4)],
+        "cp_y": [int((cy == k).sum()) for k in range(4)],
+        "false_positives": int((~crit_x & crit_y).sum()),
+        "false_negatives": int((crit_x & ~crit_y).sum()),
+        "false_types": int((crit_x & crit_y & (cx != cy)).sum()),
+        "link_mismatches": int(((lx != ly) | (ux != uy)).sum()),
+        "x_min": x_min, "x_max": x_max, "max_abs_err": max_err, "mse": mse, "psnr": float(psnr),
+        "eps": float(eps), "bound_ok": bool(max_err <= eps),
+    }
