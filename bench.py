@@ -382,6 +382,30 @@ def e2e_leg(torch, lopc, x_np, eb, steps, warmup, dev):
             "statuses_ok": bool(ok)}
 
 
+def verify_leg(torch, lopc, x, xhat, eb, flush, steps, warmup, hbm):
+    """lopc_verify on the headline field and its reconstruction: the report (local
+    order, critical-point classes, Table III counts, error bound, PSNR) and the
+    verifier kernel's time per launch (CUDA events, L2 flushed before each)."""
+    d = lopc.make_desc(tuple(x.shape), x.dtype, lopc.NOA, eb)
+    vws = torch.empty(lopc.verify_workspace_size(d), dtype=torch.uint8, device=x.device)
+    for _ in range(warmup):
+        rep = lopc.verify(x, xhat, eb, lopc.NOA, workspace=vws)
+    lopc.profile_reset()
+    lopc.profile_enable(True)
+    for _ in range(steps):
+        flush.zero_()
+        rep = lopc.verify(x, xhat, eb, lopc.NOA, workspace=vws)
+    prof = lopc.profile_read()
+    lopc.profile_enable(False)
+    launches, total = prof["verify"]
+    per = total / launches
+    nb = 2 * x.numel() * x.element_size()          # x and x_hat read once
+    gbs = nb / (per * 1e-3) / 1e9
+    return {"ms": per, "gbs": gbs, "hbm_frac": gbs / hbm, "bytes_per_launch": nb,
+            "finalize_ms": prof["verify_finalize"][1] / prof["verify_finalize"][0],
+            "report": rep, "timing": f"CUDA events around each launch, {steps} launches, L2 flushed before each"}
+
+
 def serve_leg(torch, lopc, args):
     """Poisson serving at the configured rate, then at half of it (below saturation)."""
     from paper_2603_26968_b300 import serve, synth_gpu as SG
@@ -560,6 +584,10 @@ def main():
     launches_per_step = sum(v["launches_per_step"] for v in kern.values())
     gpu_launches = int(round(launches_per_step * args.steps))
 
+    # the verifier on the headline field and its reconstruction (x_hat of the last
+    # profiled step, at the configured bound)
+    verify = verify_leg(torch, lopc, x, xhat, args.eb, flush, args.steps, args.warmup, hbm)
+
     # other bounds of the same field
     extra = {}
     for eb in [float(v) for v in args.extra_ebs.split(",") if v]:
@@ -612,6 +640,7 @@ def main():
                            "hbm_frac_algorithmic": algo_dec / (td.mean() * 1e-3) / 1e9 / hbm,
                            "phase_cycles": dec_phases},
             "other_bounds": extra,
+            "verify": verify,
             "other_configs": configs,
             "kernels": kern,
             "roofline": roof,

@@ -157,6 +157,57 @@ LOPC_API int64_t lopc_noalloc_max_chunks(void);
 LOPC_API int lopc_quantize_repair(const lopc_field_desc* desc, const void* d_x, int64_t* d_bins, uint64_t* d_subbins,
                          void* d_ws, size_t ws_size, void* stream);
 
+/* ---- verification.  What a reconstruction y keeps of the field x, in one pass over
+ * both on the GPU:
+ *   - the local order of Sec. II: neighbour pairs (Freudenthal neighbourhood, each
+ *     pair once) whose order differs, ties broken by the lower index in each field;
+ *   - critical points (Sec. II): every point of x and of y is a minimum (empty lower
+ *     link), else a maximum (empty upper link), else regular (one lower and one upper
+ *     link piece), else a saddle; link pieces are connected in the triangulation;
+ *   - Table III's counts: false positives (regular in x, critical in y), false
+ *     negatives (critical in x, regular in y), false types (critical in both with
+ *     another class); link_mismatches: points whose pair (lower pieces, upper pieces)
+ *     differs, which also catches a saddle of another multiplicity;
+ *   - the error bound of Sec. III-A: max |x - y| and eps = eb (ABS) or
+ *     eb * (max(x) - min(x)) (NOA), in binary64; and the PSNR,
+ *     20 log10(max(x) - min(x)) - 10 log10(mse), +inf when mse = 0.
+ * Integer counts and max_abs_err are exact; mse (and so psnr) is a sum in a fixed
+ * order, deterministic on a given GPU; for float32 fields the squares are summed in
+ * float32 over at most 16 points before binary64 (relative error below 2e-6). */
+typedef struct {
+  int64_t points;
+  int64_t order_violations;
+  int64_t cp_x[4];          /* minima, maxima, saddles, regular points of x */
+  int64_t cp_y[4];          /* the same for y */
+  int64_t false_positives;
+  int64_t false_negatives;
+  int64_t false_types;
+  int64_t link_mismatches;
+  int64_t nonfinite;        /* points where x or y is NaN or infinite */
+  double x_min, x_max;
+  double max_abs_err;       /* max |x - y| */
+  double mse;               /* mean (x - y)^2 */
+  double psnr;
+  double eps;               /* the bound of desc (mode, eb) for x */
+  int32_t bound_ok;         /* max_abs_err <= eps */
+  int32_t reserved;
+} lopc_verify_report;
+
+/* Device scratch bytes that lopc_verify needs (0 for an invalid descriptor). */
+LOPC_API size_t lopc_verify_workspace_size(const lopc_field_desc* desc);
+
+/* Compares d_y (a reconstruction) with d_x, both fields described by desc (the
+ * bound fields mode and eb give report.eps), and writes the report to h_report
+ * (host).  d_types_x, if not NULL, receives one byte per point of x in C order:
+ * the number of lower-link pieces | the number of upper-link pieces << 4 (Sec. II);
+ * d_types_y the same for y (only together with d_types_x).  The workspace must be
+ * 256-byte aligned.  Synchronising.
+ * Errors: INVALID_ARG, WORKSPACE, CUDA; NONFINITE when x or y holds NaN or an
+ * infinity (the report is filled, with the count in report.nonfinite). */
+LOPC_API int lopc_verify(const lopc_field_desc* desc, const void* d_x, const void* d_y, uint8_t* d_types_x,
+                         uint8_t* d_types_y, lopc_verify_report* h_report, void* d_ws, size_t ws_size,
+                         void* stream);
+
 /* Caps the number of repair rounds after the first (all-tile) round for later calls
  * on this thread (0 restores the default, which a valid field never reaches).  A
  * lowered cap makes lopc_compress return LOPC_ERR_NOT_CONVERGED.  Returns the

@@ -11,6 +11,7 @@
 
 #include "lopc.h"
 #include "lopc_decompress.cuh"
+#include "lopc_verify.cuh"
 
 using namespace lopc;
 
@@ -1021,7 +1022,72 @@ int engine_step(lopc_engine* e, int rounds, int* active) {
   return LOPC_OK;
 }
 
+// ---------------------------------------------------------------- verifier
+// Workspace: the link table (one byte per 14-bit neighbour set), the blocks'
+// partial sums and the report.
+constexpr int64_t kVerifyMaxParts = 4096;
+struct VerifyLayout {
+  size_t table, parts, report, total;
+};
+VerifyLayout verify_layout(int64_t ntiles) {
+  VerifyLayout L;
+  L.table = 0;
+  L.parts = align256(1 << 14);
+  L.report = L.parts + align256(sizeof(VerifyPartial) * (size_t)std::min<int64_t>(ntiles, kVerifyMaxParts));
+  L.total = L.report + align256(sizeof(lopc_verify_report));
+  return L;
+}
+
+template <typename T, int ND>
+int launch_verify(const Geometry& g, const void* d_x, const void* d_y, uint8_t* tx, uint8_t* ty, uint8_t* ws,
+                  const VerifyLayout& L, int64_t& nparts, cudaStream_t st) {
+  using VS = VerifySmem<T, ND>;
+  constexpr int NT = TileCfg<T, ND>::NT;
+  static int per_sm = 0;  // resident blocks per SM (per instantiation, device-wide)
+  if (!per_sm) {
+    CK(cudaFuncSetAttribute(k_verify<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)VS::bytes()));
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_verify<T, ND>, NT, VS::bytes()));
+    per_sm = std::max(1, occ);
+  }
+  nparts = std::min<int64_t>(std::min<int64_t>(g.ntiles, (int64_t)per_sm * sm_count()), kVerifyMaxParts);
+  LAUNCH("verify", st,
+         k_verify<T, ND><<<(unsigned)nparts, NT, VS::bytes(), st>>>(
+             g, reinterpret_cast<const T*>(d_x), reinterpret_cast<const T*>(d_y), ws + L.table, tx, ty,
+             reinterpret_cast<VerifyPartial*>(ws + L.parts)));
+  CK(cudaGetLastError());
+  return LOPC_OK;
+}
+
+int verify_one(const lopc_field_desc* d, const void* d_x, const void* d_y, uint8_t* tx, uint8_t* ty,
+               lopc_verify_report* h_report, uint8_t* ws, size_t ws_size, cudaStream_t st) {
+  const Geometry g = geometry_of(d);
+  const VerifyLayout L = verify_layout(g.ntiles);
+  if (!ws || ws_size < L.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return LOPC_ERR_WORKSPACE;
+  LAUNCH("link_table", st, k_link_table<<<(1 << 14) / 256, 256, 0, st>>>(ws + L.table));
+  CK(cudaGetLastError());
+  int64_t nparts = 0;
+  int rc;
+  switch (class_of(d->dtype, d->ndim)) {
+    case 0: rc = launch_verify<float, 2>(g, d_x, d_y, tx, ty, ws, L, nparts, st); break;
+    case 1: rc = launch_verify<float, 3>(g, d_x, d_y, tx, ty, ws, L, nparts, st); break;
+    case 2: rc = launch_verify<double, 2>(g, d_x, d_y, tx, ty, ws, L, nparts, st); break;
+    default: rc = launch_verify<double, 3>(g, d_x, d_y, tx, ty, ws, L, nparts, st); break;
+  }
+  if (rc) return rc;
+  const int64_t points = g.nz * g.ny * g.nx;
+  lopc_verify_report* d_rep = reinterpret_cast<lopc_verify_report*>(ws + L.report);
+  LAUNCH("verify_finalize", st,
+         k_verify_finalize<256><<<1, 256, 0, st>>>(reinterpret_cast<const VerifyPartial*>(ws + L.parts),
+                                                    (int)nparts, points, d->mode, d->eb, d_rep));
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(h_report, d_rep, sizeof(lopc_verify_report), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return h_report->nonfinite ? LOPC_ERR_NONFINITE : LOPC_OK;
+}
+
 }  // namespace
+
 
 // ================================================================ C ABI
 
@@ -1395,6 +1461,20 @@ int lopc_engine_sync(lopc_engine* e) {
   CK(cudaStreamSynchronize(e->sm));
   CK(cudaStreamSynchronize(e->sa));
   return LOPC_OK;
+}
+
+size_t lopc_verify_workspace_size(const lopc_field_desc* d) {
+  if (!desc_valid(d)) return 0;
+  return verify_layout(geometry_of(d).ntiles).total;
+}
+
+int lopc_verify(const lopc_field_desc* d, const void* d_x, const void* d_y, uint8_t* d_types_x,
+                uint8_t* d_types_y, lopc_verify_report* h_report, void* d_ws, size_t ws_size, void* stream) {
+  if (!desc_valid(d) || !d_x || !d_y || !h_report || (d_types_y && !d_types_x)) return LOPC_ERR_INVALID_ARG;
+  const int rc = verify_one(d, d_x, d_y, d_types_x, d_types_y, h_report, reinterpret_cast<uint8_t*>(d_ws), ws_size,
+                            reinterpret_cast<cudaStream_t>(stream));
+  g_prof.resolve();
+  return rc;
 }
 
 }  // extern "C"

@@ -47,6 +47,15 @@ class FieldDesc(C.Structure):
 _lib = None
 
 
+class VerifyReport(C.Structure):
+    """lopc_verify_report (include/lopc.h)."""
+    _fields_ = [("points", C.c_int64), ("order_violations", C.c_int64), ("cp_x", C.c_int64 * 4),
+                ("cp_y", C.c_int64 * 4), ("false_positives", C.c_int64), ("false_negatives", C.c_int64),
+                ("false_types", C.c_int64), ("link_mismatches", C.c_int64), ("nonfinite", C.c_int64),
+                ("x_min", C.c_double), ("x_max", C.c_double), ("max_abs_err", C.c_double), ("mse", C.c_double),
+                ("psnr", C.c_double), ("eps", C.c_double), ("bound_ok", C.c_int32), ("reserved", C.c_int32)]
+
+
 def lib():
     """Loads ``liblopc.so`` (raises if it has not been built)."""
     global _lib
@@ -110,6 +119,9 @@ def lib():
         L.lopc_tune_set_dense.restype = None
         L.lopc_tune_get_dense.argtypes = [C.POINTER(C.c_int)]
         L.lopc_tune_get_dense.restype = None
+        L.lopc_verify_workspace_size.argtypes = [D]
+        L.lopc_verify_workspace_size.restype = C.c_size_t
+        L.lopc_verify.argtypes = [D, P, P, P, P, C.POINTER(VerifyReport), P, C.c_size_t, P]
         L.lopc_strerror.argtypes = [C.c_int]
         L.lopc_strerror.restype = C.c_char_p
         _lib = L
@@ -225,6 +237,41 @@ def quantize_repair(x: torch.Tensor, eb: float, mode: int = NOA) -> Tuple[torch.
                                     C.c_void_p(_stream(None)))
     _check(rc, "lopc_quantize_repair")
     return b, s
+
+
+def verify_workspace_size(desc: FieldDesc) -> int:
+    return int(lib().lopc_verify_workspace_size(C.byref(desc)))
+
+
+def verify(x: torch.Tensor, y: torch.Tensor, eb: float = 1e-3, mode: int = NOA,
+           types_x: Optional[torch.Tensor] = None, types_y: Optional[torch.Tensor] = None,
+           workspace: Optional[torch.Tensor] = None, stream=None) -> dict:
+    """What the reconstruction ``y`` keeps of ``x`` (lopc_verify): order violations,
+    critical-point classes of both, false positives / negatives / types, link
+    mismatches, range, max |x - y|, MSE, PSNR and the bound of (mode, eb).  Given
+    uint8 CUDA tensors of x's shape, ``types_x`` / ``types_y`` receive each point's
+    lower-link pieces | upper-link pieces << 4."""
+    if y.shape != x.shape or y.dtype != x.dtype or not y.is_cuda or not y.is_contiguous():
+        raise ValueError("y must be a contiguous CUDA tensor like x")
+    d = _field_desc(x, mode, eb)
+    if workspace is None:
+        workspace = torch.empty(verify_workspace_size(d), dtype=torch.uint8, device=x.device)
+    for t in (types_x, types_y):
+        if t is not None and (t.dtype != torch.uint8 or t.shape != x.shape or not t.is_cuda or not t.is_contiguous()):
+            raise ValueError("types must be contiguous uint8 CUDA tensors of the field's shape")
+    tx = C.c_void_p(types_x.data_ptr()) if types_x is not None else None
+    ty = C.c_void_p(types_y.data_ptr()) if types_y is not None else None
+    r = VerifyReport()
+    rc = lib().lopc_verify(C.byref(d), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), tx, ty, C.byref(r),
+                           C.c_void_p(workspace.data_ptr()), workspace.numel(), C.c_void_p(_stream(stream)))
+    _check(rc, "lopc_verify")
+    return {
+        "points": r.points, "order_violations": r.order_violations, "cp_x": list(r.cp_x), "cp_y": list(r.cp_y),
+        "false_positives": r.false_positives, "false_negatives": r.false_negatives,
+        "false_types": r.false_types, "link_mismatches": r.link_mismatches,
+        "x_min": r.x_min, "x_max": r.x_max, "max_abs_err": r.max_abs_err, "mse": r.mse, "psnr": r.psnr,
+        "eps": r.eps, "bound_ok": bool(r.bound_ok),
+    }
 
 
 def set_round_cap(cap: int) -> int:

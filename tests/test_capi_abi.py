@@ -71,3 +71,18 @@ def test_peek_reads_oracle_headers(L, orc):
     assert (d.dtype, d.ndim, d.shape, d.mode, d.eb) == (1, 3, (5, 6, 7), 0, 1e-3)
     with pytest.raises(L.LopcError):
         L.peek(b"XXXX" + st[4:128])
+
+
+def test_verify_host_checks(L):
+    lib = L.lib()
+    # the report's layout: 15 int64 counts, 6 doubles, two int32
+    assert C.sizeof(L.VerifyReport) == 15 * 8 + 6 * 8 + 8
+    bad = L.make_desc((4, 4), "f32", L.NOA, 1e-3)
+    bad.ndim = 4
+    assert lib.lopc_verify_workspace_size(C.byref(bad)) == 0
+    r = L.VerifyReport()
+    assert lib.lopc_verify(C.byref(bad), None, None, None, None, C.byref(r), None, 0, None) == -1
+    good = L.make_desc((300, 200, 100), "f64", L.ABS, 0.5)
+    ws = lib.lopc_verify_workspace_size(C.byref(good))
+    assert ws >= (1 << 14) and ws % 256 == 0
+    assert lib.lopc_verify(C.byref(good), None, None, None, None, C.byref(r), None, 0, None) == -1
