@@ -406,6 +406,42 @@ def verify_leg(torch, lopc, x, xhat, eb, flush, steps, warmup, hbm):
             "report": rep, "timing": f"CUDA events around each launch, {steps} launches, L2 flushed before each"}
 
 
+def repair_modes_leg(torch, lopc, x, eb, flush, steps, warmup):
+    """Compression of the headline field under both repair schedules (graph mode,
+    CUDA events, L2 flushed before each): the tile design and the paper's per-point
+    worklist (Sec. III-D).  Both must give the same stream."""
+    out = {}
+    streams = {}
+    for name, mode in (("tiles", lopc.REPAIR_TILES), ("worklist", lopc.REPAIR_WORKLIST)):
+        prev = lopc.set_repair_mode(mode)
+        try:
+            d = lopc.make_desc(tuple(x.shape), x.dtype, lopc.NOA, eb)
+            ws = torch.empty(lopc.compress_workspace_size(d), dtype=torch.uint8, device=x.device)
+            o = torch.empty(lopc.compress_bound(d), dtype=torch.uint8, device=x.device)
+            for _ in range(warmup):
+                st = lopc.compress(x, eb, lopc.NOA, out=o, workspace=ws)
+            ms = []
+            stream = torch.cuda.current_stream()
+            for _ in range(steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                st = lopc.compress(x, eb, lopc.NOA, out=o, workspace=ws)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            rounds, runs = lopc.last_stats()
+            streams[name] = st.cpu().numpy().tobytes()
+            out[name] = {"compress_ms": float(np.median(ms)), "rounds": rounds, "tile_runs": runs,
+                         "work": lopc.last_fixpoint_work(), "workspace_bytes": ws.numel()}
+            del ws, o
+        finally:
+            lopc.set_repair_mode(prev)
+    out["identical_streams"] = streams["tiles"] == streams["worklist"]
+    out["timing"] = f"median of {steps} compressions, CUDA graphs, L2 flushed before each"
+    return out
+
+
 def serve_leg(torch, lopc, args):
     """Poisson serving at the configured rate, then at half of it (below saturation)."""
     from paper_2603_26968_b300 import serve, synth_gpu as SG
@@ -440,6 +476,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--no-repair-modes", action="store_true")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--retune", action="store_true")
@@ -588,6 +625,9 @@ def main():
     # profiled step, at the configured bound)
     verify = verify_leg(torch, lopc, x, xhat, args.eb, flush, args.steps, args.warmup, hbm)
 
+    repair_modes = None if args.no_repair_modes else repair_modes_leg(torch, lopc, x, args.eb, flush,
+                                                                      max(3, args.steps // 2), 2)
+
     # other bounds of the same field
     extra = {}
     for eb in [float(v) for v in args.extra_ebs.split(",") if v]:
@@ -641,6 +681,7 @@ def main():
                            "phase_cycles": dec_phases},
             "other_bounds": extra,
             "verify": verify,
+            "repair_modes": repair_modes,
             "other_configs": configs,
             "kernels": kern,
             "roofline": roof,

@@ -208,6 +208,20 @@ LOPC_API int lopc_verify(const lopc_field_desc* desc, const void* d_x, const voi
                          uint8_t* d_types_y, lopc_verify_report* h_report, void* d_ws, size_t ws_size,
                          void* stream);
 
+/* Repair schedules of the single-field calls (lopc_compress, lopc_quantize_repair):
+ *   LOPC_REPAIR_TILES (default): tile-local fixpoints in shared memory, then reruns of
+ *     the tiles whose halo rose, in device-driven rounds;
+ *   LOPC_REPAIR_WORKLIST: the paper's schedule (Sec. III-D, Alg. 2): from subbins 0,
+ *     one thread per worklist point, atomicMax raises, the greater same-bin neighbours
+ *     of a raised point on the next worklist (deduplicated by an iteration stamp).
+ * Both reach the same least fixpoint, so streams are identical.  The worklist mode
+ * needs 12 more workspace bytes per point: query lopc_compress_workspace_size after
+ * setting the mode.  Batches and the serving engine always use tiles.  Per thread;
+ * returns the previous mode, or INVALID_ARG for an unknown one. */
+#define LOPC_REPAIR_TILES 0
+#define LOPC_REPAIR_WORKLIST 1
+LOPC_API int lopc_set_repair_mode(int mode);
+
 /* Caps the number of repair rounds after the first (all-tile) round for later calls
  * on this thread (0 restores the default, which a valid field never reaches).  A
  * lowered cap makes lopc_compress return LOPC_ERR_NOT_CONVERGED.  Returns the

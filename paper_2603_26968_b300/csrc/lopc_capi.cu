@@ -12,12 +12,15 @@
 #include "lopc.h"
 #include "lopc_decompress.cuh"
 #include "lopc_verify.cuh"
+#include "lopc_worklist.cuh"
 
 using namespace lopc;
 
 namespace {
 
 thread_local int64_t g_round_cap = 0;  // 0 = default
+// Repair schedule of single-field compressions (lopc_set_repair_mode).
+thread_local int g_repair_mode = LOPC_REPAIR_TILES;
 
 // ---------------------------------------------------------------- profiling
 // Event pairs around each launch while profiling is on; resolved at the end of
@@ -322,7 +325,7 @@ int launch_init(const Table& t, const FieldInfo* dF, cudaStream_t st) {
 }
 
 template <typename T, int ND>
-int launch_class_pre(const Table& t, int c, const FieldInfo* dF, cudaStream_t st) {
+int launch_class_pre(const Table& t, int c, const FieldInfo* dF, int fix, cudaStream_t st) {
   using C = TileCfg<T, ND>;
   if (!t.cls_nf[c]) return LOPC_OK;
   int rc = set_smem_attrs<T, ND>();
@@ -331,7 +334,7 @@ int launch_class_pre(const Table& t, int c, const FieldInfo* dF, cudaStream_t st
   LAUNCH("resolve_eps", st, k_resolve_eps<T><<<(t.cls_nf[c] + 63) / 64, 64, 0, st>>>(dF, t.cls_f0[c], t.cls_nf[c]));
   LAUNCH("tile_pass", st,
          k_pass<T, ND><<<(unsigned)t.cls_nt[c], C::NT, PassSmem<T, ND>::bytes(), st>>>(
-             dF, t.cls_f0[c], t.cls_nf[c], t.cls_t0[c], (unsigned)g_pass_budget16[c], (unsigned)g_pass_dense16[c]));
+             dF, t.cls_f0[c], t.cls_nf[c], t.cls_t0[c], (unsigned)g_pass_budget16[c], (unsigned)g_pass_dense16[c], fix));
   CK(cudaGetLastError());
   return LOPC_OK;
 }
@@ -360,14 +363,15 @@ int launch_class_encode(const Table& t, int c, const FieldInfo* dF, cudaStream_t
   return LOPC_OK;
 }
 
-// State reset, range, eps and the tile pass of every field of the table.
-int launch_pre(const Table& t, const FieldInfo* dF, cudaStream_t st) {
+// State reset, range, eps and the tile pass of every field of the table (fix = 0:
+// the pass leaves every subbin at 0, for the worklist schedule).
+int launch_pre(const Table& t, const FieldInfo* dF, cudaStream_t st, int fix = 1) {
   int rc;
   if ((rc = launch_init(t, dF, st))) return rc;
-  if ((rc = launch_class_pre<float, 2>(t, 0, dF, st))) return rc;
-  if ((rc = launch_class_pre<float, 3>(t, 1, dF, st))) return rc;
-  if ((rc = launch_class_pre<double, 2>(t, 2, dF, st))) return rc;
-  return launch_class_pre<double, 3>(t, 3, dF, st);
+  if ((rc = launch_class_pre<float, 2>(t, 0, dF, fix, st))) return rc;
+  if ((rc = launch_class_pre<float, 3>(t, 1, dF, fix, st))) return rc;
+  if ((rc = launch_class_pre<double, 2>(t, 2, dF, fix, st))) return rc;
+  return launch_class_pre<double, 3>(t, 3, dF, fix, st);
 }
 
 // One rerun round: of every tile (list == null, the first round) or of the listed ones.
@@ -409,15 +413,19 @@ int launch_epilogue(const Table& t, const FieldInfo* dF, cudaStream_t st) {
 struct CompressPlan {
   Table t;
   std::vector<int> order;  // position in the table -> caller's index
+  bool worklist = false;   // one field, repaired by the worklist schedule
   size_t off_state = 0, off_table = 0, off_results = 0, off_list = 0;
+  size_t off_wl_state = 0, off_stamp = 0, off_wl = 0;
   std::vector<size_t> off_field;
   size_t ws_total = 0;
 };
 
 // Lays out a call over descs[0..n) (sorted by class); fills pointers when ws != null.
 int plan_compress(int n, const lopc_field_desc* descs, const void* const* xs, void* const* outs, const size_t* caps,
-                  uint64_t* d_sizes, int* d_status, int64_t* bins_out, uint8_t* ws, CompressPlan& p) {
+                  uint64_t* d_sizes, int* d_status, int64_t* bins_out, uint8_t* ws, CompressPlan& p,
+                  bool worklist = false) {
   p = CompressPlan{};  // planning twice (size, then pointers) must not accumulate
+  p.worklist = worklist && n == 1;
   p.order.resize(n);
   for (int i = 0; i < n; ++i) p.order[i] = i;
   std::stable_sort(p.order.begin(), p.order.end(), [&](int a, int b) {
@@ -440,6 +448,16 @@ int plan_compress(int n, const lopc_field_desc* descs, const void* const* xs, vo
   for (int k = 0; k < n; ++k) {
     p.off_field[k] = o;
     o += field_part(p.t.F[k].g).total;
+  }
+  if (p.worklist) {  // worklist state, one stamp per point, two worklists of a point each
+    const size_t npts = (size_t)(p.t.F[0].g.nz * p.t.F[0].g.ny * p.t.F[0].g.nx);
+    o = align256(o);
+    p.off_wl_state = o;
+    o = align256(o + sizeof(WorklistState));
+    p.off_stamp = o;
+    o = align256(o + 4 * npts);
+    p.off_wl = o;
+    o = align256(o + 8 * npts);
   }
   p.ws_total = o;
   if (!ws) return LOPC_OK;
@@ -471,9 +489,29 @@ Ptrs ptrs_of(const CompressPlan& p, uint8_t* ws) {
 
 // Everything before the repair loop: state reset, range, eps, tile pass, the first
 // (all-tile) rerun round and its compaction.
+// The worklist schedule: launches of one iteration and of its swap.
+int launch_wl(const CompressPlan& p, const Ptrs& q, uint8_t* ws, int all, cudaStream_t st,
+              cudaGraphConditionalHandle h, int use_h) {
+  WorklistState* W = reinterpret_cast<WorklistState*>(ws + p.off_wl_state);
+  LAUNCH(all ? "wl_iter_all" : "wl_iter", st,
+         k_wl_iter<<<sm_count() * 8, 256, 0, st>>>(q.F, W, reinterpret_cast<uint32_t*>(ws + p.off_wl),
+                                                  reinterpret_cast<uint32_t*>(ws + p.off_stamp), all));
+  LAUNCH("wl_next", st, k_wl_next<<<1, 1, 0, st>>>(q.F, W, q.B, h, use_h));
+  CK(cudaGetLastError());
+  return LOPC_OK;
+}
+
 int enqueue_prologue(const CompressPlan& p, const Ptrs& q, cudaStream_t st, cudaGraphConditionalHandle h, int use_h) {
   int rc;
   CK(cudaMemsetAsync(q.B, 0, sizeof(BatchState), st));
+  if (p.worklist) {
+    uint8_t* ws = reinterpret_cast<uint8_t*>(q.B) - p.off_state;
+    const size_t npts = (size_t)(p.t.F[0].g.nz * p.t.F[0].g.ny * p.t.F[0].g.nx);
+    CK(cudaMemsetAsync(ws + p.off_wl_state, 0, sizeof(WorklistState), st));
+    CK(cudaMemsetAsync(ws + p.off_stamp, 0, 4 * npts, st));
+    if ((rc = launch_pre(p.t, q.F, st, 0))) return rc;
+    return launch_wl(p, q, ws, 1, st, h, use_h);
+  }
   if ((rc = launch_pre(p.t, q.F, st))) return rc;
   if ((rc = launch_reruns(p.t, q.F, q.B, nullptr, st))) return rc;
   return launch_compact(p.t, q.F, q.list, q.B, nullptr, h, use_h, st);
@@ -481,6 +519,7 @@ int enqueue_prologue(const CompressPlan& p, const Ptrs& q, cudaStream_t st, cuda
 
 int enqueue_loop_body(const CompressPlan& p, const Ptrs& q, cudaStream_t st, cudaGraphConditionalHandle h, int use_h) {
   int rc;
+  if (p.worklist) return launch_wl(p, q, reinterpret_cast<uint8_t*>(q.B) - p.off_state, 0, st, h, use_h);
   if ((rc = launch_reruns(p.t, q.F, q.B, q.list, st))) return rc;
   return launch_compact(p.t, q.F, q.list, q.B, nullptr, h, use_h, st);
 }
@@ -599,7 +638,7 @@ std::vector<uint64_t> plan_key(const CompressPlan& p, const uint8_t* ws) {
   cudaGetDevice(&dev);
   k.push_back((uint64_t)dev);
   k.push_back((uint64_t)(uintptr_t)ws);
-  k.push_back((uint64_t)p.t.n());
+  k.push_back((uint64_t)p.t.n() | ((uint64_t)p.worklist << 32));
   for (int c = 0; c < 4; ++c)
     k.push_back((uint64_t)rerun_blocks(c) | ((uint64_t)g_pass_budget16[c] << 20) | ((uint64_t)g_pass_dense16[c] << 40));
   for (const FieldInfo& f : p.t.F) {
@@ -635,12 +674,13 @@ int compress_one(const lopc_field_desc* d, const void* d_x, void* d_out, size_t 
   const void* xs[1] = {d_x};
   void* outs[1] = {d_out};
   size_t caps[1] = {out_cap};
-  plan_compress(1, d, xs, outs, caps, nullptr, nullptr, nullptr, nullptr, p);
+  const bool wl = g_repair_mode == LOPC_REPAIR_WORKLIST;
+  plan_compress(1, d, xs, outs, caps, nullptr, nullptr, nullptr, nullptr, p, wl);
   if (!d_ws || ws_size < p.ws_total) return LOPC_ERR_WORKSPACE;
   uint8_t* ws = reinterpret_cast<uint8_t*>(d_ws);
   uint64_t* dsize = reinterpret_cast<uint64_t*>(ws + p.off_results);
   int* dstat = reinterpret_cast<int*>(ws + p.off_results + 8);
-  plan_compress(1, d, xs, outs, caps, dsize, dstat, bins_out, ws, p);
+  plan_compress(1, d, xs, outs, caps, dsize, dstat, bins_out, ws, p, wl);
   int rc = run_compress(p, ws, st);
   if (rc) return rc;
   const FieldInfo& f = p.t.F[0];
@@ -659,7 +699,7 @@ int compress_one(const lopc_field_desc* d, const void* d_x, void* d_out, size_t 
   CK(cudaMemcpyAsync(&hb, ptrs_of(p, ws).B, sizeof(BatchState), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   g_last_rounds = (int64_t)hb.rounds;
-  g_last_tile_runs = (int64_t)(2 * f.g.ntiles + hb.runs);
+  g_last_tile_runs = p.worklist ? f.g.ntiles : (int64_t)(2 * f.g.ntiles + hb.runs);
   g_last_fix_iters = (int64_t)hp.fix_iters;
   g_last_fix_iters_max = (int64_t)hp.fix_iters_max;
   for (int k = 0; k < 9; ++k) g_last_phase[k] = (int64_t)hp.phase[k];
@@ -1100,7 +1140,20 @@ size_t lopc_compress_bound(const lopc_field_desc* d) {
   return kHeaderBytes + ((size_t)g.ntiles * 8 + 15) / 16 * 16 + 2 * (n * word_bytes(d->dtype) + 16 * (size_t)g.ntiles);
 }
 
-size_t lopc_compress_workspace_size(const lopc_field_desc* d) { return lopc_batch_compress_workspace_size(1, d); }
+size_t lopc_compress_workspace_size(const lopc_field_desc* d) {
+  if (!desc_valid(d)) return 0;
+  CompressPlan p;
+  plan_compress(1, d, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, p,
+                g_repair_mode == LOPC_REPAIR_WORKLIST);
+  return p.ws_total;
+}
+
+int lopc_set_repair_mode(int mode) {
+  if (mode != LOPC_REPAIR_TILES && mode != LOPC_REPAIR_WORKLIST) return LOPC_ERR_INVALID_ARG;
+  const int prev = g_repair_mode;
+  g_repair_mode = mode;
+  return prev;
+}
 
 size_t lopc_batch_compress_workspace_size(int n, const lopc_field_desc* descs) {
   if (n <= 0 || !descs) return 0;

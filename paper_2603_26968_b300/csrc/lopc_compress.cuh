@@ -607,11 +607,13 @@ struct PassSmem {
 //   1. load x on the tile and its halo, quantize (Sec. III-A) and take order keys;
 //   2. flags (Alg. 1): the lower same-bin neighbours of every point;
 //   3. encode the tile's bin record (Sec. III-C; bins are final once quantized);
-//   4. tile-local least fixpoint with halo subbins taken as 0 (a lower bound);
+//   4. tile-local least fixpoint with halo subbins taken as 0 (a lower bound), unless
+//      fix = 0 (the worklist schedule starts from subbins 0);
 //   5. write subbins and lower masks (what reruns and the boundary check need).
 template <typename T, int ND>
 __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
-    k_pass(const FieldInfo* __restrict__ F, int f0, int nf, int64_t tile0, unsigned budget16, unsigned dense16) {
+    k_pass(const FieldInfo* __restrict__ F, int f0, int nf, int64_t tile0, unsigned budget16, unsigned dense16,
+           int fix) {
   using G = TileGeom<T, ND>;
   using PS = PassSmem<T, ND>;
   using K = typename Traits<T>::Key;
@@ -813,11 +815,11 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   int iters = 0;
   // a tile whose neighbour pairs are mostly same-bin (thick bins, long chains) takes
   // the topological order at once
-  if (!dense_tile) {
+  if (fix && !dense_tile) {
     iters = frontier_fixpoint<G, false>(sv, cml, fa, fb, rb, cnt, flist, 4 * G::NP + 64, over, evals, raises,
                                         (unsigned)G::NP * budget16 / 16u);
   }
-  if (over || dense_tile) {
+  if (fix && (over || dense_tile)) {
     __syncthreads();
     iters += topo_fixpoint<G, false>(sv, cml, indeg, la, lb, cnt, tb, nullptr, evals, raises);
   }

@@ -23,6 +23,7 @@ ERR_BUSY = -9
 ERRORS_INV = {v: k for k, v in ERRORS.items()}
 F32, F64 = 0, 1
 ABS, NOA = 0, 1
+REPAIR_TILES, REPAIR_WORKLIST = 0, 1
 
 
 class LopcError(RuntimeError):
@@ -122,6 +123,8 @@ def lib():
         L.lopc_verify_workspace_size.argtypes = [D]
         L.lopc_verify_workspace_size.restype = C.c_size_t
         L.lopc_verify.argtypes = [D, P, P, P, P, C.POINTER(VerifyReport), P, C.c_size_t, P]
+        L.lopc_set_repair_mode.argtypes = [C.c_int]
+        L.lopc_set_repair_mode.restype = C.c_int
         L.lopc_strerror.argtypes = [C.c_int]
         L.lopc_strerror.restype = C.c_char_p
         _lib = L
@@ -272,6 +275,15 @@ def verify(x: torch.Tensor, y: torch.Tensor, eb: float = 1e-3, mode: int = NOA,
         "x_min": r.x_min, "x_max": r.x_max, "max_abs_err": r.max_abs_err, "mse": r.mse, "psnr": r.psnr,
         "eps": r.eps, "bound_ok": bool(r.bound_ok),
     }
+
+
+def set_repair_mode(mode: int) -> int:
+    """Repair schedule of single-field calls on this thread (REPAIR_TILES or
+    REPAIR_WORKLIST); returns the previous one.  Query workspace sizes after it."""
+    rc = lib().lopc_set_repair_mode(int(mode))
+    if rc < 0:
+        raise LopcError(rc, "lopc_set_repair_mode")
+    return rc
 
 
 def set_round_cap(cap: int) -> int:

@@ -86,3 +86,17 @@ def test_verify_host_checks(L):
     ws = lib.lopc_verify_workspace_size(C.byref(good))
     assert ws >= (1 << 14) and ws % 256 == 0
     assert lib.lopc_verify(C.byref(good), None, None, None, None, C.byref(r), None, 0, None) == -1
+
+
+def test_repair_mode_knob(L):
+    lib = L.lib()
+    assert lib.lopc_set_repair_mode(7) == -1
+    prev = lib.lopc_set_repair_mode(L.REPAIR_WORKLIST)
+    assert prev == L.REPAIR_TILES
+    d = L.make_desc((30, 40, 50), "f32", L.NOA, 1e-3)
+    wl = lib.lopc_compress_workspace_size(C.byref(d))
+    assert lib.lopc_set_repair_mode(L.REPAIR_TILES) == L.REPAIR_WORKLIST
+    tiles = lib.lopc_compress_workspace_size(C.byref(d))
+    assert wl >= tiles + 12 * 30 * 40 * 50
+    # batches always use tiles
+    assert lib.lopc_batch_compress_workspace_size(1, C.byref(d)) == tiles
