@@ -1069,11 +1069,11 @@ constexpr int64_t kVerifyMaxParts = 4096;
 struct VerifyLayout {
   size_t table, parts, report, total;
 };
-VerifyLayout verify_layout(int64_t ntiles) {
+VerifyLayout verify_layout() {
   VerifyLayout L;
   L.table = 0;
-  L.parts = align256(1 << 14);
-  L.report = L.parts + align256(sizeof(VerifyPartial) * (size_t)std::min<int64_t>(ntiles, kVerifyMaxParts));
+  L.parts = align256(3 << 14);  // cc, full3, full2; then one partial per block of the grid
+  L.report = L.parts + align256(sizeof(VerifyPartial) * (size_t)kVerifyMaxParts);
   L.total = L.report + align256(sizeof(lopc_verify_report));
   return L;
 }
@@ -1093,7 +1093,8 @@ int launch_verify(const Geometry& g, const void* d_x, const void* d_y, uint8_t* 
   nparts = std::min<int64_t>(std::min<int64_t>(g.ntiles, (int64_t)per_sm * sm_count()), kVerifyMaxParts);
   LAUNCH("verify", st,
          k_verify<T, ND><<<(unsigned)nparts, NT, VS::bytes(), st>>>(
-             g, reinterpret_cast<const T*>(d_x), reinterpret_cast<const T*>(d_y), ws + L.table, tx, ty,
+             g, reinterpret_cast<const T*>(d_x), reinterpret_cast<const T*>(d_y), ws + L.table,
+             ws + L.table + (ND == 3 ? 1 : 2) * (1 << 14), tx, ty,
              reinterpret_cast<VerifyPartial*>(ws + L.parts)));
   CK(cudaGetLastError());
   return LOPC_OK;
@@ -1102,9 +1103,10 @@ int launch_verify(const Geometry& g, const void* d_x, const void* d_y, uint8_t* 
 int verify_one(const lopc_field_desc* d, const void* d_x, const void* d_y, uint8_t* tx, uint8_t* ty,
                lopc_verify_report* h_report, uint8_t* ws, size_t ws_size, cudaStream_t st) {
   const Geometry g = geometry_of(d);
-  const VerifyLayout L = verify_layout(g.ntiles);
+  const VerifyLayout L = verify_layout();
   if (!ws || ws_size < L.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return LOPC_ERR_WORKSPACE;
-  LAUNCH("link_table", st, k_link_table<<<(1 << 14) / 256, 256, 0, st>>>(ws + L.table));
+  LAUNCH("link_table", st,
+         k_link_table<<<(1 << 14) / 256, 256, 0, st>>>(ws + L.table, ws + L.table + (1 << 14), ws + L.table + (2 << 14)));
   CK(cudaGetLastError());
   int64_t nparts = 0;
   int rc;
@@ -1518,7 +1520,7 @@ int lopc_engine_sync(lopc_engine* e) {
 
 size_t lopc_verify_workspace_size(const lopc_field_desc* d) {
   if (!desc_valid(d)) return 0;
-  return verify_layout(geometry_of(d).ntiles).total;
+  return verify_layout().total;
 }
 
 int lopc_verify(const lopc_field_desc* d, const void* d_x, const void* d_y, uint8_t* d_types_x,

@@ -368,25 +368,61 @@ struct FixSmem {
 // recomputed only for points whose lower same-bin neighbours rose; a point that
 // rises puts its greater same-bin neighbours of the tile on the next frontier.  Each
 // sweep compacts the frontier bitmap into a list that all threads share evenly, so a
-// sweep costs about one evaluation per thread.  Raised subbins are visible to the
-// rest of the sweep at once; a neighbour read before it rose is queued again by
+// sweep costs about one evaluation per thread.  Once a frontier is small (the thin
+// tail of the chains), warp 0 runs the sweeps alone with warp barriers, and hands a
+// frontier that has grown again back to the block.  Raised subbins are visible to
+// the rest of the sweep at once; a neighbour read before it rose is queued again by
 // that rise.  `over` is set, with the last frontier not evaluated, after `limit`
-// sweeps or before the evaluations would exceed `eval_budget`.  Chaotic relaxation from lower bounds reaches the unique least fixpoint
-// (Sec. III-E) whatever the schedule.  `cml[o]` holds, for tile point o (linear
-// order), its lower same-bin neighbours in bits 0-13, and in bits 16-29 its same-bin
-// upper neighbours inside the tile (SAME = false) or all its same-bin neighbours
-// (SAME = true; the in-tile upper ones are derived).  `fa`
-// holds the first frontier, `fb` and `rb` must be clear; `rb` receives the points
-// that rose.  Returns the number of sweeps.
+// sweeps or before the evaluations would exceed `eval_budget`.  Chaotic relaxation
+// from lower bounds reaches the unique least fixpoint (Sec. III-E) whatever the
+// schedule.  `cml[o]` holds, for tile point o (linear order), its lower same-bin
+// neighbours in bits 0-13, and in bits 16-29 its same-bin upper neighbours inside the
+// tile (SAME = false) or all its same-bin neighbours (SAME = true; the in-tile upper
+// ones are derived).  `fa` holds the first frontier, `fb` and `rb` must be clear;
+// `rb` receives the points that rose; cnt[0..3] are scratch.  Returns the number of
+// sweeps.
 template <typename G, bool SAME>
 __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint32_t* cml, uint32_t* fa, uint32_t* fb,
                                                  uint32_t* rb, unsigned* cnt, uint16_t* list, int limit, bool& over,
                                                  unsigned& evals, unsigned& raises,
                                                  unsigned eval_budget = 0xffffffffu) {
   constexpr int NW = G::NP / 32, NT = G::NT;
-  static_assert(NW <= NT, "one frontier word per thread");
+  constexpr unsigned kTail = 32, kBack = 64;  // warp 0 alone below kTail points, until above kBack
+  static_assert(NW <= NT && NW % 32 == 0, "one frontier word per thread; whole words per lane");
   volatile uint32_t* vs = sv;
   const int lane = threadIdx.x & 31;
+  // evaluates tile point o; a rise records o and queues o's in-tile upper neighbours in `next`
+  auto eval_point = [&](int o, uint32_t* next) {
+    int lz, ly, lx;
+    point_of_lin<G>(o, lz, ly, lx);
+    const int e = G::entry(lz, ly, lx);
+    const uint32_t m = cml[o];
+    const uint32_t before = vs[e];
+    ++evals;
+    uint32_t best = before;
+#pragma unroll
+    for (int k = 0; k < 14; ++k) {  // predicated loads at constant offsets, all in flight together
+      if (!G::HZ && dz_of(k) != 0) continue;
+      if (m & (1u << k)) {
+        const uint32_t cand = vs[e + G::off(dz_of(k), dy_of(k), dx_of(k))] + (k >= 7 ? 1u : 0u);
+        best = cand > best ? cand : best;
+      }
+    }
+    if (best == before) return;
+    vs[e] = best;
+    ++raises;
+    atomicOr(&rb[o >> 5], 1u << (o & 31));
+    // in-tile upper neighbours: stored as such, or derived from the same-bin bits
+    const uint32_t um = SAME ? ((m >> 16) & ~m & ~out_of_box_bits<G>(lz, ly, lx)) : (m >> 16);
+#pragma unroll
+    for (int k = 0; k < 14; ++k) {
+      if (!G::HZ && dz_of(k) != 0) continue;
+      if (um & (1u << k)) {
+        const int qn = o + G::loff(dz_of(k), dy_of(k), dx_of(k));
+        atomicOr(&next[qn >> 5], 1u << (qn & 31));
+      }
+    }
+  };
   if (threadIdx.x == 0) cnt[0] = cnt[1] = 0;
   __syncthreads();
   int iter = 0;
@@ -419,39 +455,75 @@ __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint32_t* c
       break;
     }
     spent += n;
-    if (threadIdx.x == 0) cnt[iter & 1] = 0;  // the counter of the next sweep
-    for (unsigned i = threadIdx.x; i < n; i += NT) {
-      const int o = list[i];
-      int lz, ly, lx;
-      point_of_lin<G>(o, lz, ly, lx);
-      const int e = G::entry(lz, ly, lx);
-      const uint32_t m = cml[o];
-      const uint32_t before = vs[e];
-      ++evals;
-      uint32_t best = before;
+    if (n <= kTail) {
+      // the tail: warp 0 sweeps alone from this list (fa and fb are clear)
+      if (threadIdx.x < 32) {
+        unsigned wn = n, wspent = spent;
+        int wit = iter;
+        unsigned flags = 0;  // 1: over, 2: done
+        while (true) {
+          for (unsigned i = lane; i < wn; i += 32) eval_point(list[i], fb);
+          __syncwarp();
+          // compact fb into the list, lane by lane over contiguous words
+          constexpr int WPL = NW / 32;
+          uint32_t wv[WPL];
+          unsigned cw = 0;
 #pragma unroll
-      for (int k = 0; k < 14; ++k) {  // predicated loads at constant offsets, all in flight together
-        if (!G::HZ && dz_of(k) != 0) continue;
-        if (m & (1u << k)) {
-          const uint32_t cand = vs[e + G::off(dz_of(k), dy_of(k), dx_of(k))] + (k >= 7 ? 1u : 0u);
-          best = cand > best ? cand : best;
+          for (int r = 0; r < WPL; ++r) {
+            wv[r] = fb[lane * WPL + r];
+            cw += __popc(wv[r]);
+          }
+          unsigned wi = cw;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+          }
+          const unsigned total = __shfl_sync(0xffffffffu, wi, 31);
+          unsigned wp = wi - cw;
+#pragma unroll
+          for (int r = 0; r < WPL; ++r) {
+            if (wv[r]) fb[lane * WPL + r] = 0u;
+            for (uint32_t b = wv[r]; b; b &= b - 1) list[wp++] = (uint16_t)((lane * WPL + r) * 32 + __ffs(b) - 1);
+          }
+          __syncwarp();
+          wn = total;
+          if (wn == 0) {
+            flags = 2;
+            break;
+          }
+          if (wn > kBack) {  // grown again: back to the block, as frontier bits (counted there)
+            for (unsigned i = lane; i < wn; i += 32) {
+              const int o = list[i];
+              atomicOr(&fa[o >> 5], 1u << (o & 31));
+            }
+            break;
+          }
+          if (++wit > limit || wspent + wn > eval_budget) {
+            flags = 1;
+            break;
+          }
+          wspent += wn;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          cnt[0] = cnt[1] = 0;
+          cnt[2] = (unsigned)wit | (flags << 30);
+          cnt[3] = wspent;
         }
       }
-      if (best == before) continue;
-      vs[e] = best;
-      ++raises;
-      atomicOr(&rb[o >> 5], 1u << (o & 31));
-      // in-tile upper neighbours: stored as such, or derived from the same-bin bits
-      const uint32_t um = SAME ? ((m >> 16) & ~m & ~out_of_box_bits<G>(lz, ly, lx)) : (m >> 16);
-#pragma unroll
-      for (int k = 0; k < 14; ++k) {
-        if (!G::HZ && dz_of(k) != 0) continue;
-        if (um & (1u << k)) {
-          const int qn = o + G::loff(dz_of(k), dy_of(k), dx_of(k));
-          atomicOr(&fb[qn >> 5], 1u << (qn & 31));
-        }
+      __syncthreads();
+      const unsigned st = cnt[2];
+      iter = (int)(st & 0x3FFFFFFFu);
+      spent = cnt[3];
+      if (st >> 30) {
+        over = (st >> 30) == 1u;
+        break;
       }
+      continue;
     }
+    if (threadIdx.x == 0) cnt[iter & 1] = 0;  // the counter of the next sweep
+    for (unsigned i = threadIdx.x; i < n; i += NT) eval_point(list[i], fb);
     __syncthreads();
     uint32_t* t = fa;
     fa = fb;

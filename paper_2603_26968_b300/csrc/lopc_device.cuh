@@ -87,6 +87,7 @@ struct Traits<float> {
   static constexpr int64_t kBinLimit = int64_t(1) << 30;
   static constexpr Key kMaxKey = 0x7f7fffff;
   static constexpr Bin kAbsent = INT32_MIN;
+  static constexpr float kMaxFinite = 3.40282347e+38f;
   __device__ static Bits bits(float v) { return __float_as_uint(v); }
   __device__ static float from_bits(Bits u) { return __uint_as_float(u); }
 };
@@ -100,6 +101,7 @@ struct Traits<double> {
   static constexpr int64_t kBinLimit = int64_t(1) << 52;
   static constexpr Key kMaxKey = 0x7fefffffffffffffLL;
   static constexpr Bin kAbsent = INT64_MIN;
+  static constexpr double kMaxFinite = 1.7976931348623157e+308;
   __device__ static Bits bits(double v) { return (Bits)__double_as_longlong(v); }
   __device__ static double from_bits(Bits u) { return __longlong_as_double((long long)u); }
 };
@@ -443,9 +445,13 @@ struct TileBox {
   int n;
 };
 
+// (A field has fewer than 2^32 points, so tile indices and counts fit 32 bits and
+// the divisions are 32-bit ones.)
 __device__ __forceinline__ TileBox tile_box(const Geometry& g, int64_t tid) {
   TileBox t;
-  const int64_t tx = tid % g.ntx, ty = (tid / g.ntx) % g.nty, tz = tid / (g.ntx * g.nty);
+  const uint32_t i = (uint32_t)tid, ntx = (uint32_t)g.ntx, nty = (uint32_t)g.nty;
+  const uint32_t row = i / ntx;
+  const int64_t tx = i - row * ntx, tz = row / nty, ty = row - (uint32_t)tz * nty;
   t.z0 = tz * g.tz;
   t.y0 = ty * g.ty;
   t.x0 = tx * g.tx;

@@ -43,12 +43,10 @@ __host__ __device__ constexpr uint32_t link_adjacent(int a) {
   return r;
 }
 
-// cc[m] = number of connected pieces of the link vertices in the 14-bit set m
-// (one thread per set; flood fill from the lowest vertex left, at most 14 growths)
-__global__ void k_link_table(uint8_t* __restrict__ cc) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= (1 << 14)) return;
-  uint32_t rem = (uint32_t)m;
+// Number of connected pieces of the link vertices in the 14-bit set m (flood fill
+// from the lowest vertex left, at most 14 growths per piece).
+__device__ inline int link_pieces(uint32_t m) {
+  uint32_t rem = m;
   int pieces = 0;
   while (rem) {
     uint32_t piece = rem & (0u - rem), prev = 0;
@@ -58,27 +56,12 @@ __global__ void k_link_table(uint8_t* __restrict__ cc) {
 #pragma unroll
       for (int k = 0; k < 14; ++k)
         if (piece & (1u << k)) grown |= link_adjacent(k);
-      piece = grown & (uint32_t)m;
+      piece = grown & m;
     }
     rem &= ~piece;
     ++pieces;
   }
-  cc[m] = (uint8_t)pieces;
-}
-
-// Sec. II's classes: 0 minimum (no lower neighbour), 1 maximum (no upper one),
-// 3 regular (one lower and one upper piece), 2 saddle (anything else)
-__device__ __forceinline__ int cp_class(int lower, int upper) {
-  return lower == 0 ? 0 : upper == 0 ? 1 : (lower == 1 && upper == 1) ? 3 : 2;
-}
-
-// Directions whose neighbour lies outside the field, for a point at (gz, gy, gx).
-template <int ND>
-__device__ __forceinline__ uint32_t outside_field_bits(const Geometry& g, int64_t gz, int64_t gy, int64_t gx) {
-  uint32_t r = (gy == 0 ? dir_mask(1, -1) : 0u) | (gy == g.ny - 1 ? dir_mask(1, 1) : 0u) |
-               (gx == 0 ? dir_mask(2, -1) : 0u) | (gx == g.nx - 1 ? dir_mask(2, 1) : 0u);
-  if (ND == 3) r |= (gz == 0 ? dir_mask(0, -1) : 0u) | (gz == g.nz - 1 ? dir_mask(0, 1) : 0u);
-  return r;
+  return pieces;
 }
 
 template <int ND>
@@ -87,6 +70,24 @@ __host__ __device__ constexpr uint32_t all_dirs() {
   for (int k = 0; k < 14; ++k)
     if (ND == 3 || dz_of(k) == 0) r |= 1u << k;
   return r;
+}
+
+// Link tables, one thread per 14-bit set m of lower neighbours: cc[m], the pieces of
+// m; full3[m] and full2[m], the pieces of m and (<< 4) of the rest of a whole 3D or
+// 2D link (an interior point's lower and upper pieces in one lookup).
+__global__ void k_link_table(uint8_t* __restrict__ cc, uint8_t* __restrict__ full3, uint8_t* __restrict__ full2) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= (1 << 14)) return;
+  const int lo = link_pieces((uint32_t)m);
+  cc[m] = (uint8_t)lo;
+  full3[m] = (uint8_t)(lo | (link_pieces(all_dirs<3>() & ~(uint32_t)m) << 4));
+  full2[m] = (uint8_t)(link_pieces((uint32_t)m & all_dirs<2>()) | (link_pieces(all_dirs<2>() & ~(uint32_t)m) << 4));
+}
+
+// Sec. II's classes from a point's (lower pieces | upper pieces << 4): 0 minimum (no
+// lower neighbour), 1 maximum (no upper one), 3 regular (one piece each), 2 saddle
+__device__ __forceinline__ int cp_class(uint32_t pair) {
+  return (pair & 15u) == 0 ? 0 : (pair >> 4) == 0 ? 1 : pair == 0x11u ? 3 : 2;
 }
 
 // Lower-neighbour bits of the point at entry e of a box: neighbour k is lower when
@@ -121,6 +122,7 @@ template <typename T, int ND>
 __global__ void __launch_bounds__(TileCfg<T, ND>::NT, 3) k_verify(Geometry g, const T* __restrict__ x,
                                                               const T* __restrict__ y,
                                                               const uint8_t* __restrict__ cc,
+                                                              const uint8_t* __restrict__ full,
                                                               uint8_t* __restrict__ types_x,
                                                               uint8_t* __restrict__ types_y,
                                                               VerifyPartial* __restrict__ part) {
@@ -142,6 +144,8 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, 3) k_verify(Geometry g, co
   float m32 = -1.0f;
   double m64 = 0.0, sumsq = 0.0;
   T vmin = (T)INFINITY, vmax = (T)-INFINITY;
+  constexpr uint32_t FULL = all_dirs<ND>();
+  constexpr uint32_t YL = dir_mask(1, -1), YH = dir_mask(1, 1);
 
   for (int64_t tid = blockIdx.x; tid < g.ntiles; tid += gridDim.x) {
     const TileBox tb = tile_box(g, tid);
@@ -151,33 +155,44 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, 3) k_verify(Geometry g, co
     __syncthreads();
     if (sp.lz < tb.cz && sp.lx < tb.cx) {
       const int64_t gz = tb.z0 + sp.lz, gx = tb.x0 + sp.lx;
-      uint32_t px = 0, py = 0;  // class counts of this tile, one byte per class
+      // neighbours outside the field: x and z faces per column, y faces per point
+      uint32_t col = FULL & ~((gx == 0 ? dir_mask(2, -1) : 0u) | (gx == g.nx - 1 ? dir_mask(2, 1) : 0u));
+      if (ND == 3) col &= ~((gz == 0 ? dir_mask(0, -1) : 0u) | (gz == g.nz - 1 ? dir_mask(0, 1) : 0u));
+      const int yfirst = tb.y0 == 0 ? 0 : -1;
+      const int ylast = tb.y0 + tb.cy == g.ny ? tb.cy - 1 : -1;
+      // (class of x, class of y) counts of this tile, one byte each: lo holds x
+      // classes 0-1, hi classes 2-3
+      unsigned long long conf_lo = 0, conf_hi = 0;
       float s32 = 0.0f;
 #pragma unroll 2
       for (int j = 0; j < G::SEG; ++j) {
         const int ly = sp.ly0 + j;
         if (ly >= tb.cy) break;
         const int e = sp.e0 + j * G::BXP;
-        const uint32_t pres = all_dirs<ND>() & ~outside_field_bits<ND>(g, gz, tb.y0 + ly, gx);
+        const uint32_t pres = col & ~((ly == yfirst ? YL : 0u) | (ly == ylast ? YH : 0u));
         const uint32_t lx_ = lower_bits<G>(xs, e) & pres;
         const uint32_t ly_ = lower_bits<G>(ys, e) & pres;
         cnt[kVOrder] += __popc((lx_ ^ ly_) & kUpper);
-        const int lcx = __ldg(&cc[lx_]), ucx = __ldg(&cc[pres & ~lx_]);
-        const int lcy = __ldg(&cc[ly_]), ucy = __ldg(&cc[pres & ~ly_]);
-        const int cx = cp_class(lcx, ucx), cy = cp_class(lcy, ucy);
+        uint32_t px, py;
+        if (pres == FULL) {
+          px = __ldg(&full[lx_]);
+          py = __ldg(&full[ly_]);
+        } else {
+          px = __ldg(&cc[lx_]) | ((uint32_t)__ldg(&cc[pres & ~lx_]) << 4);
+          py = __ldg(&cc[ly_]) | ((uint32_t)__ldg(&cc[pres & ~ly_]) << 4);
+        }
         if (types_x) {
           const int64_t gi = (gz * g.ny + tb.y0 + ly) * g.nx + gx;
-          types_x[gi] = (uint8_t)(lcx | (ucx << 4));
-          if (types_y) types_y[gi] = (uint8_t)(lcy | (ucy << 4));
+          types_x[gi] = (uint8_t)px;
+          if (types_y) types_y[gi] = (uint8_t)py;
         }
-        px += 1u << (8 * cx);
-        py += 1u << (8 * cy);
-        cnt[kVFalsePos] += (cx == 3 && cy != 3);
-        cnt[kVFalseNeg] += (cx != 3 && cy == 3);
-        cnt[kVFalseType] += (cx != 3 && cy != 3 && cx != cy);
-        cnt[kVLink] += (lcx != lcy || ucx != ucy);
+        cnt[kVLink] += px != py;
+        const int cell = cp_class(px) * 4 + cp_class(py);
+        const unsigned long long inc = 1ull << (8 * (cell & 7));
+        conf_lo += cell < 8 ? inc : 0ull;
+        conf_hi += cell < 8 ? 0ull : inc;
         const T xv = xs[e], yv = ys[e];
-        cnt[kVNonfinite] += !(is_finite_bits<T>(xv) && is_finite_bits<T>(yv));
+        cnt[kVNonfinite] += !(fabs(xv) <= Traits<T>::kMaxFinite && fabs(yv) <= Traits<T>::kMaxFinite);
         vmin = xv < vmin ? xv : vmin;
         vmax = xv > vmax ? xv : vmax;
         if (sizeof(T) == 4) {
@@ -194,10 +209,19 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, 3) k_verify(Geometry g, co
           m64 = fmax(m64, d);
         }
       }
+      // the tile's (x class, y class) counts into the class and Table III counters
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        cnt[kVClsX + c] += (px >> (8 * c)) & 0xFFu;
-        cnt[kVClsY + c] += (py >> (8 * c)) & 0xFFu;
+      for (int cx = 0; cx < 4; ++cx) {
+#pragma unroll
+        for (int cy = 0; cy < 4; ++cy) {
+          const int cell = cx * 4 + cy;
+          const unsigned v = (unsigned)(((cell < 8 ? conf_lo : conf_hi) >> (8 * (cell & 7))) & 0xFFu);
+          cnt[kVClsX + cx] += v;
+          cnt[kVClsY + cy] += v;
+          if (cx == 3 && cy != 3) cnt[kVFalsePos] += v;
+          if (cx != 3 && cy == 3) cnt[kVFalseNeg] += v;
+          if (cx != 3 && cy != 3 && cx != cy) cnt[kVFalseType] += v;
+        }
       }
       sumsq += (double)s32;
     }
