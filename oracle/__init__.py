@@ -69,7 +69,7 @@ def lib():
         L.orc_rze.argtypes = [C.c_int, P, C.c_size_t, P]
         L.orc_rze.restype = C.c_size_t
         L.orc_unrze.argtypes = [C.c_int, P, C.c_size_t, C.c_size_t, P]
-        L.orc_encode_chunk.argtypes = [C.c_int, P, P, C.c_int64, P, P, P, P]
+        L.orc_encode_chunk.argtypes = [C.c_int, P, P, P, P, P, P, P]
         L.orc_compress_bound.argtypes = [C.POINTER(Desc)]
         L.orc_compress_bound.restype = C.c_size_t
         L.orc_compress.argtypes = [C.POINTER(Desc), P, P, C.c_size_t, C.POINTER(C.c_size_t)]
@@ -238,16 +238,22 @@ def unrze(g: int, data: bytes, L: int) -> bytes:
     return out[:L].tobytes()
 
 
-def encode_chunk(dtype_c: int, b: np.ndarray, s: np.ndarray):
-    """Records of one chunk: (bin_size, bin_record, subbin_size, subbin_record)."""
+SIZE_MASK, DIFF_FLAG, RAW_FLAG = 0x3FFFFFFF, 0x40000000, 0x80000000
+
+
+def encode_chunk(dtype_c: int, b: np.ndarray, s: np.ndarray, shape):
+    """Records of one chunk of `shape` (cz, cy, cx; 2D: cz = 1), points in chunk
+    order: (bin_size, bin_record, subbin_size, subbin_record)."""
     b = _c(b.astype(np.int64))
     s = _c(s.astype(np.uint64))
+    dims = np.array(list(shape), np.int64)
+    assert dims.size == 3 and int(np.prod(dims)) == b.size
     w = 4 if dtype_c == 0 else 8
     rb = np.zeros(b.size * w + 64, np.uint8)
     rs = np.zeros(b.size * w + 64, np.uint8)
     sb, ss = C.c_uint32(), C.c_uint32()
-    lib().orc_encode_chunk(dtype_c, _ptr(b), _ptr(s), b.size, _ptr(rb), C.byref(sb), _ptr(rs), C.byref(ss))
-    return sb.value, rb[: sb.value & 0x7FFFFFFF].tobytes(), ss.value, rs[: ss.value & 0x7FFFFFFF].tobytes()
+    lib().orc_encode_chunk(dtype_c, _ptr(b), _ptr(s), _ptr(dims), _ptr(rb), C.byref(sb), _ptr(rs), C.byref(ss))
+    return sb.value, rb[: sb.value & SIZE_MASK].tobytes(), ss.value, rs[: ss.value & SIZE_MASK].tobytes()
 
 
 # whole stream ------------------------------------------------------------------

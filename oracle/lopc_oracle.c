@@ -563,15 +563,85 @@ done:
 /* ---------------------------------------------------------------- chunks */
 
 #define RAW_FLAG 0x80000000u
+#define DIFF_FLAG 0x40000000u /* format 2: this bin record uses the 1D difference */
+#define SIZE_MASK 0x3FFFFFFFu
+#define NB_MASK 0xAAAAAAAAAAAAAAAAull
 
-/* Bins (Sec. III-C): DIFFNB_w, BIT_w, RZE_1; stored raw when that is not smaller. */
-static uint32_t enc_bins(int w, const int64_t* b, int64_t n, uint8_t* rec) {
+static int popcount64(uint64_t v) {
+  int c = 0;
+  for (; v; v &= v - 1) c++;
+  return c;
+}
+
+/* The 3D Lorenzo residual of a chunk's bins (cz x cy x cx points, row-major; a 2D
+ * chunk has cz = 1): r[z][y][x] = sum over (a, b, c) in {0,1}^3 of
+ * (-1)^(a+b+c) bins[z-a][y-b][x-c], bins outside the chunk taken as 0, in w-byte
+ * wrapping arithmetic.  Written as NB-mapped words, (r + M) xor M. */
+static void lorenzo_nb(int w, const int64_t* b, const int64_t d[3], uint8_t* out) {
+  for (int64_t z = 0; z < d[0]; z++)
+    for (int64_t y = 0; y < d[1]; y++)
+      for (int64_t x = 0; x < d[2]; x++) {
+        uint64_t acc = 0;
+        for (int a = 0; a < 2; a++)
+          for (int bb = 0; bb < 2; bb++)
+            for (int c = 0; c < 2; c++) {
+              int64_t zz = z - a, yy = y - bb, xx = x - c;
+              if (zz < 0 || yy < 0 || xx < 0) continue;
+              uint64_t v = (uint64_t)b[(zz * d[1] + yy) * d[2] + xx];
+              acc = ((a + bb + c) & 1) ? acc - v : acc + v;
+            }
+        uint64_t u = ((acc + NB_MASK) ^ NB_MASK) & wmask(w);
+        put_word(out + ((z * d[1] + y) * d[2] + x) * w, w, u);
+      }
+}
+
+/* Inverse of lorenzo_nb: unmap, then inclusive prefix sums along x, y and z. */
+static void unlorenzo_nb(int w, const uint8_t* in, const int64_t d[3], int64_t* b) {
+  int64_t n = d[0] * d[1] * d[2];
+  uint64_t* r = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n ? n : 1));
+  for (int64_t i = 0; i < n; i++) r[i] = ((get_word(in + i * w, w) ^ NB_MASK) - NB_MASK) & wmask(w);
+  for (int64_t z = 0; z < d[0]; z++)
+    for (int64_t y = 0; y < d[1]; y++)
+      for (int64_t x = 1; x < d[2]; x++) {
+        int64_t i = (z * d[1] + y) * d[2] + x;
+        r[i] = (r[i] + r[i - 1]) & wmask(w);
+      }
+  for (int64_t z = 0; z < d[0]; z++)
+    for (int64_t y = 1; y < d[1]; y++)
+      for (int64_t x = 0; x < d[2]; x++) {
+        int64_t i = (z * d[1] + y) * d[2] + x;
+        r[i] = (r[i] + r[i - d[2]]) & wmask(w);
+      }
+  for (int64_t z = 1; z < d[0]; z++)
+    for (int64_t y = 0; y < d[1]; y++)
+      for (int64_t x = 0; x < d[2]; x++) {
+        int64_t i = (z * d[1] + y) * d[2] + x;
+        r[i] = (r[i] + r[i - d[1] * d[2]]) & wmask(w);
+      }
+  for (int64_t i = 0; i < n; i++) b[i] = w == 4 ? (int64_t)(int32_t)(uint32_t)r[i] : (int64_t)r[i];
+  free(r);
+}
+
+/* Bins (Sec. III-C; format 2): a predictor's residual, NB-mapped, then BIT_w and
+ * RZE_1.  The predictor is the chunk's Lorenzo residual, or the 1D difference along
+ * the chunk's point order (DIFFNB_w, the only one of format 1) when its mapped words
+ * hold strictly fewer one bits.  Stored raw when the encoding is not smaller. */
+static uint32_t enc_bins(int w, const int64_t* b, const int64_t d[3], uint8_t* rec) {
+  int64_t n = d[0] * d[1] * d[2];
   int64_t n32 = (n + 31) / 32 * 32;
-  uint8_t* t1 = (uint8_t*)calloc((size_t)n32 * w, 1);
+  uint8_t* tl = (uint8_t*)calloc((size_t)n32 * w, 1);
+  uint8_t* td = (uint8_t*)calloc((size_t)n32 * w, 1);
   uint8_t* t2 = (uint8_t*)malloc((size_t)n32 * w);
   uint8_t* t3 = (uint8_t*)malloc((size_t)n32 * w * 2 + 64);
-  orc_diffnb(w, b, n, t1);
-  size_t L = orc_bit(w, t1, n, t2);
+  lorenzo_nb(w, b, d, tl);
+  orc_diffnb(w, b, n, td);
+  int64_t cost_l = 0, cost_d = 0;
+  for (int64_t i = 0; i < n; i++) {
+    cost_l += popcount64(get_word(tl + i * w, w));
+    cost_d += popcount64(get_word(td + i * w, w));
+  }
+  int use_diff = cost_d < cost_l;
+  size_t L = orc_bit(w, use_diff ? td : tl, n, t2);
   size_t R = orc_rze(1, t2, L, t3);
   uint32_t sz;
   if (R >= (size_t)n * w) {
@@ -579,9 +649,10 @@ static uint32_t enc_bins(int w, const int64_t* b, int64_t n, uint8_t* rec) {
     sz = (uint32_t)(n * w) | RAW_FLAG;
   } else {
     memcpy(rec, t3, R);
-    sz = (uint32_t)R;
+    sz = (uint32_t)R | (use_diff ? DIFF_FLAG : 0u);
   }
-  free(t1);
+  free(tl);
+  free(td);
   free(t2);
   free(t3);
   return sz;
@@ -615,9 +686,12 @@ static uint32_t enc_subbins(int w, const uint64_t* s, int64_t n, uint8_t* rec) {
   return sz;
 }
 
-static int dec_bins(int w, const uint8_t* rec, uint32_t sz, int64_t n, int64_t* b) {
+static int dec_bins(int w, int version, const uint8_t* rec, uint32_t sz, const int64_t d[3], int64_t* b) {
+  int64_t n = d[0] * d[1] * d[2];
   int64_t n32 = (n + 31) / 32 * 32;
-  uint32_t len = sz & ~RAW_FLAG;
+  uint32_t len = sz & SIZE_MASK;
+  if ((sz & DIFF_FLAG) && (version == 1 || (sz & RAW_FLAG))) return ORC_CORRUPT;
+  int use_diff = version == 1 || (sz & DIFF_FLAG);
   if (sz & RAW_FLAG) {
     if (len != (uint32_t)(n * w)) return ORC_CORRUPT;
     for (int64_t i = 0; i < n; i++) {
@@ -634,7 +708,12 @@ static int dec_bins(int w, const uint8_t* rec, uint32_t sz, int64_t n, int64_t* 
     orc_unbit(w, t2, n32, t1);
     for (int64_t i = n * w; i < n32 * w; i++)
       if (t1[i]) rc = ORC_CORRUPT;
-    if (rc == ORC_OK) orc_undiffnb(w, t1, n, b);
+    if (rc == ORC_OK) {
+      if (use_diff)
+        orc_undiffnb(w, t1, n, b);
+      else
+        unlorenzo_nb(w, t1, d, b);
+    }
   }
   free(t1);
   free(t2);
@@ -643,7 +722,8 @@ static int dec_bins(int w, const uint8_t* rec, uint32_t sz, int64_t n, int64_t* 
 
 static int dec_subbins(int w, const uint8_t* rec, uint32_t sz, int64_t n, uint64_t* s) {
   int64_t n32 = (n + 31) / 32 * 32;
-  uint32_t len = sz & ~RAW_FLAG;
+  if (sz & DIFF_FLAG) return ORC_CORRUPT;
+  uint32_t len = sz & SIZE_MASK;
   if (sz & RAW_FLAG) {
     if (len != (uint32_t)(n * w)) return ORC_CORRUPT;
     for (int64_t i = 0; i < n; i++) s[i] = get_word(rec + i * w, w);
@@ -671,18 +751,18 @@ static int dec_subbins(int w, const uint8_t* rec, uint32_t sz, int64_t n, uint64
   return rc;
 }
 
-void orc_encode_chunk(int dtype, const int64_t* b, const uint64_t* s, int64_t n, uint8_t* bin_rec,
+void orc_encode_chunk(int dtype, const int64_t* b, const uint64_t* s, const int64_t dims[3], uint8_t* bin_rec,
                       uint32_t* bin_size, uint8_t* sub_rec, uint32_t* sub_size) {
   int w = dtype == 0 ? 4 : 8;
-  *bin_size = enc_bins(w, b, n, bin_rec);
-  *sub_size = enc_subbins(w, s, n, sub_rec);
+  *bin_size = enc_bins(w, b, dims, bin_rec);
+  *sub_size = enc_subbins(w, s, dims[0] * dims[1] * dims[2], sub_rec);
 }
 
 /* ---------------------------------------------------------------- stream */
 
 #define HDR 128
 #define MAGIC 0x43504F4Cu /* "LOPC" */
-#define VERSION 1
+#define VERSION 2 /* format 1 (bin records DIFFNB only) is still read */
 
 static size_t pad16(size_t v) { return (v + 15) & ~(size_t)15; }
 
@@ -721,7 +801,8 @@ static tiling tiling_of(const orc_desc* d) {
 }
 
 /* Linear indices of the points of tile `tid`, row-major inside the (clipped) tile. */
-static int64_t tile_points(const tiling* T, int64_t tid, int64_t* idx) {
+/* Flat indices of chunk tid's points in chunk order; dims receives its clipped shape. */
+static int64_t tile_points(const tiling* T, int64_t tid, int64_t* idx, int64_t dims[3]) {
   int64_t tx = tid % T->nt[2], ty = (tid / T->nt[2]) % T->nt[1], tz = tid / (T->nt[2] * T->nt[1]);
   int64_t z0 = tz * T->t[0], y0 = ty * T->t[1], x0 = tx * T->t[2];
   int64_t z1 = z0 + T->t[0] < T->g.nz ? z0 + T->t[0] : T->g.nz;
@@ -731,6 +812,9 @@ static int64_t tile_points(const tiling* T, int64_t tid, int64_t* idx) {
   for (int64_t z = z0; z < z1; z++)
     for (int64_t y = y0; y < y1; y++)
       for (int64_t x = x0; x < x1; x++) idx[c++] = (z * T->g.ny + y) * T->g.nx + x;
+  dims[0] = z1 - z0;
+  dims[1] = y1 - y0;
+  dims[2] = x1 - x0;
   return c;
 }
 
@@ -813,19 +897,20 @@ int orc_compress(const orc_desc* d, const void* x, uint8_t* out, size_t cap, siz
   uint32_t* sizes = (uint32_t*)malloc(sizeof(uint32_t) * 2 * (size_t)T.ntiles);
   uint8_t** recs = (uint8_t**)malloc(sizeof(uint8_t*) * 2 * (size_t)T.ntiles);
   for (int64_t c = 0; c < T.ntiles; c++) {
-    int64_t m = tile_points(&T, c, idx);
+    int64_t dims[3];
+    int64_t m = tile_points(&T, c, idx, dims);
     for (int64_t i = 0; i < m; i++) {
       tb[i] = b[idx[i]];
       ts[i] = s[idx[i]];
     }
     recs[c] = (uint8_t*)malloc((size_t)m * w + 64);
     recs[T.ntiles + c] = (uint8_t*)malloc((size_t)m * w + 64);
-    sizes[c] = enc_bins(w, tb, m, recs[c]);
+    sizes[c] = enc_bins(w, tb, dims, recs[c]);
     sizes[T.ntiles + c] = enc_subbins(w, ts, m, recs[T.ntiles + c]);
   }
   size_t table = pad16((size_t)T.ntiles * 8);
   size_t total = HDR + table;
-  for (int64_t c = 0; c < 2 * T.ntiles; c++) total += pad16(sizes[c] & ~RAW_FLAG);
+  for (int64_t c = 0; c < 2 * T.ntiles; c++) total += pad16(sizes[c] & SIZE_MASK);
   if (total > cap) {
     rc = ORC_CAPACITY;
   } else {
@@ -834,7 +919,7 @@ int orc_compress(const orc_desc* d, const void* x, uint8_t* out, size_t cap, siz
     for (int64_t c = 0; c < 2 * T.ntiles; c++) put_u32(out + HDR + 4 * c, sizes[c]);
     size_t o = HDR + table;
     for (int64_t c = 0; c < 2 * T.ntiles; c++) {
-      uint32_t len = sizes[c] & ~RAW_FLAG;
+      uint32_t len = sizes[c] & SIZE_MASK;
       memcpy(out + o, recs[c], len);
       o += pad16(len);
     }
@@ -853,6 +938,7 @@ int orc_compress(const orc_desc* d, const void* x, uint8_t* out, size_t cap, siz
 
 typedef struct {
   orc_desc d;
+  int version;
   int constant;
   double eps, inv, cval;
   uint64_t nchunks, total;
@@ -860,8 +946,10 @@ typedef struct {
 
 static int parse_header(const uint8_t* in, size_t n, hdr_t* H) {
   if (!in || n < HDR) return ORC_CORRUPT;
-  if (get_word(in, 4) != MAGIC || get_word(in + 4, 2) != VERSION) return ORC_CORRUPT;
+  uint64_t version = get_word(in + 4, 2);
+  if (get_word(in, 4) != MAGIC || version < 1 || version > VERSION) return ORC_CORRUPT;
   memset(H, 0, sizeof(*H));
+  H->version = (int)version;
   H->d.dtype = in[6];
   H->d.ndim = in[7];
   if (H->d.dtype > 1 || (H->d.ndim != 2 && H->d.ndim != 3)) return ORC_CORRUPT;
@@ -929,7 +1017,7 @@ int orc_decompress(const uint8_t* in, size_t n, void* xhat, size_t cap_bytes) {
   size_t o = HDR + table;
   for (int64_t c = 0; c < 2 * T.ntiles; c++) {
     off[c] = o;
-    o += pad16((uint32_t)get_word(tab + 4 * c, 4) & ~RAW_FLAG);
+    o += pad16((uint32_t)get_word(tab + 4 * c, 4) & SIZE_MASK);
   }
   if (o != H.total) {
     free(off);
@@ -940,9 +1028,10 @@ int orc_decompress(const uint8_t* in, size_t n, void* xhat, size_t cap_bytes) {
   int64_t* tb = (int64_t*)malloc(sizeof(int64_t) * (size_t)cmax);
   uint64_t* ts = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)cmax);
   for (int64_t c = 0; c < T.ntiles && rc == ORC_OK; c++) {
-    int64_t m = tile_points(&T, c, idx);
+    int64_t dims[3];
+    int64_t m = tile_points(&T, c, idx, dims);
     uint32_t sb = (uint32_t)get_word(tab + 4 * c, 4), ss = (uint32_t)get_word(tab + 4 * (T.ntiles + c), 4);
-    rc = dec_bins(w, in + off[c], sb, m, tb);
+    rc = dec_bins(w, H.version, in + off[c], sb, dims, tb);
     if (rc == ORC_OK) rc = dec_subbins(w, in + off[T.ntiles + c], ss, m, ts);
     for (int64_t i = 0; i < m && rc == ORC_OK; i++) {
       double lo;

@@ -69,9 +69,11 @@ void orc_unbit(int w, const uint8_t* in, int64_t n32, uint8_t* words);
 size_t orc_rze(int g, const uint8_t* in, size_t L, uint8_t* out);
 int orc_unrze(int g, const uint8_t* in, size_t in_len, size_t L, uint8_t* out);
 
-/* One chunk's records (Sec. III-C): bins and subbins of its n points in chunk
- * order; each record buffer needs n*w bytes; sizes carry the raw flag (bit 31). */
-void orc_encode_chunk(int dtype, const int64_t* b, const uint64_t* s, int64_t n, uint8_t* bin_rec,
+/* One chunk's records (Sec. III-C): bins and subbins of its points in chunk order,
+ * the chunk being dims[0] x dims[1] x dims[2] points (2D: dims[0] = 1); each record
+ * buffer needs n*w bytes; sizes carry the raw flag (bit 31) and, for bins, the flag
+ * of the 1D-difference predictor (bit 30; otherwise the Lorenzo residual). */
+void orc_encode_chunk(int dtype, const int64_t* b, const uint64_t* s, const int64_t dims[3], uint8_t* bin_rec,
                       uint32_t* bin_size, uint8_t* sub_rec, uint32_t* sub_size);
 
 /* Whole stream. */

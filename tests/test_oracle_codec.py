@@ -106,7 +106,7 @@ def test_stream_header_fields(orc):
     st = orc.compress(x, 1, 1e-2)
     h = np.frombuffer(st[:128], np.uint8)
     assert st[:4] == b"LOPC"
-    assert int.from_bytes(st[4:6], "little") == 1
+    assert int.from_bytes(st[4:6], "little") == 2  # format 2: Lorenzo or 1D-difference bin records
     assert h[6] == 0 and h[7] == 2
     assert int.from_bytes(st[8:16], "little") == 70 and int.from_bytes(st[16:24], "little") == 90
     tiles = -(-70 // 64) * -(-90 // 64)
@@ -184,3 +184,90 @@ def test_capacity_and_corrupt(orc):
         b[pos] ^= 1 << int(rng.integers(0, 8))
         rc = orc.decompress_status(bytes(b), x.shape, x.dtype)
         assert rc in (0, orc.CORRUPT)
+
+
+# ------------------------------------------------------------ format 2 bin records
+
+M32 = np.uint64(0xAAAAAAAA)
+
+
+def nb_words(r, w=4):
+    mask = (1 << (8 * w)) - 1
+    m = 0xAAAAAAAAAAAAAAAA & mask
+    return np.array([((int(v) + m) ^ m) & mask for v in r.ravel()], np.uint64 if w == 8 else np.uint32)
+
+
+def record_of(orc, words, w=4):
+    """Bin record built from given mapped words with the separately pinned stages."""
+    return orc.rze(1, orc.bit(w, words.tobytes(), words.size))
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (5, 7, 9), (1, 64, 64), (1, 13, 30)])
+def test_lorenzo_residual_of_a_linear_ramp(orc, shape):
+    # b = c0 + cx x + cy y + cz z: the Lorenzo residual is c0 at the origin, cx / cy /
+    # cz along the three axis lines through it, and 0 everywhere else (a closed form)
+    c0, cx, cy, cz = 7, 3, -5, 11
+    z, y, x = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    b = (c0 + cx * x + cy * y + cz * z).astype(np.int64)
+    r = np.zeros(shape, np.int64)
+    r[0, 0, 0] = c0
+    r[0, 0, 1:] = cx
+    r[0, 1:, 0] = cy
+    r[1:, 0, 0] = cz
+    sb, rb, _, _ = orc.encode_chunk(0, b.ravel(), np.zeros(b.size, np.uint64), shape)
+    assert not (sb & orc.DIFF_FLAG) and not (sb & orc.RAW_FLAG)
+    assert rb == record_of(orc, nb_words(r))
+
+
+def test_rows_constant_along_x_take_the_1d_difference(orc):
+    # bins constant along x with random row values: the 1D difference is nonzero only
+    # at row starts (one row against the previous); the Lorenzo residual there is a
+    # second difference of four random rows, with more one bits: the 1D difference wins
+    rng = np.random.default_rng(0)
+    shape = (16, 16, 16)
+    rows = rng.integers(-2**20, 2**20, shape[:2])
+    b = np.repeat(rows[:, :, None], shape[2], axis=2).astype(np.int64)
+    sb, rb, _, _ = orc.encode_chunk(0, b.ravel(), np.zeros(b.size, np.uint64), shape)
+    assert sb & orc.DIFF_FLAG
+    d = np.diff(np.concatenate([[0], b.ravel()]))
+    assert rb == record_of(orc, nb_words(d))
+
+
+@pytest.mark.parametrize("shape,dt", [((20, 37, 33), np.float32), ((9, 40, 45), np.float64), ((130, 70), np.float32),
+                                      ((1, 3, 200), np.float64)])
+def test_format2_roundtrip_and_both_predictors(orc, shape, dt):
+    rng = np.random.default_rng(len(shape))
+    smooth = np.cumsum(np.cumsum(rng.standard_normal(shape), axis=-1), axis=0)
+    x = (smooth + (rng.random(shape) < 0.02) * 50.0).astype(dt)
+    for eb in (1e-2, 1e-4):
+        st = orc.compress(x, 1, eb)
+        y = orc.decompress(st)
+        assert orc.order_violations(x, y) == 0
+        assert np.abs(x.astype(np.float64) - y).max() <= orc.resolve_eps(x, 1, eb)["eps"]
+
+
+def test_format1_fixtures_still_decode(orc):
+    import pathlib
+    g = pathlib.Path(__file__).resolve().parent / "golden"
+    for name in ("v1_2d_f32", "v1_3d_f64", "v1_3d_f32_abs"):
+        st = (g / f"{name}.lopc").read_bytes()
+        assert int.from_bytes(st[4:6], "little") == 1
+        y = orc.decompress(st)
+        assert y.tobytes() == np.load(g / f"{name}_xhat.npy").tobytes()
+
+
+def test_predictor_flag_corruptions(orc):
+    import pathlib
+    g = pathlib.Path(__file__).resolve().parent / "golden"
+    st = bytearray((g / "v1_2d_f32.lopc").read_bytes())
+    st[128 + 3] |= 0x40                       # bit 30 of chunk 0's bin size in a format-1 stream
+    with pytest.raises(orc.OracleError):
+        orc.decompress(bytes(st))
+    rng = np.random.default_rng(1)
+    x = rng.uniform(-1.0, 1.0, (64, 64)).astype(np.float32)
+    st = bytearray(orc.compress(x, 0, 1e-9))  # bins of +-1e9 at random: stored raw
+    size = int.from_bytes(st[128:132], "little")
+    assert size & orc.RAW_FLAG
+    st[128 + 3] |= 0x40                       # a raw record with the predictor flag
+    with pytest.raises(orc.OracleError):
+        orc.decompress(bytes(st))
