@@ -45,7 +45,10 @@
 extern "C" {
 #endif
 
-#define LOPC_VERSION 1
+/* Stream format written by this library.  Format 2 codes each chunk's bins with a
+ * Lorenzo residual or a 1D difference (bit 30 of the chunk's size entry); format 1
+ * (1D difference only) is still read. */
+#define LOPC_VERSION 2
 
 /* Status codes. */
 #define LOPC_OK 0

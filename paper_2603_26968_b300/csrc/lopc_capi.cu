@@ -728,7 +728,7 @@ struct Header {
 
 int parse_header(const uint8_t* h, size_t n, Header* H) {
   if (!h || n < (size_t)kHeaderBytes) return LOPC_ERR_CORRUPT;
-  if (rd(h, 4) != kMagic || rd(h + 4, 2) != LOPC_VERSION) return LOPC_ERR_CORRUPT;
+  if (rd(h, 4) != kMagic || rd(h + 4, 2) < 1 || rd(h + 4, 2) > LOPC_VERSION) return LOPC_ERR_CORRUPT;
   memset(H, 0, sizeof(*H));
   H->d.dtype = h[6];
   H->d.ndim = h[7];

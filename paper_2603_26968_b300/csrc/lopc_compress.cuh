@@ -737,7 +737,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   constexpr int NBOX = G::BZ * G::BY * G::BX;  // entries of the box (the rare error path walks them)
   load_box_async<G, Raw>(raw, reinterpret_cast<const Raw*>(x), g, tb);
   for (int i = threadIdx.x; i < 3 * (G::NP / 32); i += NT) fa[i] = 0;  // both frontiers, risen bits
-  if (threadIdx.x == 0) cnt[0] = 0;  // the same-bin pair count of the flags
+  if (threadIdx.x == 0) cnt[0] = cnt[2] = cnt[3] = 0;  // same-bin pairs; the bin predictors' costs
   cp_async_wait_all();
   __syncthreads();
   bool bad = false;
@@ -782,6 +782,11 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   const bool col_in = sp.lz < tb.cz && sp.lx < tb.cx;
   const int64_t gz = tb.z0 + sp.lz, gx = tb.x0 + sp.lx;
   unsigned same_pairs = 0;  // same-bin neighbour pairs of the thread's points
+  // the bin record's predictor costs: one bits of the NB-mapped Lorenzo residuals and
+  // 1D differences of the thread's points (the Lorenzo stencil's seven lower-octant
+  // points are the neighbours -D[0..6] the flags load anyway)
+  unsigned cost_l = 0, cost_d = 0;
+  constexpr WordT NBM = (WordT)0xAAAAAAAAAAAAAAAAULL;
 #pragma unroll 1
   for (int j = 0; j < G::SEG; ++j) {
     uint32_t same = 0, lo = 0;
@@ -790,16 +795,38 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
     if (col_in && ly < tb.cy) {
       const B bp = bin[e];
       const K kp = key[e];
+      B nbin[14];
 #pragma unroll
       for (int k = 0; k < 14; ++k) {
         if (!G::HZ && dz_of(k) != 0) continue;
         const int e2 = e + G::off(dz_of(k), dy_of(k), dx_of(k));
-        if (bin[e2] == bp) {
+        nbin[k] = bin[e2];
+        if (nbin[k] == bp) {
           same |= 1u << k;
           const K kn = key[e2];
           if (kn < kp || (kn == kp && k < 7)) lo |= 1u << k;
         }
       }
+      const bool hx = sp.lx > 0, hy = ly > 0, hz = G::HZ && sp.lz > 0;
+      WordT r = (WordT)bp;
+      r -= hx ? (WordT)nbin[0] : (WordT)0;
+      r -= hy ? (WordT)nbin[1] : (WordT)0;
+      r += (hx && hy) ? (WordT)nbin[2] : (WordT)0;
+      if (G::HZ) {
+        r -= hz ? (WordT)nbin[3] : (WordT)0;
+        r += (hz && hx) ? (WordT)nbin[4] : (WordT)0;
+        r += (hz && hy) ? (WordT)nbin[5] : (WordT)0;
+        r -= (hz && hy && hx) ? (WordT)nbin[6] : (WordT)0;
+      }
+      WordT prev = 0;  // the point before this one in the chunk's point order
+      if (hx)
+        prev = (WordT)nbin[0];
+      else if (hy)
+        prev = (WordT)bin[G::entry(sp.lz, ly - 1, tb.cx - 1)];
+      else if (hz)
+        prev = (WordT)bin[G::entry(sp.lz - 1, tb.cy - 1, tb.cx - 1)];
+      cost_l += __popcll((uint64_t)((WordT)(r + NBM) ^ NBM));
+      cost_d += __popcll((uint64_t)((WordT)((WordT)bp - prev + NBM) ^ NBM));
     }
     const uint32_t up = same & ~lo & ~out_of_box_bits<G>(sp.lz, ly, sp.lx);
     const int o = sp.o0 + j * G::TX;
@@ -823,7 +850,12 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   }
   {
     const unsigned wsum = __reduce_add_sync(0xffffffffu, same_pairs);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&cnt[0], wsum);
+    const unsigned wl = __reduce_add_sync(0xffffffffu, cost_l), wd = __reduce_add_sync(0xffffffffu, cost_d);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&cnt[0], wsum);
+      atomicAdd(&cnt[2], wl);
+      atomicAdd(&cnt[3], wd);
+    }
   }
   __syncthreads();  // keys are dead from here on
   // same-bin pairs over the tile's points, against 16ths of the neighbour pairs a full
@@ -832,13 +864,15 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   const bool dense_tile = (unsigned long long)cnt[0] * 16ull > (unsigned long long)pairs_full * dense16;
   phase_mark(P, 1, t0);
 
-  // 3. bin record: DIFFNB_w, BIT_w, RZE_1; raw if that is not shorter
+  // 3. bin record (format 2): a predictor's residual, NB-mapped, BIT_w, RZE_1; raw if
+  //    that is not shorter.  The predictor is the chunk's Lorenzo residual (bins
+  //    outside the chunk count as 0), or the 1D difference along the chunk's point
+  //    order when its mapped words hold strictly fewer one bits.
   {
     const int n = tb.n, n32 = (n + 31) & ~31;
     const uint32_t raw = (uint32_t)n * W;
     const bool full = n == G::NP;
-    auto bin_of = [&](int i) -> WordT {
-      int lx2, ly2, lz2;
+    auto coords = [&](int i, int& lz2, int& ly2, int& lx2) {
       if (full) {
         lx2 = i % G::TX;
         ly2 = (i / G::TX) % G::TY;
@@ -848,15 +882,40 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
         ly2 = (i / tb.cx) % tb.cy;
         lz2 = i / (tb.cx * tb.cy);
       }
+    };
+    auto bin_of = [&](int i) -> WordT {
+      int lx2, ly2, lz2;
+      coords(i, lz2, ly2, lx2);
       return (WordT)bin[G::entry(lz2, ly2, lx2)];
     };
+    auto diff_of = [&](int i) -> WordT { return bin_of(i) - (i ? bin_of(i - 1) : (WordT)0); };
+    // sum over (a, b, c) in {0,1}^3 of (-1)^(a+b+c) bins[z-a][y-b][x-c], in the chunk
+    auto lorenzo_of = [&](int i) -> WordT {
+      int lx2, ly2, lz2;
+      coords(i, lz2, ly2, lx2);
+      const int e = G::entry(lz2, ly2, lx2);
+      const bool hx = lx2 > 0, hy = ly2 > 0;
+      WordT r = (WordT)bin[e];
+      r -= hx ? (WordT)bin[e - 1] : (WordT)0;
+      r -= hy ? (WordT)bin[e - G::BXP] : (WordT)0;
+      r += (hx && hy) ? (WordT)bin[e - G::BXP - 1] : (WordT)0;
+      if (G::HZ && lz2 > 0) {
+        const int ez = e - G::PP;
+        r -= (WordT)bin[ez];
+        r += hx ? (WordT)bin[ez - 1] : (WordT)0;
+        r += hy ? (WordT)bin[ez - G::BXP] : (WordT)0;
+        r -= (hx && hy) ? (WordT)bin[ez - G::BXP - 1] : (WordT)0;
+      }
+      return r;
+    };
+    constexpr WordT M = (WordT)0xAAAAAAAAAAAAAAAAULL;
+    auto nb = [&](WordT d) -> uint64_t { return (uint64_t)((WordT)(d + M) ^ M); };
+    const bool use_diff = cnt[3] < cnt[2];  // the costs summed during the flags
     uint32_t* planes = reinterpret_cast<uint32_t*>(smem);
     const RzeWork w = rze_work_at(smem + PS::L, PS::L);
-    constexpr WordT M = (WordT)0xAAAAAAAAAAAAAAAAULL;
     bit_transpose<NT, W>(n32, [&](int i) -> uint64_t {
       if (i >= n) return 0;
-      const WordT d = bin_of(i) - (i ? bin_of(i - 1) : (WordT)0);
-      return (uint64_t)((WordT)(d + M) ^ M);
+      return nb(use_diff ? diff_of(i) : lorenzo_of(i));
     }, planes);
     __syncthreads();
     uint8_t* slot = slots + (size_t)tid * kSlotBytes;
@@ -869,7 +928,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
       zero_tail16<NT>(stage, len);
       __syncthreads();
       copy16<NT>(slot, stage, len);
-      if (threadIdx.x == 0) sizes[tid] = len;
+      if (threadIdx.x == 0) sizes[tid] = len | (use_diff ? kDiffFlag : 0u);
     }
   }
   __syncthreads();  // bins, planes and the staged record are dead from here on
@@ -1278,12 +1337,12 @@ __global__ void __launch_bounds__(NT) k_scan_sizes(const FieldInfo* __restrict__
   const int64_t per = (m + NT - 1) / NT;
   const int64_t a = min(m, (int64_t)threadIdx.x * per), b = min(m, a + per);
   uint64_t c = 0;
-  for (int64_t i = a; i < b; ++i) c += pad16(sizes[i] & ~kRawFlag);
+  for (int64_t i = a; i < b; ++i) c += pad16(sizes[i] & kSizeMask);
   uint64_t total;
   uint64_t run = block_exclusive_scan<NT, uint64_t>(c, tmp, &total) + base;
   for (int64_t i = a; i < b; ++i) {
     offs[i] = run;
-    run += pad16(sizes[i] & ~kRawFlag);
+    run += pad16(sizes[i] & kSizeMask);
   }
   if (threadIdx.x == 0) P->total = base + total;
 }
@@ -1336,7 +1395,7 @@ __global__ void k_pack(const FieldInfo* __restrict__ F) {
     reinterpret_cast<uint32_t*>(out + kHeaderBytes)[i] = i < m ? sizes[i] : 0u;
   // records: one block per record, 16-byte copies
   for (int64_t c = blockIdx.x; c < m; c += gridDim.x) {
-    const uint64_t n16 = pad16(sizes[c] & ~kRawFlag) / 16;
+    const uint64_t n16 = pad16(sizes[c] & kSizeMask) / 16;
     const uint4* src = reinterpret_cast<const uint4*>(slots + (size_t)c * kSlotBytes);
     uint4* dst = reinterpret_cast<uint4*>(out + offs[c]);
     for (uint64_t j = threadIdx.x; j < n16; j += blockDim.x) dst[j] = src[j];

@@ -20,6 +20,7 @@ struct DecField {
   unsigned long long inv_m;
   int inv_e;
   int constant;
+  int version;            // stream format, from the header
   unsigned long long const_bits;
   int64_t tile_base;
 };
@@ -49,7 +50,7 @@ __global__ void k_dec_setup(DecField* F, int nf) {
     for (int k = 0; k < nb; ++k) v |= (uint64_t)h[o + k] << (8 * k);
     return v;
   };
-  bool ok = d.in_size >= (uint64_t)kHeaderBytes && rd(0, 4) == kMagic && rd(4, 2) == LOPC_VERSION &&
+  bool ok = d.in_size >= (uint64_t)kHeaderBytes && rd(0, 4) == kMagic && rd(4, 2) >= 1 && rd(4, 2) <= LOPC_VERSION &&
             h[6] == (uint8_t)d.g.dtype && h[7] == (uint8_t)d.g.ndim;
   const uint64_t total = ok ? rd(88, 8) : 0;
   ok = ok && total <= d.in_size && total >= (uint64_t)kHeaderBytes;
@@ -62,6 +63,7 @@ __global__ void k_dec_setup(DecField* F, int nf) {
     *d.status = kErrCorrupt;
     return;
   }
+  d.version = (int)rd(4, 2);
   d.const_bits = rd(72, 8);
   const int ex = (int)((iu >> 52) & 0x7ff);
   d.inv_m = (iu & 0xfffffffffffffULL) | (ex ? 0x10000000000000ULL : 0ULL);
@@ -89,12 +91,12 @@ __global__ void __launch_bounds__(NT) k_dec_offsets(const DecField* __restrict__
   const int64_t per = (m + NT - 1) / NT;
   const int64_t a = min(m, (int64_t)threadIdx.x * per), b = min(m, a + per);
   uint64_t c = 0;
-  for (int64_t i = a; i < b; ++i) c += pad16(tab[i] & ~kRawFlag);
+  for (int64_t i = a; i < b; ++i) c += pad16(tab[i] & kSizeMask);
   uint64_t sum;
   uint64_t run = block_exclusive_scan<NT, uint64_t>(c, tmp, &sum) + base;
   for (int64_t i = a; i < b; ++i) {
     d.offs[i] = run;
-    run += pad16(tab[i] & ~kRawFlag);
+    run += pad16(tab[i] & kSizeMask);
   }
   if (threadIdx.x == 0 && base + sum != total) atomicOr(d.status, kErrCorrupt);
 }
@@ -124,7 +126,80 @@ __device__ __forceinline__ uint64_t shfl_up_w(uint64_t v, int o) { return __shfl
 __device__ __forceinline__ uint32_t shfl_idx_w(uint32_t v, int l) { return __shfl_sync(0xffffffffu, v, l); }
 __device__ __forceinline__ uint64_t shfl_idx_w(uint64_t v, int l) { return __shfl_sync(0xffffffffu, v, l); }
 
-// One block per chunk: bins (RZE_1, BIT_w, DIFFNB_w inverses), then the lowest value
+// Inverse of a chunk's Lorenzo residual (format 2 bin records): inclusive prefix sums
+// of w[(z * cy + y) * cx + x] along x, then y, then z, modulo 2^(8 W).  Rows of 16
+// or 32 words are scanned by warp shuffles in segments of a row, rows of 64 in two
+// halves with a carry, other rows (clipped chunks) by one thread each; the y and z
+// sums take one thread per line.
+template <int NT, int ND, typename W_t>
+__device__ __forceinline__ void undo_lorenzo(W_t* w, int cz, int cy, int cx) {
+  constexpr int NWARP = NT / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int rows = cz * cy;
+  if (cx == 16 || cx == 32) {
+    const int n = rows * cx;
+    for (int base = wid * 32; base < n; base += NWARP * 32) {
+      const int i = base + lane;
+      W_t v = i < n ? w[i] : (W_t)0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const W_t y = __shfl_up_sync(0xffffffffu, v, o, cx);
+        if (o < cx && (lane & (cx - 1)) >= o) v += y;
+      }
+      if (i < n) w[i] = v;
+    }
+  } else if (cx == 64) {
+    for (int r = wid; r < rows; r += NWARP) {
+      W_t* row = w + r * 64;
+      W_t a = row[lane], b = row[32 + lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const W_t ya = __shfl_up_sync(0xffffffffu, a, o), yb = __shfl_up_sync(0xffffffffu, b, o);
+        if (lane >= o) {
+          a += ya;
+          b += yb;
+        }
+      }
+      b += __shfl_sync(0xffffffffu, a, 31);
+      row[lane] = a;
+      row[32 + lane] = b;
+    }
+  } else {
+    for (int r = threadIdx.x; r < rows; r += NT) {
+      W_t acc = 0;
+      for (int x = 0; x < cx; ++x) {
+        acc += w[r * cx + x];
+        w[r * cx + x] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  // a strided line in batches of 8 independent loads, summed in registers
+  auto scan_line = [&](W_t* p, int len, int stride) {
+    W_t acc = 0;
+    for (int a = 0; a < len; a += 8) {
+      W_t v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = a + u < len ? p[(a + u) * stride] : (W_t)0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        acc += v[u];
+        if (a + u < len) p[(a + u) * stride] = acc;
+      }
+    }
+  };
+  for (int l = threadIdx.x; l < cz * cx; l += NT) {
+    const int z = l / cx, x = l - z * cx;
+    scan_line(w + z * cy * cx + x, cy, cx);
+  }
+  if (ND == 3) {
+    __syncthreads();
+    const int plane = cy * cx;
+    for (int l = threadIdx.x; l < plane; l += NT) scan_line(w + l, cz, plane);
+  }
+}
+
+// One block per chunk: bins (RZE_1, BIT_w and the predictor's inverses), then the lowest value
 // of every bin of the tile's bin range (when it is small enough to cache), then
 // subbins (RZE_1, RZE_w, BIT_w inverses) and x_hat = the subbin-th value above the
 // bin's lowest value (Sec. III-E), written as the subbin words come out.
@@ -203,18 +278,23 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC, 4) k_decode(const DecFiel
       }
     }
   };
+  // format 2: bit 30 selects the 1D difference for an encoded bin record; format 1
+  // has no other predictor
+  if ((sb & kDiffFlag) && (df.version == 1 || (sb & kRawFlag))) bad = 1;
+  const bool use_diff = df.version == 1 || (sb & kDiffFlag);
+  const uint32_t sb_len = sb & kSizeMask;
   if (sb & kRawFlag) {
     prefetch_sub();
-    if ((sb & ~kRawFlag) != raw) bad = 1;
+    if (sb_len != raw) bad = 1;
     for (int i = threadIdx.x; i < n; i += NT) wb[i] = reinterpret_cast<const W_t*>(rb)[i];
     __syncthreads();
   } else {
-    if (sb >= raw) bad = 1;  // an encoded record is shorter than the raw chunk
+    if (sb_len >= raw) bad = 1;  // an encoded record is shorter than the raw chunk
     __syncthreads();
     if (!bad) {
-      copy16<NT>(A, rb, sb);
+      copy16<NT>(A, rb, sb_len);
       __syncthreads();
-      if (!rze_decode<NT, 1>(A, sb, (uint32_t)W * n32, Bf, w)) bad = 1;
+      if (!rze_decode<NT, 1>(A, sb_len, (uint32_t)W * n32, Bf, w)) bad = 1;
       __syncthreads();
     }
     dec_mark(0, t0);
@@ -228,6 +308,9 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC, 4) k_decode(const DecFiel
           bad = 1;
       });
       __syncthreads();
+    }
+    if (!bad && !use_diff) undo_lorenzo<NT, ND>(wb, tb.cz, tb.cy, tb.cx);
+    if (!bad && use_diff) {
       // prefix sum of the deltas (mod 2^(8W)): warp w scans words [w*per, (w+1)*per)
       // in rows of 32 (one word per lane, shuffle scan, running carry), then adds
       // the totals of the warps before it

@@ -13,7 +13,9 @@ namespace lopc {
 
 constexpr int kHeaderBytes = 128;
 constexpr uint32_t kMagic = 0x43504F4Cu;  // "LOPC"
-constexpr uint32_t kRawFlag = 0x80000000u;
+constexpr uint32_t kRawFlag = 0x80000000u;   // size-table entry: the record is stored raw
+constexpr uint32_t kDiffFlag = 0x40000000u;  // bin record of format 2 coded with the 1D difference
+constexpr uint32_t kSizeMask = 0x3FFFFFFFu;  // the record length
 
 // Status bits collected on the device and mapped to a return code on the host.
 enum : uint32_t {

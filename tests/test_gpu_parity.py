@@ -139,6 +139,51 @@ def test_corrupt_streams_never_fault(L, orc):
     torch.cuda.synchronize()
 
 
+def test_gpu_decodes_format1_fixtures(L):
+    import pathlib
+    g = pathlib.Path(__file__).resolve().parent / "golden"
+    for name in ("v1_2d_f32", "v1_3d_f64", "v1_3d_f32_abs"):
+        st = (g / f"{name}.lopc").read_bytes()
+        want = np.load(g / f"{name}_xhat.npy")
+        t = torch.frombuffer(bytearray(st), dtype=torch.uint8).cuda()
+        y = L.decompress(t)
+        assert y.cpu().numpy().tobytes() == want.tobytes()
+
+
+def test_predictor_flag_corruptions_gpu(L, orc):
+    import pathlib
+    g = pathlib.Path(__file__).resolve().parent / "golden"
+    b = bytearray((g / "v1_2d_f32.lopc").read_bytes())
+    b[128 + 3] |= 0x40  # the format-2 predictor flag in a format-1 stream
+    t = torch.frombuffer(b, dtype=torch.uint8).cuda()
+    assert L.decompress_status(t, (70, 90), torch.float32) == -5
+    rng = np.random.default_rng(1)
+    x = rng.uniform(-1.0, 1.0, (64, 64)).astype(np.float32)
+    b = bytearray(orc.compress(x, 0, 1e-9))
+    assert int.from_bytes(b[128:132], "little") & 0x80000000
+    b[128 + 3] |= 0x40  # the predictor flag on a raw record
+    t = torch.frombuffer(b, dtype=torch.uint8).cuda()
+    assert L.decompress_status(t, (64, 64), torch.float32) == -5
+    torch.cuda.synchronize()
+
+
+def test_both_bin_predictors_occur(L, orc):
+    # a smooth field takes the Lorenzo residual; rows constant along x take the 1D
+    # difference; streams equal the oracle's either way
+    rng = np.random.default_rng(2)
+    rows = rng.integers(-2**20, 2**20, (32, 32)).astype(np.float64)
+    x = np.repeat(rows[:, :, None], 32, axis=2).astype(np.float32)
+    st = assert_parity(L, orc, x, 0, 1.0)[0]
+    nch = int.from_bytes(st[80:88], "little")
+    tab = np.frombuffer(st[128:128 + 4 * nch], np.uint32)
+    assert (tab & 0x40000000).any()
+    x = bumps((40, 50, 60), np.float32)
+    st = assert_parity(L, orc, x, 1, 1e-3)[0]
+    nch = int.from_bytes(st[80:88], "little")
+    tab = np.frombuffer(st[128:128 + 4 * nch], np.uint32)
+    assert ((tab & 0xC0000000) == 0).any()
+
+
 # ------------------------------------------------------------ full-size configs
 
 def lfp_local_equality(x: torch.Tensor, b: torch.Tensor, s: torch.Tensor) -> int:
@@ -195,11 +240,12 @@ def split_stream(st: bytes):
     offs = []
     for v in tab:
         offs.append(o)
-        o += ((int(v) & 0x7FFFFFFF) + 15) // 16 * 16
+        o += ((int(v) & 0x3FFFFFFF) + 15) // 16 * 16
     return tab, offs
 
 
 def tile_points(shape, tile, tid):
+    """Flat indices of chunk tid's points in chunk order, and the clipped chunk shape."""
     sh = (1,) + tuple(shape) if len(shape) == 2 else tuple(shape)
     nt = [-(-sh[k] // tile[k]) for k in range(3)]
     tz, rem = divmod(tid, nt[1] * nt[2])
@@ -207,7 +253,7 @@ def tile_points(shape, tile, tid):
     z0, y0, x0 = tz * tile[0], ty * tile[1], tx * tile[2]
     z1, y1, x1 = min(z0 + tile[0], sh[0]), min(y0 + tile[1], sh[1]), min(x0 + tile[2], sh[2])
     zz, yy, xx = np.meshgrid(np.arange(z0, z1), np.arange(y0, y1), np.arange(x0, x1), indexing="ij")
-    return ((zz * sh[1] + yy) * sh[2] + xx).ravel()
+    return ((zz * sh[1] + yy) * sh[2] + xx).ravel(), (z1 - z0, y1 - y0, x1 - x0)
 
 
 FULL = [
@@ -239,10 +285,10 @@ def test_full_size_sampled_parity(L, orc, name, make, mode, eb, tile):
     nch = len(tab) // 2
     bn, sn = b_t.view(-1).cpu().numpy(), s_t.view(-1).cpu().numpy().astype(np.uint64)
     for tid in list(rng.integers(0, nch, 40)) + [0, nch - 1]:
-        pts = tile_points(x.shape, tile, int(tid))
-        sb, rb, ss, rs = orc.encode_chunk(dc, bn[pts], sn[pts])
-        assert int(tab[tid]) == sb and st[offs[tid]:offs[tid] + (sb & 0x7FFFFFFF)] == rb
-        assert int(tab[nch + tid]) == ss and st[offs[nch + tid]:offs[nch + tid] + (ss & 0x7FFFFFFF)] == rs
+        pts, cshape = tile_points(x.shape, tile, int(tid))
+        sb, rb, ss, rs = orc.encode_chunk(dc, bn[pts], sn[pts], cshape)
+        assert int(tab[tid]) == sb and st[offs[tid]:offs[tid] + (sb & 0x3FFFFFFF)] == rb
+        assert int(tab[nch + tid]) == ss and st[offs[nch + tid]:offs[nch + tid] + (ss & 0x3FFFFFFF)] == rs
     # decompression: error bound, x_hat <= x, neighbour order, sampled values
     y = L.decompress(st_t)
     yd = y.double()
