@@ -273,16 +273,17 @@ def configs_leg(torch, lopc, fields, flush, steps, warmup):
     return out
 
 
-def e2e_leg(torch, lopc, x_np, eb, steps, warmup, dev):
+def e2e_leg(torch, lopc, x_np, eb, steps, warmup, dev, NB=2, dec_own_stream=True):
     """Host to host through the public (asynchronous) batch calls: every step uploads
     its field from pinned memory, compresses it, downloads the stream, uploads it
-    again, decompresses and downloads the field.  Two buffer sets, a software
-    pipeline on the compute stream (step k+1's compression is enqueued before step
-    k's decompression, which waits for its stream's round trip) and separate copy
-    streams for fields and for streams let the copies overlap the kernels; the host
-    waits only to learn each stream's length."""
+    again, decompresses and downloads the field.  NB buffer sets, compression and
+    decompression on streams of their own (step k's decompression, which waits for
+    its stream's round trip, runs beside step k+1's compression) and separate copy
+    streams for fields and for streams let the copies of both directions overlap the
+    kernels; the host waits only to learn each stream's length.  The timed region
+    opens before the first timed step's upload and closes after the last step's
+    download, so pipeline fill and drain are inside it."""
     import ctypes as C
-    NB = 2
     shape, nbytes = tuple(x_np.shape), x_np.nbytes
     d = lopc.make_desc(shape, "f32", lopc.NOA, eb)
     hx = torch.from_numpy(x_np).pin_memory()
@@ -296,8 +297,10 @@ def e2e_leg(torch, lopc, x_np, eb, steps, warmup, dev):
     dws = [torch.empty(lopc.decompress_workspace_size(d), dtype=torch.uint8, device=dev) for _ in range(NB)]
     dst = [torch.zeros(1, dtype=torch.int32, device=dev) for _ in range(NB)]
     size_h = torch.zeros(NB, dtype=torch.int64).pin_memory()
-    # field upload, field download, stream download, stream upload, compute
-    s_xin, s_xout, s_sout, s_sin, s_comp = (torch.cuda.Stream(device=dev) for _ in range(5))
+    # field upload, field download, stream download, stream upload, compression, decompression
+    s_xin, s_xout, s_sout, s_sin, s_comp, s_dec = (torch.cuda.Stream(device=dev) for _ in range(6))
+    if not dec_own_stream:
+        s_dec = s_comp  # step k's decompression queued behind step k+1's compression
     ev = {k: [torch.cuda.Event() for _ in range(NB)] for k in ("x", "c", "so", "si", "d", "y")}
     used = {k: [False] * NB for k in ev}
     descs = lopc._descs([d])
@@ -337,36 +340,45 @@ def e2e_leg(torch, lopc, x_np, eb, steps, warmup, dev):
         torch.cuda.synchronize()
         t_start = time.perf_counter()
 
-    if warmup == 0:
-        start_clock()
-    upload_x(0)
+    # fields are uploaded NB - 1 steps ahead: a field's upload then has about NB - 1
+    # compressions to hide under, while the previous fields' downloads share the link
+    ahead = NB - 1
+
+    def upload(j):
+        if j == warmup:
+            start_clock()  # before the first timed step's upload is enqueued
+        upload_x(j)
+
+    for j in range(min(ahead, total)):
+        upload(j)
     compress(0)
     for k in range(total):
         b = k % NB
+        if k + ahead < total:
+            upload(k + ahead)  # its buffer's previous field (step k - 1) is compressed
         if k + 1 < total:
-            if k + 1 == warmup:
-                start_clock()
-            upload_x(k + 1)
             compress(k + 1)  # runs while step k's stream makes its round trip
         ev["c"][b].synchronize()
         n = int(size_h[b])
         with torch.cuda.stream(s_sout):
             s_sout.wait_event(ev["c"][b])
+            wait(s_sout, "si", b)  # the buffer's previous stream was uploaded from hs[b]
             hs[b][:n].copy_(comps[b].outs[0][:n], non_blocking=True)
             rec("so", b, s_sout)
         with torch.cuda.stream(s_sin):
             s_sin.wait_event(ev["so"][b])
+            wait(s_sin, "d", b)  # the buffer's previous stream was decompressed from ins[b]
             ins[b][:n].copy_(hs[b][:n], non_blocking=True)
             rec("si", b, s_sin)
-        with torch.cuda.stream(s_comp):
-            s_comp.wait_event(ev["si"][b])
-            wait(s_comp, "y", b)  # the buffer's previous field was downloaded
+        with torch.cuda.stream(s_dec):
+            s_dec.wait_event(ev["si"][b])
+            wait(s_dec, "y", b)  # the buffer's previous field was downloaded
             rc = lopc.lib().lopc_batch_decompress(
                 1, descs, (C.c_void_p * 1)(ins[b].data_ptr()), (C.c_size_t * 1)(n),
                 (C.c_void_p * 1)(xh[b].data_ptr()), C.c_void_p(dst[b].data_ptr()), C.c_void_p(dws[b].data_ptr()),
-                dws[b].numel(), C.c_void_p(s_comp.cuda_stream))
+                dws[b].numel(), C.c_void_p(s_dec.cuda_stream))
             assert rc == 0, rc
-            rec("d", b, s_comp)
+            rec("d", b, s_dec)
         with torch.cuda.stream(s_xout):
             s_xout.wait_event(ev["d"][b])
             hy[b].copy_(xh[b], non_blocking=True)
@@ -376,9 +388,10 @@ def e2e_leg(torch, lopc, x_np, eb, steps, warmup, dev):
     dt = time.perf_counter() - t_start
     ok = all(int(v) == 0 for v in torch.cat(dst).cpu())
     return {"value": steps * nbytes / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h),
-            "pipelined": "two buffer sets; compute stream runs step k+1's compression before step k's "
-                         "decompression; separate copy streams for fields and streams",
+            "d2h_bytes_per_step": int(d2h), "steps": steps, "warmup": warmup,
+            "pipelined": f"{NB} buffer sets; compression and decompression on streams of their own (step k's "
+                         "decompression beside step k+1's compression); separate copy streams for fields and "
+                         "streams",
             "statuses_ok": bool(ok)}
 
 
@@ -641,7 +654,8 @@ def main():
                             "fixpoint_sweeps_max": f2[1], "fixpoint_work": lopc.last_fixpoint_work()}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    e2e = e2e_leg(torch, lopc, x_np, args.eb, args.steps, args.warmup, dev)
+    # enough steps that the copy pipeline's fill and drain do not dominate
+    e2e = e2e_leg(torch, lopc, x_np, args.eb, max(args.steps, 20), args.warmup, dev)
     del ws, dws, out, xhat
 
     configs = None
