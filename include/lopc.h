@@ -8,9 +8,13 @@
  *   - half-width quantizer, bins and subbins ..................... Sec. III-A
  *   - flags and subbin repair (Algorithms 1, 2) .................. Sec. III-B, III-D
  *   - termination, minimality, resolution ........................ Sec. III-E
- *   - lossless coding: DIFFNB.BIT.RZE_1 (bins), BIT.RZE_w.RZE_1 (subbins),
+ *   - lossless coding: bins as a Lorenzo or 1D-difference residual, NB-mapped, then
+ *     BIT.RZE_1 (the paper's DIFFNB.BIT.RZE_1 is the 1D case); subbins BIT.RZE_w.RZE_1;
  *     independent 16 KiB chunks ................................... Sec. III-C, II-C
  *   - decoding (bin, subbin) to a value .......................... Sec. III-D, III-E
+ *   - the repair schedule: tiles, or the paper's worklist ........... Sec. III-D
+ *   - verification: local order, critical points, false positives /
+ *     negatives / types, error bound, PSNR ......................... Sec. II, Table III
  * Where the paper leaves a choice open (neighbourhood, tie-break direction, exact
  * quantizer arithmetic, stream layout), the library fixes one reading; the stream
  * layout is described in the project's design notes.

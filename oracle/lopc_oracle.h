@@ -10,7 +10,8 @@
  *   - the half-width quantizer b = round(x / eps) (Sec. III-A);
  *   - flags and the subbin repair of Algorithms 1 and 2, as the least fixpoint
  *     (Sec. III-B, III-E) and, as a cross-check, as the paper's own iteration;
- *   - lossless coding: DIFFNB.BIT.RZE_1 for bins, BIT.RZE_w.RZE_1 for subbins over
+ *   - lossless coding: a Lorenzo or 1D-difference residual (format 2; DIFFNB only in
+ *     format 1), NB mapping, BIT, RZE_1 for bins, BIT.RZE_w.RZE_1 for subbins over
  *     16 KiB chunks (Sec. III-C);
  *   - the decoder: subbin k of bin b decodes to the k-th representable value above
  *     the lowest value of the bin (Sec. III-E);

@@ -1,5 +1,6 @@
 // lopc_decompress.cuh -- decompression kernels: record offsets from the size table,
-// and one block per chunk that undoes RZE/BIT/DIFFNB for bins and subbins and writes
+// and one block per chunk that undoes RZE/BIT and the bin predictor (Lorenzo or 1D
+// difference) for bins, RZE/RZE/BIT for subbins, and writes
 // x_hat = succ^s(lowest value of bin b) (Sec. III-D, III-E).
 #pragma once
 #include "lopc_compress.cuh"
