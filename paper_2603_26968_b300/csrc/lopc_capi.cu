@@ -400,7 +400,7 @@ int launch_epilogue(const Table& t, const FieldInfo* dF, cudaStream_t st) {
   if ((rc = launch_class_encode<double, 2>(t, 2, dF, st))) return rc;
   if ((rc = launch_class_encode<double, 3>(t, 3, dF, st))) return rc;
   LAUNCH("scan_sizes", st, k_scan_sizes<1024><<<t.n(), 1024, 0, st>>>(dF));
-  LAUNCH("pack", st, k_pack<<<dim3(sm_count() * 2, t.n()), 256, 0, st>>>(dF));
+  LAUNCH("pack", st, k_pack<<<dim3(sm_count() * 8, t.n()), 256, 0, st>>>(dF));
   LAUNCH("finalize", st, k_finalize<<<(t.n() + 63) / 64, 64, 0, st>>>(dF, t.n()));
   CK(cudaGetLastError());
   return LOPC_OK;

@@ -1332,19 +1332,8 @@ __global__ void __launch_bounds__(NT) k_scan_sizes(const FieldInfo* __restrict__
   }
   const int64_t m = 2 * fi.g.ntiles;
   const uint64_t base = kHeaderBytes + pad16((uint64_t)m * 4);
-  const uint32_t* __restrict__ sizes = fi.sizes;
-  uint64_t* __restrict__ offs = fi.offs;
-  const int64_t per = (m + NT - 1) / NT;
-  const int64_t a = min(m, (int64_t)threadIdx.x * per), b = min(m, a + per);
-  uint64_t c = 0;
-  for (int64_t i = a; i < b; ++i) c += pad16(sizes[i] & kSizeMask);
-  uint64_t total;
-  uint64_t run = block_exclusive_scan<NT, uint64_t>(c, tmp, &total) + base;
-  for (int64_t i = a; i < b; ++i) {
-    offs[i] = run;
-    run += pad16(sizes[i] & kSizeMask);
-  }
-  if (threadIdx.x == 0) P->total = base + total;
+  const uint64_t end = record_offsets<NT>(fi.sizes, m, base, fi.offs, tmp);
+  if (threadIdx.x == 0) P->total = end;
 }
 
 __device__ __forceinline__ void put_u64(uint8_t* p, uint64_t v) {
@@ -1393,12 +1382,20 @@ __global__ void k_pack(const FieldInfo* __restrict__ F) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)(table_end - kHeaderBytes) / 4;
        i += (int64_t)gridDim.x * blockDim.x)
     reinterpret_cast<uint32_t*>(out + kHeaderBytes)[i] = i < m ? sizes[i] : 0u;
-  // records: one block per record, 16-byte copies
-  for (int64_t c = blockIdx.x; c < m; c += gridDim.x) {
+  // records: one warp per record, 16-byte copies, two in flight per lane
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < m; c += warps) {
     const uint64_t n16 = pad16(sizes[c] & kSizeMask) / 16;
     const uint4* src = reinterpret_cast<const uint4*>(slots + (size_t)c * kSlotBytes);
     uint4* dst = reinterpret_cast<uint4*>(out + offs[c]);
-    for (uint64_t j = threadIdx.x; j < n16; j += blockDim.x) dst[j] = src[j];
+    uint64_t j = lane;
+    for (; j + 32 < n16; j += 64) {
+      const uint4 a = src[j], b = src[j + 32];
+      dst[j] = a;
+      dst[j + 32] = b;
+    }
+    if (j < n16) dst[j] = src[j];
   }
 }
 

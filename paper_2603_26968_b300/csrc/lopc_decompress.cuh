@@ -89,17 +89,8 @@ __global__ void __launch_bounds__(NT) k_dec_offsets(const DecField* __restrict__
     return;
   }
   const uint32_t* tab = reinterpret_cast<const uint32_t*>(d.in + kHeaderBytes);
-  const int64_t per = (m + NT - 1) / NT;
-  const int64_t a = min(m, (int64_t)threadIdx.x * per), b = min(m, a + per);
-  uint64_t c = 0;
-  for (int64_t i = a; i < b; ++i) c += pad16(tab[i] & kSizeMask);
-  uint64_t sum;
-  uint64_t run = block_exclusive_scan<NT, uint64_t>(c, tmp, &sum) + base;
-  for (int64_t i = a; i < b; ++i) {
-    d.offs[i] = run;
-    run += pad16(tab[i] & kSizeMask);
-  }
-  if (threadIdx.x == 0 && base + sum != total) atomicOr(d.status, kErrCorrupt);
+  const uint64_t end = record_offsets<NT>(tab, m, base, d.offs, tmp);
+  if (threadIdx.x == 0 && end != total) atomicOr(d.status, kErrCorrupt);
 }
 
 __global__ void k_dec_finalize(const DecField* __restrict__ F, int nf) {

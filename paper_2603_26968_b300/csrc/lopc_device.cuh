@@ -498,4 +498,33 @@ __device__ __forceinline__ V block_exclusive_scan(V v, V* tmp, V* total) {
   return res;
 }
 
+// Stream offsets of m records placed back to back from `base`, each taking its size
+// (kSizeMask bits of sizes[i]) padded to 16 bytes: offs[i] = base + the padded sizes
+// before i.  The block walks the table in chunks of 4 NT sizes, four consecutive ones
+// per thread, with one block scan per chunk and a running carry.  Returns base + the
+// padded total (in every thread).
+__host__ __device__ constexpr uint64_t pad16_u(uint64_t v) { return (v + 15) & ~(uint64_t)15; }
+
+template <int NT>
+__device__ __forceinline__ uint64_t record_offsets(const uint32_t* __restrict__ sizes, int64_t m, uint64_t base,
+                                                   uint64_t* __restrict__ offs, uint64_t* tmp) {
+  uint64_t carry = base;
+  for (int64_t c0 = 0; c0 < m; c0 += 4 * NT) {
+    const int64_t i0 = c0 + 4 * (int64_t)threadIdx.x;
+    uint64_t p[4], sum = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      p[u] = sum;
+      sum += i0 + u < m ? pad16_u(sizes[i0 + u] & kSizeMask) : 0;
+    }
+    uint64_t tot;
+    const uint64_t ex = block_exclusive_scan<NT, uint64_t>(sum, tmp, &tot) + carry;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i0 + u < m) offs[i0 + u] = ex + p[u];
+    carry += tot;
+  }
+  return carry;
+}
+
 }  // namespace lopc
