@@ -258,7 +258,9 @@ LOPC_API int lopc_last_round_tiles(int64_t* out, int n);
 
 /* Measurement aid: work of the tile-local fixpoint in the last compression on this
  * thread: point evaluations and subbin raises in the tile pass, then the same in
- * the reruns.  Copies min(n, 4) values and returns 4. */
+ * the reruns, then the rerun tiles loaded and how many of them found every
+ * constraint into the tile holding (check only).  Copies min(n, 6) values and
+ * returns 6. */
 LOPC_API int lopc_last_fixpoint_work(int64_t* out, int n);
 
 /* Measurement aid: while enabled, the decoder adds up SM cycles per phase over all

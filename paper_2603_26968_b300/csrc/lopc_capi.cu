@@ -100,7 +100,7 @@ thread_local Profiler g_prof;
   } while (0)
 thread_local int64_t g_last_rounds = 0, g_last_tile_runs = 0, g_last_fix_iters = 0, g_last_fix_iters_max = 0;
 thread_local int64_t g_last_phase[9] = {};
-thread_local int64_t g_last_work[4] = {};
+thread_local int64_t g_last_work[6] = {};
 thread_local std::vector<int64_t> g_round_tiles;  // tiles listed per round (host-driven loop only)
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -703,7 +703,7 @@ int compress_one(const lopc_field_desc* d, const void* d_x, void* d_out, size_t 
   g_last_fix_iters = (int64_t)hp.fix_iters;
   g_last_fix_iters_max = (int64_t)hp.fix_iters_max;
   for (int k = 0; k < 9; ++k) g_last_phase[k] = (int64_t)hp.phase[k];
-  for (int k = 0; k < 4; ++k) g_last_work[k] = (int64_t)hp.work[k];
+  for (int k = 0; k < 6; ++k) g_last_work[k] = (int64_t)hp.work[k];
   // the repair ran even if the output was too small: report the repair's status first
   if (res.status == LOPC_ERR_CAPACITY && subbins_out) res.status = LOPC_OK;
   if (res.status) return res.status;
@@ -1349,8 +1349,8 @@ int lopc_last_round_tiles(int64_t* out, int n) {
 }
 
 int lopc_last_fixpoint_work(int64_t* out, int n) {
-  for (int k = 0; k < n && k < 4; ++k) out[k] = g_last_work[k];
-  return 4;
+  for (int k = 0; k < n && k < 6; ++k) out[k] = g_last_work[k];
+  return 6;
 }
 
 void lopc_profile_enable(int on) {

@@ -51,7 +51,7 @@ __global__ void k_init_params(const FieldInfo* F, int nf) {
   P->fix_iters = 0;
   P->fix_iters_max = 0;
   for (int k = 0; k < 9; ++k) P->phase[k] = 0;
-  for (int k = 0; k < 4; ++k) P->work[k] = 0;
+  for (int k = 0; k < 6; ++k) P->work[k] = 0;
   P->fast_ok = 0;
   P->inv_f = 0.f;
 }
@@ -1098,7 +1098,12 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
         }
       }
     }
-    if (!__syncthreads_or(first)) {  // every constraint into this tile holds
+    const bool idle = !__syncthreads_or(first);
+    if (threadIdx.x == 0) {
+      atomicAdd(&P->work[4], 1ull);
+      if (idle) atomicAdd(&P->work[5], 1ull);
+    }
+    if (idle) {  // every constraint into this tile holds
       phase_mark(P, 7, t0);
       continue;
     }

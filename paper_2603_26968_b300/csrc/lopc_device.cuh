@@ -45,7 +45,7 @@ struct Params {
   unsigned long long fix_iters;   // sum over tile runs of fixpoint sweeps
   unsigned long long fix_iters_max;
   unsigned long long phase[9];    // SM cycles spent per kernel phase (block-summed, for measurement)
-  unsigned long long work[4];     // fixpoint point evaluations and raises: tile pass, reruns
+  unsigned long long work[6];     // fixpoint evaluations and raises: tile pass, reruns; rerun tiles run, of them idle
 };
 
 // Adds a and b, summed over the block, to dst[0] and dst[1] (all threads call it).

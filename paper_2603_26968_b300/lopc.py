@@ -312,9 +312,10 @@ def last_phase_cycles() -> list:
 
 def last_fixpoint_work() -> dict:
     """Fixpoint point evaluations and raises of the last compression (pass, reruns)."""
-    v = (C.c_int64 * 4)()
-    lib().lopc_last_fixpoint_work(v, 4)
-    return {"pass_evals": v[0], "pass_raises": v[1], "rerun_evals": v[2], "rerun_raises": v[3]}
+    v = (C.c_int64 * 6)()
+    lib().lopc_last_fixpoint_work(v, 6)
+    return {"pass_evals": v[0], "pass_raises": v[1], "rerun_evals": v[2], "rerun_raises": v[3],
+            "rerun_tiles": v[4], "rerun_idle": v[5]}
 
 
 def last_round_tiles() -> list:
