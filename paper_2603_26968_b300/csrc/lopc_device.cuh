@@ -223,7 +223,7 @@ __device__ __forceinline__ bool quantize_fast(T x, float inv_f, int fast_ok, uns
         const float r = rintf(t);
         const float room = __fsub_rn(0.5f, fabsf(__fsub_rn(t, r)));
         if (room > __fmul_rn(at, 9.5367431640625e-07f)) {  // 2^-20
-          bin = (long long)r;
+          bin = (long long)__float2int_rn(r);  // |r| < 2^21 and integral: exact in 32 bits
           return true;
         }
       }
