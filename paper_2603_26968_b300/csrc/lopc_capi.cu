@@ -217,7 +217,7 @@ void layout_table(Table& t) {
 // Per-field part of a compression workspace: state, subbins, lower masks, record
 // sizes and offsets, the dirty bitmap and the record slots.
 struct FieldPart {
-  size_t params, s, cm, sizes, offs, dirty, slots, total;
+  size_t params, s, cm, sizes, offs, dirty, tkey, order, rank, slots, total;
 };
 
 FieldPart field_part(const Geometry& g) {
@@ -236,6 +236,12 @@ FieldPart field_part(const Geometry& g) {
   o = align256(o + 16 * (size_t)g.ntiles);
   L.dirty = o;
   o = align256(o + 4 * (size_t)dirty_words(g.ntiles));
+  L.tkey = o;
+  o = align256(o + 4 * (size_t)g.ntiles);
+  L.order = o;
+  o = align256(o + 4 * (size_t)g.ntiles);
+  L.rank = o;
+  o = align256(o + 4 * (size_t)g.ntiles);
   L.slots = o;
   o = align256(o + 2 * (size_t)g.ntiles * kSlotBytes);
   L.total = o;
@@ -267,6 +273,9 @@ FieldInfo field_entry(const lopc_field_desc* d, const void* x, void* out, size_t
   f.sizes = reinterpret_cast<uint32_t*>(base + L.sizes);
   f.offs = reinterpret_cast<uint64_t*>(base + L.offs);
   f.dirty = reinterpret_cast<uint32_t*>(base + L.dirty);
+  f.tkey = reinterpret_cast<uint32_t*>(base + L.tkey);
+  f.order = reinterpret_cast<uint32_t*>(base + L.order);
+  f.rank = reinterpret_cast<uint32_t*>(base + L.rank);
   f.slots = base + L.slots;
   f.bins_out = bins_out;
   f.size_out = size_out;
@@ -371,7 +380,11 @@ int launch_pre(const Table& t, const FieldInfo* dF, cudaStream_t st, int fix = 1
   if ((rc = launch_class_pre<float, 2>(t, 0, dF, fix, st))) return rc;
   if ((rc = launch_class_pre<float, 3>(t, 1, dF, fix, st))) return rc;
   if ((rc = launch_class_pre<double, 2>(t, 2, dF, fix, st))) return rc;
-  return launch_class_pre<double, 3>(t, 3, dF, fix, st);
+  if ((rc = launch_class_pre<double, 3>(t, 3, dF, fix, st))) return rc;
+  // each field's tiles in ascending smallest value: reruns visit them in that order
+  LAUNCH("order", st, k_order<1024><<<t.n(), 1024, 0, st>>>(dF));
+  CK(cudaGetLastError());
+  return LOPC_OK;
 }
 
 // One rerun round: of every tile (list == null, the first round) or of the listed ones.

@@ -737,7 +737,10 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   constexpr int NBOX = G::BZ * G::BY * G::BX;  // entries of the box (the rare error path walks them)
   load_box_async<G, Raw>(raw, reinterpret_cast<const Raw*>(x), g, tb);
   for (int i = threadIdx.x; i < 3 * (G::NP / 32); i += NT) fa[i] = 0;  // both frontiers, risen bits
-  if (threadIdx.x == 0) cnt[0] = cnt[2] = cnt[3] = 0;  // same-bin pairs; the bin predictors' costs
+  if (threadIdx.x == 0) {
+    cnt[0] = cnt[2] = cnt[3] = 0;  // same-bin pairs; the bin predictors' costs
+    cnt[1] = 0xFFFFFFFFu;          // the tile's smallest key (its top 32 bits)
+  }
   cp_async_wait_all();
   __syncthreads();
   bool bad = false;
@@ -786,6 +789,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   // 1D differences of the thread's points (the Lorenzo stencil's seven lower-octant
   // points are the neighbours -D[0..6] the flags load anyway)
   unsigned cost_l = 0, cost_d = 0;
+  uint32_t tmin = 0xFFFFFFFFu;
   constexpr WordT NBM = (WordT)0xAAAAAAAAAAAAAAAAULL;
 #pragma unroll 1
   for (int j = 0; j < G::SEG; ++j) {
@@ -795,6 +799,11 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
     if (col_in && ly < tb.cy) {
       const B bp = bin[e];
       const K kp = key[e];
+      {
+        const uint64_t biased = (uint64_t)kp ^ (sizeof(K) == 4 ? 0x80000000ull : 0x8000000000000000ull);
+        const uint32_t top = sizeof(K) == 4 ? (uint32_t)biased : (uint32_t)(biased >> 32);
+        tmin = top < tmin ? top : tmin;
+      }
       B nbin[14];
 #pragma unroll
       for (int k = 0; k < 14; ++k) {
@@ -851,13 +860,16 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   {
     const unsigned wsum = __reduce_add_sync(0xffffffffu, same_pairs);
     const unsigned wl = __reduce_add_sync(0xffffffffu, cost_l), wd = __reduce_add_sync(0xffffffffu, cost_d);
+    const unsigned wmin = __reduce_min_sync(0xffffffffu, tmin);
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(&cnt[0], wsum);
       atomicAdd(&cnt[2], wl);
       atomicAdd(&cnt[3], wd);
+      atomicMin(&cnt[1], wmin);
     }
   }
   __syncthreads();  // keys are dead from here on
+  if (threadIdx.x == 0) fi.tkey[tid] = cnt[1];
   // same-bin pairs over the tile's points, against 16ths of the neighbour pairs a full
   // tile has (each pair is seen from both ends)
   const unsigned pairs_full = (unsigned)G::NP * (G::HZ ? 14u : 6u);
@@ -1031,8 +1043,9 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
     const int64_t item = (int64_t)s_item;
     __syncthreads();  // s_item is rewritten for the next item
     if (item >= count) break;
-    const int64_t gt = lst ? (int64_t)lst[item] : tile0 + item;
+    int64_t gt = lst ? (int64_t)lst[item] : tile0 + item;
     const FieldInfo& fi = F[field_of_tile(F, f0, nf, gt)];
+    if (!lst) gt = fi.tile_base + (int64_t)fi.order[gt - fi.tile_base];  // in ascending tile key
     Params* P = fi.P;
     if ((P->status & kErrNonfinite) || P->constant) continue;  // uniform per block
     const Geometry g = fi.g;
@@ -1159,20 +1172,23 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
         if (sv[e + G::off(dz_of(k), dy_of(k), dx_of(k))] >= sf + (k < 7 ? 1u : 0u)) continue;
         const int64_t qz = pz + dz_of(k), qy = py + dy_of(k), qx = px + dx_of(k);
         // a plain byte store: every writer stores the same value
-        reinterpret_cast<volatile uint8_t*>(fi.dirty)[((qz / g.tz) * g.nty + qy / g.ty) * g.ntx + qx / g.tx] = 1;
+        reinterpret_cast<volatile uint8_t*>(fi.dirty)[fi.rank[((qz / g.tz) * g.nty + qy / g.ty) * g.ntx + qx / g.tx]] = 1;
       }
     }
     phase_mark(P, 8, t0);  // the next item's first barrier separates this item's reads from its writes
   }
 }
 
-// Dirty flags -> the next round's list, in table order (one block): per class
-// the count and first position, bits cleared.  The table is sorted by class, so the
-// list is grouped by class.  Counts a round for every field of the table; a field
-// past its round cap drops its dirty tiles and is reported as not converged.
-// field_counts (optional, one per table entry) receives how many tiles each field
-// has in the list: 0 means its subbins are final.  Tells the graph's while-node
-// whether to run another round.
+// Dirty flags -> the next round's list (one block).  Flags are kept per rank (a
+// tile's position in its field's rerun order, ascending tile key), so the list holds
+// the fields in table order and each field's tiles in rerun order: within a round a
+// tile is then usually visited after the lower-valued tiles its constraints come
+// from.  Per class the count and first position, flags cleared.  The table is sorted
+// by class, so the list is grouped by class.  Counts a round for every field of the
+// table; a field past its round cap drops its dirty tiles and is reported as not
+// converged.  field_counts (optional, one per table entry) receives how many tiles
+// each field has in the list: 0 means its subbins are final.  Tells the graph's
+// while-node whether to run another round.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_compact(const FieldInfo* __restrict__ F, int nf, int64_t total_words,
                                                 uint32_t* __restrict__ list, BatchState* B,
@@ -1216,8 +1232,9 @@ __global__ void __launch_bounds__(NT) k_compact(const FieldInfo* __restrict__ F,
       continue;
     }
     const uint32_t bits = bits_of(v);
-    const int64_t t0 = F[k].tile_base + 4 * (w - F[k].word_base);
-    for (uint32_t bb = bits; bb; bb &= bb - 1) list[pos++] = (uint32_t)(t0 + __ffs(bb) - 1);
+    const int64_t r0 = 4 * (w - F[k].word_base);  // the word's first rank
+    for (uint32_t bb = bits; bb; bb &= bb - 1)
+      list[pos++] = (uint32_t)(F[k].tile_base + F[k].order[r0 + __ffs(bb) - 1]);
     const unsigned int c = __popc(bits);
     atomicAdd(&cnt[class_of_geometry(F[k].g)], c);
     if (field_counts) atomicAdd(&field_counts[k], c);
@@ -1235,6 +1252,72 @@ __global__ void __launch_bounds__(NT) k_compact(const FieldInfo* __restrict__ F,
     B->runs += tot;
     B->cap_hit |= (unsigned int)capped;
     if (use_handle) cudaGraphSetConditional(handle, tot ? 1u : 0u);
+  }
+}
+
+// Each field's rerun order: its tiles sorted by tile key (one block per field), by a
+// counting sort over 4096 buckets of the key range (the order inside a bucket is
+// arbitrary: the order only steers how fast rounds converge, never their result),
+// and its inverse.  A field whose pass did not run (constant or non-finite) gets the
+// identity.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_order(const FieldInfo* __restrict__ F) {
+  constexpr int NB = 4096, PER = NB / NT;
+  static_assert(NB % NT == 0, "whole bucket runs per thread");
+  __shared__ unsigned int hist[NB];
+  __shared__ unsigned int tmp[NT / 32 + 1];
+  __shared__ unsigned int red[2][NT / 32];
+  const FieldInfo& fi = F[blockIdx.x];
+  const int64_t n = fi.g.ntiles;
+  uint32_t* __restrict__ order = fi.order;
+  uint32_t* __restrict__ rank = fi.rank;
+  const uint32_t* __restrict__ tkey = fi.tkey;
+  if (fi.P->constant || (fi.P->status & kErrNonfinite)) {
+    for (int64_t t = threadIdx.x; t < n; t += NT) order[t] = rank[t] = (uint32_t)t;
+    return;
+  }
+  uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+  for (int64_t t = threadIdx.x; t < n; t += NT) {
+    const uint32_t k = tkey[t];
+    lo = k < lo ? k : lo;
+    hi = k > hi ? k : hi;
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = lo;
+    red[1][threadIdx.x >> 5] = hi;
+  }
+  for (int i = threadIdx.x; i < NB; i += NT) hist[i] = 0u;
+  __syncthreads();
+  lo = red[0][0];
+  hi = red[1][0];
+  for (int w = 1; w < NT / 32; ++w) {
+    lo = red[0][w] < lo ? red[0][w] : lo;
+    hi = red[1][w] > hi ? red[1][w] : hi;
+  }
+  const uint64_t span = (uint64_t)(hi - lo) + 1u;
+  auto bucket = [&](uint32_t k) { return (unsigned int)(((uint64_t)(k - lo) * NB) / span); };
+  for (int64_t t = threadIdx.x; t < n; t += NT) atomicAdd(&hist[bucket(tkey[t])], 1u);
+  __syncthreads();
+  unsigned int v[PER], sum = 0;
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    v[u] = hist[PER * threadIdx.x + u];
+    sum += v[u];
+  }
+  unsigned int total;
+  unsigned int start = block_exclusive_scan<NT, unsigned int>(sum, tmp, &total);
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    hist[PER * threadIdx.x + u] = start;  // first position of the bucket
+    start += v[u];
+  }
+  __syncthreads();
+  for (int64_t t = threadIdx.x; t < n; t += NT) {
+    const unsigned int r = atomicAdd(&hist[bucket(tkey[t])], 1u);
+    order[r] = (uint32_t)t;
+    rank[t] = r;
   }
 }
 

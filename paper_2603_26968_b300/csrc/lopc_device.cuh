@@ -389,7 +389,10 @@ struct FieldInfo {
   int64_t* bins_out;      // optional export of the bins (may be null)
   uint64_t* size_out;     // device: this field's stream length (may be null)
   int* status_out;        // device: this field's LOPC status (may be null)
-  uint32_t* dirty;        // tiles to rerun next round: one byte flag per tile, ceil(ntiles / 4) words
+  uint32_t* dirty;        // tiles to rerun next round: one byte flag per rank (below), ceil(ntiles / 4) words
+  uint32_t* tkey;         // per tile: the top 32 bits of its smallest value's order key
+  uint32_t* order;        // the tiles in ascending tkey (the order reruns visit them in): rank -> tile
+  uint32_t* rank;         // the inverse: tile -> rank
   int64_t tile_base;      // first tile in the table's tile index space
   int64_t word_base;      // first dirty word in the table's flat word space
   int64_t round_cap;
