@@ -350,13 +350,13 @@ int launch_class_pre(const Table& t, int c, const FieldInfo* dF, int fix, cudaSt
 
 template <typename T, int ND>
 int launch_class_rerun(const Table& t, int c, const FieldInfo* dF, BatchState* dB, const uint32_t* list,
-                       cudaStream_t st) {
+                       uint32_t* app, cudaStream_t st) {
   using C = TileCfg<T, ND>;
   if (!t.cls_nf[c]) return LOPC_OK;
   const unsigned grid = (unsigned)imin64(t.cls_nt[c], rerun_blocks(c));
   LAUNCH(list ? "tile_rerun" : "tile_rerun_all", st,
          k_rerun<T, ND><<<grid, C::NT, RerunSmem<T, ND>::bytes(), st>>>(dF, t.cls_f0[c], t.cls_nf[c], t.cls_t0[c],
-                                                                       t.cls_nt[c], c, dB, list));
+                                                                       t.cls_nt[c], c, dB, list, app));
   CK(cudaGetLastError());
   return LOPC_OK;
 }
@@ -388,13 +388,17 @@ int launch_pre(const Table& t, const FieldInfo* dF, cudaStream_t st, int fix = 1
 }
 
 // One rerun round: of every tile (list == null, the first round) or of the listed ones.
-int launch_reruns(const Table& t, const FieldInfo* dF, BatchState* dB, const uint32_t* list, cudaStream_t st) {
+// app (total_tiles entries, or null: no appends) receives the tiles reruns mark, for
+// the round in progress to take.
+int launch_reruns(const Table& t, const FieldInfo* dF, BatchState* dB, const uint32_t* list, uint32_t* app,
+                  cudaStream_t st) {
   int rc;
   if (!list) CK(cudaMemsetAsync(dB->next_all, 0, sizeof(dB->next_all), st));  // the all-tile round's counters
-  if ((rc = launch_class_rerun<float, 2>(t, 0, dF, dB, list, st))) return rc;
-  if ((rc = launch_class_rerun<float, 3>(t, 1, dF, dB, list, st))) return rc;
-  if ((rc = launch_class_rerun<double, 2>(t, 2, dF, dB, list, st))) return rc;
-  return launch_class_rerun<double, 3>(t, 3, dF, dB, list, st);
+  if (!list && app) CK(cudaMemsetAsync(dB->app, 0, sizeof(dB->app), st));
+  if ((rc = launch_class_rerun<float, 2>(t, 0, dF, dB, list, app, st))) return rc;
+  if ((rc = launch_class_rerun<float, 3>(t, 1, dF, dB, list, app, st))) return rc;
+  if ((rc = launch_class_rerun<double, 2>(t, 2, dF, dB, list, app, st))) return rc;
+  return launch_class_rerun<double, 3>(t, 3, dF, dB, list, app, st);
 }
 
 int launch_compact(const Table& t, FieldInfo* dF, uint32_t* list, BatchState* dB, unsigned int* field_counts,
@@ -427,7 +431,7 @@ struct CompressPlan {
   Table t;
   std::vector<int> order;  // position in the table -> caller's index
   bool worklist = false;   // one field, repaired by the worklist schedule
-  size_t off_state = 0, off_table = 0, off_results = 0, off_list = 0;
+  size_t off_state = 0, off_table = 0, off_results = 0, off_list = 0, off_app = 0;
   size_t off_wl_state = 0, off_stamp = 0, off_wl = 0;
   std::vector<size_t> off_field;
   size_t ws_total = 0;
@@ -456,6 +460,8 @@ int plan_compress(int n, const lopc_field_desc* descs, const void* const* xs, vo
   p.off_results = o;
   o = align256(o + 16);
   p.off_list = o;
+  o = align256(o + 4 * (size_t)p.t.total_tiles);
+  p.off_app = o;
   o = align256(o + 4 * (size_t)p.t.total_tiles);
   p.off_field.resize(n);
   for (int k = 0; k < n; ++k) {
@@ -490,6 +496,7 @@ struct Ptrs {
   FieldInfo* F;
   BatchState* B;
   uint32_t* list;
+  uint32_t* app;
 };
 
 Ptrs ptrs_of(const CompressPlan& p, uint8_t* ws) {
@@ -497,6 +504,7 @@ Ptrs ptrs_of(const CompressPlan& p, uint8_t* ws) {
   q.F = reinterpret_cast<FieldInfo*>(ws + p.off_table);
   q.B = reinterpret_cast<BatchState*>(ws + p.off_state);
   q.list = reinterpret_cast<uint32_t*>(ws + p.off_list);
+  q.app = reinterpret_cast<uint32_t*>(ws + p.off_app);
   return q;
 }
 
@@ -526,14 +534,14 @@ int enqueue_prologue(const CompressPlan& p, const Ptrs& q, cudaStream_t st, cuda
     return launch_wl(p, q, ws, 1, st, h, use_h);
   }
   if ((rc = launch_pre(p.t, q.F, st))) return rc;
-  if ((rc = launch_reruns(p.t, q.F, q.B, nullptr, st))) return rc;
+  if ((rc = launch_reruns(p.t, q.F, q.B, nullptr, q.app, st))) return rc;
   return launch_compact(p.t, q.F, q.list, q.B, nullptr, h, use_h, st);
 }
 
 int enqueue_loop_body(const CompressPlan& p, const Ptrs& q, cudaStream_t st, cudaGraphConditionalHandle h, int use_h) {
   int rc;
   if (p.worklist) return launch_wl(p, q, reinterpret_cast<uint8_t*>(q.B) - p.off_state, 0, st, h, use_h);
-  if ((rc = launch_reruns(p.t, q.F, q.B, q.list, st))) return rc;
+  if ((rc = launch_reruns(p.t, q.F, q.B, q.list, q.app, st))) return rc;
   return launch_compact(p.t, q.F, q.list, q.B, nullptr, h, use_h, st);
 }
 
@@ -926,6 +934,7 @@ struct lopc_engine {
   FieldInfo* hT[3] = {nullptr, nullptr, nullptr};  // their pinned staging copies
   BatchState* dB = nullptr;
   uint32_t* dlist = nullptr;
+  uint32_t* dapp = nullptr;  // tiles the running fields' reruns append to their round
   unsigned int* dcounts = nullptr;
   unsigned int* hcounts = nullptr;  // pinned
   uint64_t* hsize = nullptr;        // pinned and mapped: k_finalize writes each field's result here
@@ -956,6 +965,7 @@ void engine_free(lopc_engine* e) {
   }
   if (e->dB) cudaFree(e->dB);
   if (e->dlist) cudaFree(e->dlist);
+  if (e->dapp) cudaFree(e->dapp);
   if (e->dcounts) cudaFree(e->dcounts);
   if (e->hcounts) cudaFreeHost(e->hcounts);
   if (e->hsize) cudaFreeHost(e->hsize);
@@ -980,6 +990,7 @@ int engine_init(lopc_engine* e) {
   CK(cudaMalloc(&e->dB, sizeof(BatchState)));
   CK(cudaMemset(e->dB, 0, sizeof(BatchState)));
   CK(cudaMalloc(&e->dlist, 4 * (size_t)std::max<int64_t>(1, e->max_tiles)));
+  CK(cudaMalloc(&e->dapp, 4 * (size_t)std::max<int64_t>(1, e->max_tiles)));
   CK(cudaMalloc(&e->dcounts, 4 * (size_t)e->max_fields));
   CK(cudaHostAlloc(&e->hcounts, 4 * (size_t)e->max_fields, cudaHostAllocDefault));
   CK(cudaHostAlloc(&e->hsize, 8 * (size_t)e->max_fields, cudaHostAllocMapped));
@@ -1028,7 +1039,7 @@ int engine_step(lopc_engine* e, int rounds, int* active) {
         CK(cudaMemcpyAsync(e->hcounts, e->dcounts, 4 * (size_t)tr.n(), cudaMemcpyDeviceToHost, e->sm));
         CK(cudaEventRecord(e->ev_counts, e->sm));
       }
-      if ((rc = launch_reruns(tr, e->dT[0], e->dB, e->dlist, e->sm))) return rc;
+      if ((rc = launch_reruns(tr, e->dT[0], e->dB, e->dlist, e->dapp, e->sm))) return rc;
     }
   }
   if (!e->fresh.empty()) {
@@ -1036,7 +1047,9 @@ int engine_step(lopc_engine* e, int rounds, int* active) {
     engine_table(e->fresh, ta);
     if ((rc = engine_upload(e, 1, ta, e->sa))) return rc;
     if ((rc = launch_pre(ta, e->dT[1], e->sa))) return rc;
-    if ((rc = launch_reruns(ta, e->dT[1], e->dB, nullptr, e->sa))) return rc;
+    // no appends here: this round runs beside the running fields' round, which owns
+    // the append counters
+    if ((rc = launch_reruns(ta, e->dT[1], e->dB, nullptr, nullptr, e->sa))) return rc;
     CK(cudaEventRecord(e->ev_pro, e->sa));
     e->pro_pending = true;
   }

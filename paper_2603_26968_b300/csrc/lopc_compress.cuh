@@ -1010,7 +1010,7 @@ struct RerunSmem {
 template <typename T, int ND>
 __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN)
     k_rerun(const FieldInfo* __restrict__ F, int f0, int nf, int64_t tile0, int64_t ntile_cls, int cls,
-            BatchState* __restrict__ B, const uint32_t* __restrict__ list) {
+            BatchState* __restrict__ B, const uint32_t* __restrict__ list, uint32_t* __restrict__ app) {
   using G = TileGeom<T, ND, true>;  // interior rows on 16-byte boundaries
   using RS = RerunSmem<T, ND>;
   constexpr int NT = G::NT;
@@ -1023,12 +1023,18 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
   uint16_t* flist = reinterpret_cast<uint16_t*>(smem + RS::LIST);
   uint32_t* queue = reinterpret_cast<uint32_t*>(smem + RS::QUEUE);
   __shared__ uint32_t qn;
-  __shared__ unsigned s_item;
+  __shared__ unsigned s_item, s_claimed;
+  __shared__ long long s_lim, s_app_gt;
   // the first round (list == nullptr) visits every tile of the class; blocks take
-  // items from a counter, so a slow tile holds up only its own block
+  // items from a counter, so a slow tile holds up only its own block.  Items past the
+  // list are tiles that reruns of this round marked (app, the class's segment of a
+  // table-wide array): a block takes them while any are left and never waits, and a
+  // tile marked after the last block has gone keeps its flag for the next round.
   const int64_t count = list ? (int64_t)B->count[cls] : ntile_cls;
   const uint32_t* lst = list ? list + B->off[cls] : nullptr;
   unsigned* next = list ? &B->next[cls] : &B->next_all[cls];
+  uint32_t* app_seg = app ? app + tile0 : nullptr;
+  volatile unsigned* napp = &B->app[cls];
   // thread 0 takes the following item while the block works on this one, so the
   // counter's latency is hidden
   unsigned ahead = 0;
@@ -1036,18 +1042,50 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
 #pragma unroll 1
   while (true) {
     if (threadIdx.x == 0) {
+      const long long appended = app_seg ? (long long)min(*napp, (unsigned)ntile_cls) : 0ll;
+      const long long lim = (long long)count + appended;
+      long long agt = -1;
+      if ((long long)ahead < lim) {
+        // an appended tile, read once for the block (the entry may not be written yet:
+        // then it is stale and checked below, and the tile itself keeps its flag)
+        if ((long long)ahead >= count) agt = (long long)reinterpret_cast<volatile uint32_t*>(app_seg)[ahead - count];
+      }
       s_item = ahead;
-      if ((int64_t)ahead < count) ahead = atomicAdd(next, 1u);
+      s_lim = lim;
+      s_app_gt = agt;
+      if ((long long)ahead < lim) ahead = atomicAdd(next, 1u);
     }
     __syncthreads();  // also: the last item's shared state is no longer read
     const int64_t item = (int64_t)s_item;
+    const int64_t lim = (int64_t)s_lim;
+    const int64_t agt = (int64_t)s_app_gt;
     __syncthreads();  // s_item is rewritten for the next item
-    if (item >= count) break;
-    int64_t gt = lst ? (int64_t)lst[item] : tile0 + item;
+    if (item >= lim) break;
+    int64_t gt;
+    if (item < count) {
+      gt = lst ? (int64_t)lst[item] : tile0 + item;
+    } else {
+      gt = agt;
+      if (gt < tile0 || gt >= tile0 + ntile_cls) continue;  // uniform per block
+    }
     const FieldInfo& fi = F[field_of_tile(F, f0, nf, gt)];
-    if (!lst) gt = fi.tile_base + (int64_t)fi.order[gt - fi.tile_base];  // in ascending tile key
+    if (!lst && item < count) gt = fi.tile_base + (int64_t)fi.order[gt - fi.tile_base];  // in ascending tile key
     Params* P = fi.P;
     if ((P->status & kErrNonfinite) || P->constant) continue;  // uniform per block
+    if (app_seg) {
+      // claim the tile: clear its flag, so that a mark from now on queues it again; an
+      // appended copy whose flag is already clear was taken by another block
+      if (threadIdx.x == 0) {
+        const uint32_t r = fi.rank[gt - fi.tile_base], sh = 8u * (r & 3u);
+        const uint32_t old = atomicAnd(&fi.dirty[r >> 2], ~(0xFFu << sh));
+        __threadfence();  // a marker's raised subbins, fenced before its flag, are read after this
+        s_claimed = (old >> sh) & 0xFFu;
+      }
+      __syncthreads();
+      const bool claimed = s_claimed != 0u;
+      __syncthreads();
+      if (item >= count && !claimed) continue;
+    }
     const Geometry g = fi.g;
     uint32_t* __restrict__ s_glob = fi.s;
     const uint32_t* __restrict__ cm_glob = fi.cm;
@@ -1136,14 +1174,17 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
     }
     block_add2(evals, raises, &P->work[2]);
     phase_mark(P, 6, t0);
-    // write the subbins that rose; queue the risen boundary points
+    // write the subbins that rose; queue the risen boundary points.  With appended
+    // tiles two blocks can hold the same tile at once, each from its own snapshot: the
+    // write takes the larger value, and the elementwise max of two tile-local
+    // fixpoints is again one (each is a lower bound of the least fixpoint)
     const int64_t gz = tb.z0 + sp.lz, gx = tb.x0 + sp.lx;
     if (col_in && risen) {
 #pragma unroll 1
       for (int j = 0; j < G::SEG; ++j) {
         if (!((risen >> j) & 1u)) continue;
         const int ly = sp.ly0 + j;
-        s_glob[gz * plane + (tb.y0 + ly) * g.nx + gx] = sv[sp.e0 + j * G::BXP];
+        atomicMax(&s_glob[gz * plane + (tb.y0 + ly) * g.nx + gx], sv[sp.e0 + j * G::BXP]);
         if (out_of_box_bits<G>(sp.lz, ly, sp.lx)) {
           const uint32_t slot = atomicAdd(&qn, 1u);
           if (slot < (uint32_t)RS::QMAX) queue[slot] = ((uint32_t)sp.lz << 20) | ((uint32_t)ly << 10) | (uint32_t)sp.lx;
@@ -1156,6 +1197,8 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
     // holds.  q's subbin is read from the halo loaded at the start: it can only have
     // risen since, so a tile is sometimes marked when it need not be (its rerun then
     // finds every constraint held) but never missed.
+    __threadfence();  // the raised subbins are visible before any tile is marked
+    __syncthreads();
     const uint32_t nq = min(qn, (uint32_t)RS::QMAX);
     for (uint32_t qi = threadIdx.x; qi < nq; qi += NT) {
       const uint32_t v = queue[qi];
@@ -1171,8 +1214,20 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
         if (!((up >> k) & 1u)) continue;
         if (sv[e + G::off(dz_of(k), dy_of(k), dx_of(k))] >= sf + (k < 7 ? 1u : 0u)) continue;
         const int64_t qz = pz + dz_of(k), qy = py + dy_of(k), qx = px + dx_of(k);
-        // a plain byte store: every writer stores the same value
-        reinterpret_cast<volatile uint8_t*>(fi.dirty)[fi.rank[((qz / g.tz) * g.nty + qy / g.ty) * g.ntx + qx / g.tx]] = 1;
+        const int64_t tq = ((qz / g.tz) * g.nty + qy / g.ty) * g.ntx + qx / g.tx;
+        const uint32_t r = fi.rank[tq];
+        if (!app_seg) {
+          // a plain byte store: every writer stores the same value
+          reinterpret_cast<volatile uint8_t*>(fi.dirty)[r] = 1;
+        } else {
+          // newly dirty: also offer the tile to this round
+          const uint32_t sh = 8u * (r & 3u);
+          const uint32_t old = atomicOr(&fi.dirty[r >> 2], 1u << sh);
+          if (!((old >> sh) & 0xFFu)) {
+            const unsigned pos = atomicAdd(&B->app[cls], 1u);
+            if ((int64_t)pos < ntile_cls) app_seg[pos] = (uint32_t)(fi.tile_base + tq);
+          }
+        }
       }
     }
     phase_mark(P, 8, t0);  // the next item's first barrier separates this item's reads from its writes
@@ -1246,6 +1301,7 @@ __global__ void __launch_bounds__(NT) k_compact(const FieldInfo* __restrict__ F,
       B->count[c] = cnt[c];
       B->off[c] = o;
       B->next[c] = 0;
+      B->app[c] = 0;
       o += cnt[c];
     }
     B->rounds += 1;

@@ -411,6 +411,7 @@ struct BatchState {
   unsigned int off[4];        // their first position in the list
   unsigned int next[4];       // per class: the next listed item a rerun block takes
   unsigned int next_all[4];   // per class: the next tile of the all-tile round
+  unsigned int app[4];        // per class: tiles reruns appended to the round in progress
   unsigned long long rounds;  // repair rounds done
   unsigned long long runs;    // tile runs launched (first round included)
   unsigned int cap_hit;
