@@ -38,7 +38,7 @@ METRIC = "compress/decompress GB/s (1 B300, bit-exact) & % HBM peak; batched vs 
 # DRAM bytes (read + write) of one tile-pass launch on the headline workload (512^3
 # f32, NOA 1e-3), from the ncu capture in profiles/launches_3d_f32_512_noa1e-3.md;
 # None whenever k_pass has changed since it was captured.
-PASS_TRAFFIC = 543187200 + 1071419136
+PASS_TRAFFIC = 543233792 + 1071651584
 
 
 def peaks():
