@@ -294,25 +294,31 @@ cudaStream_t side_stream() {
 
 template <typename T, int ND>
 int set_smem_attrs() {
-  static bool done = false;  // per instantiation; attributes are per function and device-wide
-  if (done) return LOPC_OK;
+  // per instantiation and thread: one bit per device (attributes are per function and device)
+  thread_local uint64_t done = 0;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done & bit) return LOPC_OK;
   CK(cudaFuncSetAttribute(k_pass<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassSmem<T, ND>::bytes()));
   CK(cudaFuncSetAttribute(k_rerun<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RerunSmem<T, ND>::bytes()));
   CK(cudaFuncSetAttribute(k_encode_sub<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EncSmem<T, ND>::bytes()));
   CK(cudaFuncSetAttribute(k_decode<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DecSmem<T, ND>::bytes()));
-  done = true;
+  done |= bit;
   return LOPC_OK;
 }
 
 int sm_count() {
-  thread_local int v = 0;
-  if (!v) {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
+  thread_local int v[64] = {};  // per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int& c = v[dev & 63];
+  if (!c) {
+    int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    v = sms;
+    c = sms;
   }
-  return v;
+  return c;
 }
 
 // Persistent rerun blocks per SM, per class (set by lopc_tune_set).
@@ -1109,7 +1115,10 @@ int launch_verify(const Geometry& g, const void* d_x, const void* d_y, uint8_t* 
                   const VerifyLayout& L, int64_t& nparts, cudaStream_t st) {
   using VS = VerifySmem<T, ND>;
   constexpr int NT = TileCfg<T, ND>::NT;
-  static int per_sm = 0;  // resident blocks per SM (per instantiation, device-wide)
+  thread_local int per_sm_dev[64] = {};  // resident blocks per SM, per instantiation and device
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  int& per_sm = per_sm_dev[dev & 63];
   if (!per_sm) {
     CK(cudaFuncSetAttribute(k_verify<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)VS::bytes()));
     int occ = 0;
