@@ -581,71 +581,105 @@ __device__ __forceinline__ int topo_fixpoint(uint32_t* sv, const uint32_t* cml, 
     for (unsigned m = readym; m; m &= m - 1) la[base++] = (uint16_t)(4 * o4 + __ffs(m) - 1);
   }
   __syncthreads();
+  // one warp's share of a wave: item i of the ready list `lin_` (n items); the points
+  // it makes ready go to `lout` (counter `cout`), appended by the warp as a whole
+  auto step = [&](unsigned i, unsigned n, const uint16_t* lin_, uint16_t* lout, unsigned* cout) {
+    unsigned readym = 0;
+    int o = 0;
+    uint32_t m = 0;
+    if (i < n) {
+      o = lin_[i];
+      int lz, ly, lx;
+      point_of_lin<G>(o, lz, ly, lx);
+      const int e = G::entry(lz, ly, lx);
+      m = cml[o];
+      const uint32_t before = sv[e];
+      uint32_t best = before;
+#pragma unroll
+      for (int k = 0; k < 14; ++k) {
+        if (!G::HZ && dz_of(k) != 0) continue;
+        if (m & (1u << k)) {
+          const uint32_t cand = sv[e + G::off(dz_of(k), dy_of(k), dx_of(k))] + (k >= 7 ? 1u : 0u);
+          best = cand > best ? cand : best;
+        }
+      }
+      if (best != before) {
+        ++raises;
+        sv[e] = best;
+        if (rb) atomicOr(&rb[o >> 5], 1u << (o & 31));
+      }
+      ++evals;
+      // release the in-tile upper neighbours; record those this point made ready
+      const uint32_t um = SAME ? ((m >> 16) & ~m & ~out_of_box_bits<G>(lz, ly, lx)) : (m >> 16);
+#pragma unroll
+      for (int k = 0; k < 14; ++k) {
+        if (!G::HZ && dz_of(k) != 0) continue;
+        if (um & (1u << k)) {
+          const int q = o + G::loff(dz_of(k), dy_of(k), dx_of(k));
+          const uint32_t sh = 8u * (uint32_t)(q & 3);
+          const uint32_t old = atomicSub(&indeg[q >> 2], 1u << sh);
+          if (((old >> sh) & 0xFFu) == 1u) readym |= 1u << k;
+        }
+      }
+    }
+    const unsigned r = __popc(readym);
+    unsigned incl = r;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += y;
+    }
+    const unsigned wt = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned base = 0;
+    if (lane == 31 && wt) base = atomicAdd(cout, wt);
+    base = __shfl_sync(0xffffffffu, base, 31) + incl - r;
+#pragma unroll
+    for (int k = 0; k < 14; ++k) {
+      if (!G::HZ && dz_of(k) != 0) continue;
+      if (readym & (1u << k)) lout[base++] = (uint16_t)(o + G::loff(dz_of(k), dy_of(k), dx_of(k)));
+    }
+  };
+  constexpr unsigned kTail = 32, kBack = 64;  // warp 0 alone below kTail ready points, until above kBack
   unsigned n = cnt[0];
   int cur = 0;
   int wave = 0;
   while (n) {
+    if (n <= kTail) {
+      // the thin waves: warp 0 alone, with warp barriers; the same list protocol
+      // (input count in cnt[cur], output counter cnt[cur ^ 1] clear)
+      if (threadIdx.x < 32) {
+        unsigned wn = n;
+        int wcur = cur, wwave = wave;
+        while (wn && wn <= kBack) {
+          ++wwave;
+          const uint16_t* lin_ = wcur ? lb : la;
+          uint16_t* lout = wcur ? la : lb;
+          unsigned* cout = &cnt[wcur ^ 1];
+          for (unsigned b0 = 0; b0 < wn; b0 += 32) step(b0 + lane, wn, lin_, lout, cout);
+          __syncwarp();
+          wn = *reinterpret_cast<volatile unsigned*>(cout);
+          __syncwarp();
+          if (lane == 0) cnt[wcur] = 0;
+          wcur ^= 1;
+          __syncwarp();
+        }
+        if (lane == 0) {
+          cnt[2] = wn;
+          cnt[3] = (unsigned)wcur | ((unsigned)wwave << 1);
+        }
+      }
+      __syncthreads();
+      n = cnt[2];
+      cur = (int)(cnt[3] & 1u);
+      wave = (int)(cnt[3] >> 1);
+      __syncthreads();
+      continue;
+    }
     ++wave;
     const uint16_t* lin_ = cur ? lb : la;
     uint16_t* lout = cur ? la : lb;
     unsigned* cout = &cnt[cur ^ 1];
-    for (unsigned b0 = 0; b0 < n; b0 += NT) {  // uniform trip count: every lane takes part in the scans
-      const unsigned i = b0 + threadIdx.x;
-      unsigned readym = 0;
-      int o = 0;
-      uint32_t m = 0;
-      if (i < n) {
-        o = lin_[i];
-        int lz, ly, lx;
-        point_of_lin<G>(o, lz, ly, lx);
-        const int e = G::entry(lz, ly, lx);
-        m = cml[o];
-        const uint32_t before = sv[e];
-        uint32_t best = before;
-#pragma unroll
-        for (int k = 0; k < 14; ++k) {
-          if (!G::HZ && dz_of(k) != 0) continue;
-          if (m & (1u << k)) {
-            const uint32_t cand = sv[e + G::off(dz_of(k), dy_of(k), dx_of(k))] + (k >= 7 ? 1u : 0u);
-            best = cand > best ? cand : best;
-          }
-        }
-        if (best != before) {
-          ++raises;
-          sv[e] = best;
-          if (rb) atomicOr(&rb[o >> 5], 1u << (o & 31));
-        }
-        ++evals;
-        // release the in-tile upper neighbours; record those this point made ready
-        const uint32_t um = SAME ? ((m >> 16) & ~m & ~out_of_box_bits<G>(lz, ly, lx)) : (m >> 16);
-#pragma unroll
-        for (int k = 0; k < 14; ++k) {
-          if (!G::HZ && dz_of(k) != 0) continue;
-          if (um & (1u << k)) {
-            const int q = o + G::loff(dz_of(k), dy_of(k), dx_of(k));
-            const uint32_t sh = 8u * (uint32_t)(q & 3);
-            const uint32_t old = atomicSub(&indeg[q >> 2], 1u << sh);
-            if (((old >> sh) & 0xFFu) == 1u) readym |= 1u << k;
-          }
-        }
-      }
-      const unsigned r = __popc(readym);
-      unsigned incl = r;
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += y;
-      }
-      const unsigned wt = __shfl_sync(0xffffffffu, incl, 31);
-      unsigned base = 0;
-      if (lane == 31 && wt) base = atomicAdd(cout, wt);
-      base = __shfl_sync(0xffffffffu, base, 31) + incl - r;
-#pragma unroll
-      for (int k = 0; k < 14; ++k) {
-        if (!G::HZ && dz_of(k) != 0) continue;
-        if (readym & (1u << k)) lout[base++] = (uint16_t)(o + G::loff(dz_of(k), dy_of(k), dx_of(k)));
-      }
-    }
+    for (unsigned b0 = 0; b0 < n; b0 += NT) step(b0 + threadIdx.x, n, lin_, lout, cout);  // uniform trip count
     __syncthreads();
     n = *cout;
     if (threadIdx.x == 0) cnt[cur] = 0;  // the counter of the wave after next
