@@ -259,8 +259,9 @@ LOPC_API int lopc_last_round_tiles(int64_t* out, int n);
 /* Measurement aid: work of the tile-local fixpoint in the last compression on this
  * thread: point evaluations and subbin raises in the tile pass, then the same in
  * the reruns, then the rerun tiles loaded and how many of them found every
- * constraint into the tile holding (check only).  Copies min(n, 6) values and
- * returns 6. */
+ * constraint into the tile holding (check only), then 1 if the tile pass took the
+ * tiles in tile-key order (lopc_tune_set_pass_order), else 0.  Copies min(n, 7)
+ * values and returns 7. */
 LOPC_API int lopc_last_fixpoint_work(int64_t* out, int n);
 
 /* Measurement aid: while enabled, the decoder adds up SM cycles per phase over all
@@ -345,6 +346,16 @@ LOPC_API void lopc_tune_set_budget(const int* sixteenths);
 LOPC_API void lopc_tune_get_budget(int* sixteenths);
 LOPC_API void lopc_tune_set_dense(const int* sixteenths);
 LOPC_API void lopc_tune_get_dense(int* sixteenths);
+
+/* Order in which the tile pass takes a field's tiles, per field class; later calls on
+ * this thread use it and output bytes never depend on it.  0 (default): by the field,
+ * as in 2 when the bins its tiles' samples span (each tile clamped at 256) average
+ * below 48, else as in 1.  1: tile index order, each tile's fixpoint starting from
+ * halo subbins 0.  2: ascending tile key (the rerun order), each tile's fixpoint
+ * starting from the subbins its earlier neighbour tiles have written.  Clamped to
+ * [0, 2]. */
+LOPC_API void lopc_tune_set_pass_order(const int* modes);
+LOPC_API void lopc_tune_get_pass_order(int* modes);
 
 /* Human-readable text of a status code (static storage). */
 LOPC_API const char* lopc_strerror(int status);

@@ -100,7 +100,7 @@ thread_local Profiler g_prof;
   } while (0)
 thread_local int64_t g_last_rounds = 0, g_last_tile_runs = 0, g_last_fix_iters = 0, g_last_fix_iters_max = 0;
 thread_local int64_t g_last_phase[9] = {};
-thread_local int64_t g_last_work[6] = {};
+thread_local int64_t g_last_work[7] = {};
 thread_local std::vector<int64_t> g_round_tiles;  // tiles listed per round (host-driven loop only)
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -329,6 +329,9 @@ thread_local int g_pass_budget16[4] = {64, 64, 64, 64};
 // Same-bin neighbour pairs, in sixteenths of a full tile's pairs, above which a tile
 // pass goes straight to the topological order (set by lopc_tune_set_dense; 17 = never).
 thread_local int g_pass_dense16[4] = {8, 8, 8, 8};
+// Order of the tile pass, per class: 0 by the field's sample span, 1 tile index, 2 tile
+// key (set by lopc_tune_set_pass_order).
+thread_local int g_pass_order[4] = {0, 0, 0, 0};
 
 int rerun_blocks(int c) { return sm_count() * g_rerun_per_sm[c]; }
 
@@ -339,14 +342,24 @@ int launch_init(const Table& t, const FieldInfo* dF, cudaStream_t st) {
   return LOPC_OK;
 }
 
+// Range, eps and tile keys of one class's fields.
 template <typename T, int ND>
-int launch_class_pre(const Table& t, int c, const FieldInfo* dF, int fix, cudaStream_t st) {
-  using C = TileCfg<T, ND>;
+int launch_class_range(const Table& t, int c, const FieldInfo* dF, cudaStream_t st) {
   if (!t.cls_nf[c]) return LOPC_OK;
   int rc = set_smem_attrs<T, ND>();
   if (rc) return rc;
   LAUNCH("range", st, k_range<T><<<dim3(sm_count() * 4, t.cls_nf[c]), 256, 0, st>>>(dF, t.cls_f0[c]));
   LAUNCH("resolve_eps", st, k_resolve_eps<T><<<(t.cls_nf[c] + 63) / 64, 64, 0, st>>>(dF, t.cls_f0[c], t.cls_nf[c]));
+  LAUNCH("tile_keys", st, k_tile_keys<T, ND><<<(unsigned)t.cls_nt[c], 64, 0, st>>>(dF, t.cls_f0[c], t.cls_nf[c], t.cls_t0[c]));
+  CK(cudaGetLastError());
+  return LOPC_OK;
+}
+
+// The tile pass of one class's fields.
+template <typename T, int ND>
+int launch_class_pre(const Table& t, int c, const FieldInfo* dF, int fix, cudaStream_t st) {
+  using C = TileCfg<T, ND>;
+  if (!t.cls_nf[c]) return LOPC_OK;
   LAUNCH("tile_pass", st,
          k_pass<T, ND><<<(unsigned)t.cls_nt[c], C::NT, PassSmem<T, ND>::bytes(), st>>>(
              dF, t.cls_f0[c], t.cls_nf[c], t.cls_t0[c], (unsigned)g_pass_budget16[c], (unsigned)g_pass_dense16[c], fix));
@@ -378,19 +391,26 @@ int launch_class_encode(const Table& t, int c, const FieldInfo* dF, cudaStream_t
   return LOPC_OK;
 }
 
-// State reset, range, eps and the tile pass of every field of the table (fix = 0:
-// the pass leaves every subbin at 0, for the worklist schedule).
+// State reset, range, eps, tile keys and order, cleared subbins (ordered passes only)
+// and the tile pass of every field of the table (fix = 0: the pass leaves every subbin
+// at 0, for the worklist schedule).  The reruns visit each field's tiles in ascending
+// tile key, and so does the pass of a field whose tiles span few bins.
 int launch_pre(const Table& t, const FieldInfo* dF, cudaStream_t st, int fix = 1) {
   int rc;
   if ((rc = launch_init(t, dF, st))) return rc;
+  if ((rc = launch_class_range<float, 2>(t, 0, dF, st))) return rc;
+  if ((rc = launch_class_range<float, 3>(t, 1, dF, st))) return rc;
+  if ((rc = launch_class_range<double, 2>(t, 2, dF, st))) return rc;
+  if ((rc = launch_class_range<double, 3>(t, 3, dF, st))) return rc;
+  unsigned pass_order = 0;
+  for (int c = 0; c < 4; ++c) pass_order |= (unsigned)g_pass_order[c] << (2 * c);
+  LAUNCH("order", st, k_order<1024><<<t.n(), 1024, 0, st>>>(dF, pass_order));
+  LAUNCH("clear_subbins", st, k_clear_subbins<<<dim3(sm_count() * 2, t.n()), 256, 0, st>>>(dF));
+  CK(cudaGetLastError());
   if ((rc = launch_class_pre<float, 2>(t, 0, dF, fix, st))) return rc;
   if ((rc = launch_class_pre<float, 3>(t, 1, dF, fix, st))) return rc;
   if ((rc = launch_class_pre<double, 2>(t, 2, dF, fix, st))) return rc;
-  if ((rc = launch_class_pre<double, 3>(t, 3, dF, fix, st))) return rc;
-  // each field's tiles in ascending smallest value: reruns visit them in that order
-  LAUNCH("order", st, k_order<1024><<<t.n(), 1024, 0, st>>>(dF));
-  CK(cudaGetLastError());
-  return LOPC_OK;
+  return launch_class_pre<double, 3>(t, 3, dF, fix, st);
 }
 
 // One rerun round: of every tile (list == null, the first round) or of the listed ones.
@@ -667,7 +687,8 @@ std::vector<uint64_t> plan_key(const CompressPlan& p, const uint8_t* ws) {
   k.push_back((uint64_t)(uintptr_t)ws);
   k.push_back((uint64_t)p.t.n() | ((uint64_t)p.worklist << 32));
   for (int c = 0; c < 4; ++c)
-    k.push_back((uint64_t)rerun_blocks(c) | ((uint64_t)g_pass_budget16[c] << 20) | ((uint64_t)g_pass_dense16[c] << 40));
+    k.push_back((uint64_t)rerun_blocks(c) | ((uint64_t)g_pass_budget16[c] << 20) | ((uint64_t)g_pass_dense16[c] << 40) |
+                ((uint64_t)g_pass_order[c] << 56));
   for (const FieldInfo& f : p.t.F) {
     const uint64_t* w = reinterpret_cast<const uint64_t*>(&f);
     for (size_t i = 0; i < sizeof(FieldInfo) / 8; ++i) k.push_back(w[i]);
@@ -731,6 +752,7 @@ int compress_one(const lopc_field_desc* d, const void* d_x, void* d_out, size_t 
   g_last_fix_iters_max = (int64_t)hp.fix_iters_max;
   for (int k = 0; k < 9; ++k) g_last_phase[k] = (int64_t)hp.phase[k];
   for (int k = 0; k < 6; ++k) g_last_work[k] = (int64_t)hp.work[k];
+  g_last_work[6] = (int64_t)hp.pass_ordered;
   // the repair ran even if the output was too small: report the repair's status first
   if (res.status == LOPC_ERR_CAPACITY && subbins_out) res.status = LOPC_OK;
   if (res.status) return res.status;
@@ -1384,8 +1406,8 @@ int lopc_last_round_tiles(int64_t* out, int n) {
 }
 
 int lopc_last_fixpoint_work(int64_t* out, int n) {
-  for (int k = 0; k < n && k < 6; ++k) out[k] = g_last_work[k];
-  return 6;
+  for (int k = 0; k < n && k < 7; ++k) out[k] = g_last_work[k];
+  return 7;
 }
 
 void lopc_profile_enable(int on) {
@@ -1464,6 +1486,16 @@ void lopc_tune_set_dense(const int* v) {
 void lopc_tune_get_dense(int* v) {
   if (!v) return;
   for (int c = 0; c < 4; ++c) v[c] = g_pass_dense16[c];
+}
+
+void lopc_tune_set_pass_order(const int* v) {
+  if (!v) return;
+  for (int c = 0; c < 4; ++c) g_pass_order[c] = v[c] < 0 ? 0 : (v[c] > 2 ? 2 : v[c]);
+}
+
+void lopc_tune_get_pass_order(int* v) {
+  if (!v) return;
+  for (int c = 0; c < 4; ++c) v[c] = g_pass_order[c];
 }
 
 // ------------------------------------------------------------ serving engine ABI

@@ -46,6 +46,7 @@ __global__ void k_init_params(const FieldInfo* F, int nf) {
   P->mode = F[f].hdr.mode;
   P->status = 0;
   P->constant = 0;
+  P->pass_ordered = 0;
   P->total = 0;
   P->rounds = 0;
   P->fix_iters = 0;
@@ -726,9 +727,14 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   using B = typename Traits<T>::Bin;
   using WordT = typename Traits<T>::Bits;
   constexpr int NT = G::NT, W = Traits<T>::W;
-  const int64_t gt = tile0 + blockIdx.x;
-  const FieldInfo& fi = F[field_of_tile(F, f0, nf, gt)];
+  const int64_t gt0 = tile0 + blockIdx.x;
+  const FieldInfo& fi = F[field_of_tile(F, f0, nf, gt0)];
   Params* P = fi.P;
+  // in an ordered pass the blocks take the field's tiles in ascending tile key, so that a
+  // tile's lower-valued neighbours, whose subbins its halo reads, have usually been
+  // passed already; otherwise in index order, with halo subbins 0
+  const bool ordered = P->pass_ordered != 0;
+  const int64_t gt = ordered ? fi.tile_base + (int64_t)fi.order[gt0 - fi.tile_base] : gt0;
   if (P->status & kErrNonfinite) return;
   if (P->constant) return;
   const Geometry g = fi.g;
@@ -771,10 +777,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   constexpr int NBOX = G::BZ * G::BY * G::BX;  // entries of the box (the rare error path walks them)
   load_box_async<G, Raw>(raw, reinterpret_cast<const Raw*>(x), g, tb);
   for (int i = threadIdx.x; i < 3 * (G::NP / 32); i += NT) fa[i] = 0;  // both frontiers, risen bits
-  if (threadIdx.x == 0) {
-    cnt[0] = cnt[2] = cnt[3] = 0;  // same-bin pairs; the bin predictors' costs
-    cnt[1] = 0xFFFFFFFFu;          // the tile's smallest key (its top 32 bits)
-  }
+  if (threadIdx.x == 0) cnt[0] = cnt[2] = cnt[3] = 0;  // same-bin pairs; the bin predictors' costs
   cp_async_wait_all();
   __syncthreads();
   bool bad = false;
@@ -823,7 +826,6 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   // 1D differences of the thread's points (the Lorenzo stencil's seven lower-octant
   // points are the neighbours -D[0..6] the flags load anyway)
   unsigned cost_l = 0, cost_d = 0;
-  uint32_t tmin = 0xFFFFFFFFu;
   constexpr WordT NBM = (WordT)0xAAAAAAAAAAAAAAAAULL;
 #pragma unroll 1
   for (int j = 0; j < G::SEG; ++j) {
@@ -833,11 +835,6 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
     if (col_in && ly < tb.cy) {
       const B bp = bin[e];
       const K kp = key[e];
-      {
-        const uint64_t biased = (uint64_t)kp ^ (sizeof(K) == 4 ? 0x80000000ull : 0x8000000000000000ull);
-        const uint32_t top = sizeof(K) == 4 ? (uint32_t)biased : (uint32_t)(biased >> 32);
-        tmin = top < tmin ? top : tmin;
-      }
       B nbin[14];
 #pragma unroll
       for (int k = 0; k < 14; ++k) {
@@ -877,9 +874,12 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
     cml[o] = lo | (up << 16);
     // the global copy (for reruns) keeps the lower and all the same-bin bits
     if (col_in && ly < tb.cy) cm_glob[gz * plane + (tb.y0 + ly) * g.nx + gx] = lo | (same << 16);
-    // first-frontier bits (all subbins are 0, so only a point with a +1 constraint can
-    // rise first), one ballot per warp: a row of lanes holds consecutive points
-    const uint32_t bal = __ballot_sync(0xffffffffu, (lo >> 7) != 0);
+    // first-frontier bits: the tile's own subbins start at 0, so a point can rise first
+    // only through a +1 constraint or, in an ordered pass, a lower neighbour outside the
+    // tile (whose subbin the halo holds); one ballot per warp: a row of lanes holds
+    // consecutive points
+    const uint32_t bal = __ballot_sync(
+        0xffffffffu, (lo >> 7) != 0 || (ordered && (lo & out_of_box_bits<G>(sp.lz, ly, sp.lx)) != 0));
     if (G::TX >= 32) {
       if ((threadIdx.x & 31) == 0 && bal) atomicOr(&fa[o >> 5], bal);
     } else if ((threadIdx.x & 15) == 0) {
@@ -894,16 +894,13 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   {
     const unsigned wsum = __reduce_add_sync(0xffffffffu, same_pairs);
     const unsigned wl = __reduce_add_sync(0xffffffffu, cost_l), wd = __reduce_add_sync(0xffffffffu, cost_d);
-    const unsigned wmin = __reduce_min_sync(0xffffffffu, tmin);
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(&cnt[0], wsum);
       atomicAdd(&cnt[2], wl);
       atomicAdd(&cnt[3], wd);
-      atomicMin(&cnt[1], wmin);
     }
   }
   __syncthreads();  // keys are dead from here on
-  if (threadIdx.x == 0) fi.tkey[tid] = cnt[1];
   // same-bin pairs over the tile's points, against 16ths of the neighbour pairs a full
   // tile has (each pair is seen from both ends)
   const unsigned pairs_full = (unsigned)G::NP * (G::HZ ? 14u : 6u);
@@ -980,9 +977,62 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   __syncthreads();  // bins, planes and the staged record are dead from here on
   phase_mark(P, 4, t0);
 
-  // 4. tile-local least fixpoint, halo subbins 0
+  // 4. tile-local least fixpoint from subbins 0 on the tile and, on the halo of an
+  //    ordered pass, the subbins neighbours have written so far (cleared before the
+  //    pass; any value read is a lower bound, so the result is one too)
   for (int e = threadIdx.x; e < G::E; e += NT) sv[e] = 0;
   __syncthreads();
+  if (fix && ordered) {
+    // only neighbour tiles passed before this one (lower rank) have written subbins
+    __shared__ uint32_t earlier;  // bit (dz+1)*9 + (dy+1)*3 + (dx+1) per neighbour tile
+    if (threadIdx.x == 0) earlier = 0u;
+    __syncthreads();
+    const int64_t tz = tid / (g.ntx * g.nty), ty = (tid / g.ntx) % g.nty, tx = tid % g.ntx;
+    const uint32_t my_rank = gt0 - fi.tile_base;
+    if (threadIdx.x < 27) {
+      const int dz = threadIdx.x / 9 - 1, dy = (threadIdx.x / 3) % 3 - 1, dx = threadIdx.x % 3 - 1;
+      const int64_t nz_ = tz + dz, ny_ = ty + dy, nx_ = tx + dx;
+      if ((dz | dy | dx) != 0 && (G::HZ || dz == 0) && nz_ >= 0 && nz_ < g.ntz && ny_ >= 0 && ny_ < g.nty &&
+          nx_ >= 0 && nx_ < g.ntx && fi.rank[(nz_ * g.nty + ny_) * g.ntx + nx_] < my_rank)
+        atomicOr(&earlier, 1u << threadIdx.x);
+    }
+    __syncthreads();
+    const uint32_t ebits = earlier;
+    auto tile_bit = [](int lz, int ly, int lx) {  // which neighbour tile a halo entry lies in
+      const int dz = lz < 0 ? -1 : lz >= G::TZ ? 1 : 0, dy = ly < 0 ? -1 : ly >= G::TY ? 1 : 0;
+      const int dx = lx < 0 ? -1 : lx >= G::TX ? 1 : 0;
+      return 1u << ((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
+    };
+    if (ebits) {
+      constexpr int NZF = G::HZ ? 2 * G::BY * G::BX : 0;  // z faces (whole planes)
+      constexpr int NYF = 2 * G::TZ * G::BX;              // y faces of the tile's planes
+      constexpr int NXF = 2 * G::TZ * G::TY;              // x faces of the tile's rows
+      for (int i = threadIdx.x; i < NZF + NYF + NXF; i += NT) {
+        int lz, ly, lx;
+        if (i < NZF) {
+          const int r = i % (G::BY * G::BX);
+          lz = i < G::BY * G::BX ? -1 : G::TZ;
+          ly = r / G::BX - 1;
+          lx = r % G::BX - 1;
+        } else if (i < NZF + NYF) {
+          const int jj = i - NZF, r = jj % (G::TZ * G::BX);
+          lz = r / G::BX;
+          ly = jj < G::TZ * G::BX ? -1 : G::TY;
+          lx = r % G::BX - 1;
+        } else {
+          const int jj = i - NZF - NYF, r = jj % (G::TZ * G::TY);
+          lz = r / G::TY;
+          ly = r % G::TY;
+          lx = jj < G::TZ * G::TY ? -1 : G::TX;
+        }
+        if (!(ebits & tile_bit(lz, ly, lx))) continue;  // a later tile: its subbins are still 0
+        const int64_t qz = tb.z0 + lz, qy = tb.y0 + ly, qx = tb.x0 + lx;
+        if (qz >= 0 && qz < g.nz && qy >= 0 && qy < g.ny && qx >= 0 && qx < g.nx)
+          sv[G::entry(lz, ly, lx)] = __ldcg(&s_glob[qz * plane + qy * g.nx + qx]);
+      }
+    }
+    __syncthreads();
+  }
   // frontier sweeps (cheaper while chains are short), and for a tile whose chains
   // outlast the evaluation budget (budget16 / 16 evaluations per point) the
   // topological order, which evaluates each point once, from the values reached so
@@ -1345,13 +1395,73 @@ __global__ void __launch_bounds__(NT) k_compact(const FieldInfo* __restrict__ F,
   }
 }
 
-// Each field's rerun order: its tiles sorted by tile key (one block per field), by a
-// counting sort over 4096 buckets of the key range (the order inside a bucket is
-// arbitrary: the order only steers how fast rounds converge, never their result),
-// and its inverse.  A field whose pass did not run (constant or non-finite) gets the
-// identity.
+// Tile keys for the rerun order: the top 32 bits of the smallest order key among 64
+// sample points of the tile (a 4 x 4 x 4 grid over the clipped tile, 8 x 8 in 2D); one
+// block of 64 threads per tile.  Only an approximate value order is needed.  The block
+// also measures how many bins the samples span, (max - min) * inv clamped to
+// kSpanClamp bins, in sixteenths of a bin, and leaves it in rank[tile] for k_order.
+constexpr unsigned kSpanClamp = 256;
+template <typename T, int ND>
+__global__ void __launch_bounds__(64) k_tile_keys(const FieldInfo* __restrict__ F, int f0, int nf, int64_t tile0) {
+  using K = typename Traits<T>::Key;
+  __shared__ uint32_t wmin[2], wmax[2];
+  const int64_t gt = tile0 + blockIdx.x;
+  const FieldInfo& fi = F[field_of_tile(F, f0, nf, gt)];
+  const int64_t tid = gt - fi.tile_base;
+  const Geometry g = fi.g;
+  if (tid < 0 || tid >= g.ntiles) return;  // never for a consistent plan
+  const TileBox tb = tile_box(g, tid);
+  const int t = threadIdx.x;
+  int lz, ly, lx;
+  if (ND == 3) {
+    lz = (t >> 4) * (tb.cz - 1) / 3;
+    ly = ((t >> 2) & 3) * (tb.cy - 1) / 3;
+    lx = (t & 3) * (tb.cx - 1) / 3;
+  } else {
+    lz = 0;
+    ly = (t >> 3) * (tb.cy - 1) / 7;
+    lx = (t & 7) * (tb.cx - 1) / 7;
+  }
+  constexpr uint64_t kBias = sizeof(K) == 4 ? 0x80000000ull : 0x8000000000000000ull;
+  constexpr int kShift = 8 * (int)sizeof(K) - 32;
+  const T v = reinterpret_cast<const T*>(fi.x)[((tb.z0 + lz) * g.ny + tb.y0 + ly) * g.nx + tb.x0 + lx];
+  uint32_t kmin = 0xFFFFFFFFu, kmax = 0u;  // top 32 bits of the biased order keys
+  if (is_finite_bits<T>(v)) kmin = kmax = (uint32_t)(((uint64_t)order_key<T>(v) ^ kBias) >> kShift);
+  kmin = __reduce_min_sync(0xffffffffu, kmin);
+  kmax = __reduce_max_sync(0xffffffffu, kmax);
+  if ((t & 31) == 0) {
+    wmin[t >> 5] = kmin;
+    wmax[t >> 5] = kmax;
+  }
+  __syncthreads();
+  if (t == 0) {
+    kmin = wmin[0] < wmin[1] ? wmin[0] : wmin[1];
+    kmax = wmax[0] > wmax[1] ? wmax[0] : wmax[1];
+    fi.tkey[tid] = kmin;
+    double c = 0.0;  // constant fields (inv undefined) and tiles without finite samples count as 0
+    const Params* P = fi.P;
+    if (kmin <= kmax && !P->constant) {
+      // the keys' dropped low bits (f64) only round the span down a little
+      const double lo = (double)value_of_key<T>((K)((((uint64_t)kmin) << kShift) ^ kBias));
+      const double hi = (double)value_of_key<T>((K)((((uint64_t)kmax) << kShift) ^ kBias));
+      const double span = (hi - lo) * P->inv;
+      c = span >= 0.0 ? fmin(span, (double)kSpanClamp) : 0.0;
+    }
+    fi.rank[tid] = (uint32_t)(c * 16.0);
+  }
+}
+
+// Mean sample span (k_tile_keys), in bins, below which the tile pass of a field takes
+// its tiles in tile-key order: thick bins relative to a tile's values, so same-bin
+// chains cross many tile faces and a halo read from lower-valued neighbours already
+// passed saves rerun rounds.  With thin bins the chains end inside their tiles, and
+// the index order keeps neighbouring boxes in L2.
+constexpr unsigned kOrderedSpan = 48;
+
+// pass_order: two bits per field class (0 f32 2D, 1 f32 3D, 2 f64 2D, 3 f64 3D): 0 the
+// span decides, 1 index order, 2 tile-key order.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_order(const FieldInfo* __restrict__ F) {
+__global__ void __launch_bounds__(NT) k_order(const FieldInfo* __restrict__ F, unsigned pass_order) {
   constexpr int NB = 4096, PER = NB / NT;
   static_assert(NB % NT == 0, "whole bucket runs per thread");
   __shared__ unsigned int hist[NB];
@@ -1364,13 +1474,26 @@ __global__ void __launch_bounds__(NT) k_order(const FieldInfo* __restrict__ F) {
   const uint32_t* __restrict__ tkey = fi.tkey;
   if (fi.P->constant || (fi.P->status & kErrNonfinite)) {
     for (int64_t t = threadIdx.x; t < n; t += NT) order[t] = rank[t] = (uint32_t)t;
+    if (threadIdx.x == 0) fi.P->pass_ordered = 0u;
     return;
   }
   uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+  unsigned long long span16 = 0;  // sum of the tiles' sample spans (sixteenths of a bin)
   for (int64_t t = threadIdx.x; t < n; t += NT) {
     const uint32_t k = tkey[t];
     lo = k < lo ? k : lo;
     hi = k > hi ? k : hi;
+    span16 += rank[t];
+  }
+  {
+    __shared__ unsigned long long tmp64[NT / 32 + 1];
+    unsigned long long tot;
+    block_exclusive_scan<NT, unsigned long long>(span16, tmp64, &tot);
+    if (threadIdx.x == 0) {
+      const int cls = 2 * (fi.g.dtype == 1) + (fi.g.ndim == 3);
+      const unsigned mode = (pass_order >> (2 * cls)) & 3u;
+      fi.P->pass_ordered = mode == 2u || (mode == 0u && tot < 16ull * kOrderedSpan * (unsigned long long)n);
+    }
   }
   lo = __reduce_min_sync(0xffffffffu, lo);
   hi = __reduce_max_sync(0xffffffffu, hi);
@@ -1409,6 +1532,21 @@ __global__ void __launch_bounds__(NT) k_order(const FieldInfo* __restrict__ F) {
     order[r] = (uint32_t)t;
     rank[t] = r;
   }
+}
+
+// Clears the subbins of every field whose tile pass is ordered (the pass reads its
+// neighbours' subbins as they are written, so unwritten ones must read 0); other
+// fields' passes write every subbin before anything reads it.  blockIdx.y is the field.
+__global__ void __launch_bounds__(256) k_clear_subbins(const FieldInfo* __restrict__ F) {
+  const FieldInfo& f = F[blockIdx.y];
+  if (!f.P->pass_ordered) return;
+  const int64_t n = f.g.nz * f.g.ny * f.g.nx;
+  uint32_t* __restrict__ s = f.s;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n4 = ((uintptr_t)s & 15u) ? 0 : n / 4;  // 16-byte stores where aligned
+  for (int64_t i = i0; i < n4; i += stride) reinterpret_cast<uint4*>(s)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int64_t i = n4 * 4 + i0; i < n; i += stride) s[i] = 0u;
 }
 
 // ----------------------------------------------------------------- subbin encoder

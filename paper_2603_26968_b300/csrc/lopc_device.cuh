@@ -39,7 +39,7 @@ struct Params {
   unsigned long long const_bits;  // the constant's bits (float32: low 32 bits)
   int fast_ok;                    // inv_f is a normal float: the fast quantizer path may run
   float inv_f;                    // inv rounded to float
-  unsigned int pad0;
+  unsigned int pass_ordered;       // the tile pass takes the tiles in ascending tile key (k_order decides)
   unsigned long long total;       // stream bytes
   unsigned long long rounds;
   unsigned long long fix_iters;   // sum over tile runs of fixpoint sweeps
@@ -390,8 +390,8 @@ struct FieldInfo {
   uint64_t* size_out;     // device: this field's stream length (may be null)
   int* status_out;        // device: this field's LOPC status (may be null)
   uint32_t* dirty;        // tiles to rerun next round: one byte flag per rank (below), ceil(ntiles / 4) words
-  uint32_t* tkey;         // per tile: the top 32 bits of its smallest value's order key
-  uint32_t* order;        // the tiles in ascending tkey (the order reruns visit them in): rank -> tile
+  uint32_t* tkey;         // per tile: the top 32 bits of the smallest order key of its sample points
+  uint32_t* order;        // the tiles in ascending tkey (the order the pass and the reruns visit them in): rank -> tile
   uint32_t* rank;         // the inverse: tile -> rank
   int64_t tile_base;      // first tile in the table's tile index space
   int64_t word_base;      // first dirty word in the table's flat word space

@@ -118,6 +118,10 @@ def lib():
         L.lopc_tune_get_budget.restype = None
         L.lopc_tune_set_dense.argtypes = [C.POINTER(C.c_int)]
         L.lopc_tune_set_dense.restype = None
+        L.lopc_tune_set_pass_order.argtypes = [C.POINTER(C.c_int)]
+        L.lopc_tune_set_pass_order.restype = None
+        L.lopc_tune_get_pass_order.argtypes = [C.POINTER(C.c_int)]
+        L.lopc_tune_get_pass_order.restype = None
         L.lopc_tune_get_dense.argtypes = [C.POINTER(C.c_int)]
         L.lopc_tune_get_dense.restype = None
         L.lopc_verify_workspace_size.argtypes = [D]
@@ -311,11 +315,12 @@ def last_phase_cycles() -> list:
 
 
 def last_fixpoint_work() -> dict:
-    """Fixpoint point evaluations and raises of the last compression (pass, reruns)."""
-    v = (C.c_int64 * 6)()
-    lib().lopc_last_fixpoint_work(v, 6)
+    """Fixpoint point evaluations and raises of the last compression (pass, reruns),
+    rerun tiles loaded and idle, and whether the tile pass ran in tile-key order."""
+    v = (C.c_int64 * 7)()
+    lib().lopc_last_fixpoint_work(v, 7)
     return {"pass_evals": v[0], "pass_raises": v[1], "rerun_evals": v[2], "rerun_raises": v[3],
-            "rerun_tiles": v[4], "rerun_idle": v[5]}
+            "rerun_tiles": v[4], "rerun_idle": v[5], "pass_ordered": v[6]}
 
 
 def last_round_tiles() -> list:
@@ -495,6 +500,20 @@ def tune_set_dense(sixteenths) -> None:
 def tune_get_dense() -> Tuple[int, int, int, int]:
     v = (C.c_int * 4)()
     lib().lopc_tune_get_dense(v)
+    return tuple(int(a) for a in v)
+
+
+PASS_ORDER_AUTO, PASS_ORDER_INDEX, PASS_ORDER_KEY = 0, 1, 2
+
+
+def tune_set_pass_order(modes) -> None:
+    """Tile-pass order per class: PASS_ORDER_AUTO, PASS_ORDER_INDEX or PASS_ORDER_KEY."""
+    lib().lopc_tune_set_pass_order((C.c_int * 4)(*[int(v) for v in modes]))
+
+
+def tune_get_pass_order() -> Tuple[int, int, int, int]:
+    v = (C.c_int * 4)()
+    lib().lopc_tune_get_pass_order(v)
     return tuple(int(a) for a in v)
 
 

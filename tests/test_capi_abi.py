@@ -100,3 +100,22 @@ def test_repair_mode_knob(L):
     assert wl >= tiles + 12 * 30 * 40 * 50
     # batches always use tiles
     assert lib.lopc_batch_compress_workspace_size(1, C.byref(d)) == tiles
+
+
+def test_tuning_knobs_clamp_and_read_back(L):
+    saved = (L.tune_get(), L.tune_get_budget(), L.tune_get_dense(), L.tune_get_pass_order())
+    try:
+        assert saved[3] == (L.PASS_ORDER_AUTO,) * 4  # the default: each field decides
+        L.tune_set_pass_order([-3, 1, 2, 9])
+        assert L.tune_get_pass_order() == (0, 1, 2, 2)
+        L.tune_set([0, 3, 17, 5])
+        assert L.tune_get() == (1, 3, 16, 5)
+        L.tune_set_budget([0, 64, 5000, 7])
+        assert L.tune_get_budget() == (1, 64, 4096, 7)
+        L.tune_set_dense([-1, 8, 18, 17])
+        assert L.tune_get_dense() == (0, 8, 17, 17)
+    finally:
+        L.tune_set(saved[0])
+        L.tune_set_budget(saved[1])
+        L.tune_set_dense(saved[2])
+        L.tune_set_pass_order(saved[3])
