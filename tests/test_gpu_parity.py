@@ -256,18 +256,20 @@ def tile_points(shape, tile, tid):
     return ((zz * sh[1] + yy) * sh[2] + xx).ravel(), (z1 - z0, y1 - y0, x1 - x0)
 
 
-FULL = [
-    ("c2_f32_512", lambda: S.make_field(S.spec_3d_f32(n=512)), 1, 1e-3, (16, 16, 16)),
-    ("c3_f64_ties", lambda: S.make_field(S.spec_3d_f64_ties()), 1, 5e-4, (8, 16, 16)),
+FULL = [  # name, field, mode, bound, chunk tile, whether the tile pass takes tile-key order
+    ("c2_f32_512", lambda: S.make_field(S.spec_3d_f32(n=512)), 1, 1e-3, (16, 16, 16), 0),
+    ("c2_f32_512_loose", lambda: S.make_field(S.spec_3d_f32(n=512)), 1, 1e-2, (16, 16, 16), 1),
+    ("c3_f64_ties", lambda: S.make_field(S.spec_3d_f64_ties()), 1, 5e-4, (8, 16, 16), 0),
 ]
 
 
-@pytest.mark.parametrize("name,make,mode,eb,tile", FULL, ids=[f[0] for f in FULL])
-def test_full_size_sampled_parity(L, orc, name, make, mode, eb, tile):
+@pytest.mark.parametrize("name,make,mode,eb,tile,ordered", FULL, ids=[f[0] for f in FULL])
+def test_full_size_sampled_parity(L, orc, name, make, mode, eb, tile, ordered):
     x = make()
     dc = 0 if x.dtype == np.float32 else 1
     xt = torch.from_numpy(x).cuda()
     st_t = L.compress(xt, eb, mode)
+    assert L.last_fixpoint_work()["pass_ordered"] == ordered
     st = bytes(st_t.cpu().numpy().tobytes())
     b_t, s_t = L.quantize_repair(xt, eb, mode)
     e = orc.resolve_eps(x, mode, eb)

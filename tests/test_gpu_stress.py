@@ -1,8 +1,9 @@
 """Stress of the repair's concurrency: reruns take tiles appended to the round in
-progress, two blocks can hold the same tile, and the order in which tiles are taken
-depends on timing.  Whatever the schedule, the subbins must be the least fixpoint
-(checked at every point by its defining equation) and repeated compressions, single
-or batched, must give the same bytes."""
+progress, two blocks can hold the same tile, a tile pass in tile-key order reads the
+subbins its neighbours are writing, and the order in which tiles are taken depends on
+timing.  Whatever the schedule, the subbins must be the least fixpoint (checked at
+every point by its defining equation) and repeated compressions, single or batched,
+in either pass order, must give the same bytes."""
 import numpy as np
 import pytest
 import torch
@@ -41,12 +42,21 @@ def smooth(shape, dtype, seed):
     return f.astype(dtype)
 
 
+@pytest.fixture
+def auto_order(L):
+    saved = L.tune_get_pass_order()
+    yield
+    L.tune_set_pass_order(saved)
+
+
 @pytest.mark.parametrize("shape,dtype,eb,seed", FIELDS, ids=[f"{len(f[0])}d_{np.dtype(f[1]).name}_{f[2]:g}" for f in FIELDS])
-def test_least_fixpoint_and_identical_bytes_under_any_schedule(L, shape, dtype, eb, seed):
+def test_least_fixpoint_and_identical_bytes_under_any_schedule(L, auto_order, shape, dtype, eb, seed):
     x = smooth(shape, dtype, seed)
     xt = torch.from_numpy(x).cuda()
     first = None
-    for rep in range(4):
+    for rep in range(6):
+        # alternate the pass order: index / tile key / by the field
+        L.tune_set_pass_order([(L.PASS_ORDER_INDEX, L.PASS_ORDER_KEY, L.PASS_ORDER_AUTO)[rep % 3]] * 4)
         b, s = L.quantize_repair(xt, eb, L.NOA)
         xd = xt.double() if dtype == np.float32 else xt
         assert lfp_local_equality(xd, b, s) == 0, f"repetition {rep}"
@@ -56,13 +66,14 @@ def test_least_fixpoint_and_identical_bytes_under_any_schedule(L, shape, dtype, 
         assert st == first, f"repetition {rep}"
 
 
-def test_batch_of_loose_fields_equals_single_calls(L):
+def test_batch_of_loose_fields_equals_single_calls(L, auto_order):
     xs = [smooth(sh, dt, sd) for sh, dt, _, sd in FIELDS] + [bumps((40, 50, 60), np.float32, seed=9)]
     ebs = [eb for _, _, eb, _ in FIELDS] + [1e-2]
     fields = [torch.from_numpy(x).cuda() for x in xs]
     singles = [bytes(L.compress(t, eb, L.NOA).cpu().numpy().tobytes()) for t, eb in zip(fields, ebs)]
     b = L.BatchCompress(fields, ebs)
-    for _ in range(3):
+    for rep in range(3):
+        L.tune_set_pass_order([(L.PASS_ORDER_AUTO, L.PASS_ORDER_KEY, L.PASS_ORDER_INDEX)[rep]] * 4)
         b.launch()
         streams, status = b.results()
         assert status == [0] * len(fields)
