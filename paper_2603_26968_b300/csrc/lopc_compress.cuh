@@ -1592,7 +1592,19 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC) k_encode_sub(const FieldI
   const TileBox tb = tile_box(g, tid);
   const int n = tb.n, n32 = (n + 31) & ~31;
   const int64_t plane = g.ny * g.nx;
-  if (n == G::NP && W == 4) {  // subbins are already words: asynchronous copies
+  if (n == G::NP && W == 4 && (g.nx & 3) == 0 && ((uintptr_t)s_glob & 15u) == 0) {
+    // subbins are already words, and every row of four starts on a 16-byte boundary
+    // (x0 and TX are multiples of 16): 16-byte asynchronous copies
+    static_assert(G::TX % 4 == 0, "rows of whole 16-byte copies");
+    for (int i = 4 * threadIdx.x; i < n; i += 4 * NT) {
+      const int lx = i % G::TX, ly = (i / G::TX) % G::TY, lz = i / (G::TX * G::TY);
+      const unsigned d = (unsigned)__cvta_generic_to_shared(&ws[i]);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d),
+                   "l"(&s_glob[(tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx])
+                   : "memory");
+    }
+    cp_async_wait_all();
+  } else if (n == G::NP && W == 4) {  // subbins are already words: 4-byte asynchronous copies
     for (int i = threadIdx.x; i < n; i += NT) {
       const int lx = i % G::TX, ly = (i / G::TX) % G::TY, lz = i / (G::TX * G::TY);
       cp_async4(&ws[i], &s_glob[(tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx], true);
