@@ -388,7 +388,7 @@ __device__ __forceinline__ int frontier_fixpoint(uint32_t* sv, const uint32_t* c
                                                  unsigned& evals, unsigned& raises,
                                                  unsigned eval_budget = 0xffffffffu) {
   constexpr int NW = G::NP / 32, NT = G::NT;
-  constexpr unsigned kTail = 32, kBack = 64;  // warp 0 alone below kTail points, until above kBack
+  constexpr unsigned kTail = 16, kBack = 32;  // warp 0 alone below kTail points, until above kBack
   static_assert(NW <= NT && NW % 32 == 0, "one frontier word per thread; whole words per lane");
   volatile uint32_t* vs = sv;
   const int lane = threadIdx.x & 31;
@@ -640,7 +640,7 @@ __device__ __forceinline__ int topo_fixpoint(uint32_t* sv, const uint32_t* cml, 
       if (readym & (1u << k)) lout[base++] = (uint16_t)(o + G::loff(dz_of(k), dy_of(k), dx_of(k)));
     }
   };
-  constexpr unsigned kTail = 32, kBack = 64;  // warp 0 alone below kTail ready points, until above kBack
+  constexpr unsigned kTail = 16, kBack = 32;  // warp 0 alone below kTail ready points, until above kBack
   unsigned n = cnt[0];
   int cur = 0;
   int wave = 0;
