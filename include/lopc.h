@@ -123,7 +123,10 @@ LOPC_API int lopc_decompress(const void* d_in, size_t in_size, void* d_x, size_t
  * Host arrays hold n entries; d_out_size and d_status are DEVICE arrays of n that
  * receive each field's stream length and status.  Asynchronous: nothing waits for
  * the stream; read the results after synchronising.  The workspace must not be used
- * by another call until this one has finished on the GPU. */
+ * by another call until this one has finished on the GPU.  A compression batch holds
+ * at most LOPC_MAX_BATCH_FIELDS fields (the field index is a grid dimension of several
+ * kernels): a larger n returns LOPC_ERR_INVALID_ARG, and its workspace size is 0. */
+#define LOPC_MAX_BATCH_FIELDS 65535
 LOPC_API size_t lopc_batch_compress_workspace_size(int n, const lopc_field_desc* descs);
 LOPC_API int lopc_batch_compress(int n, const lopc_field_desc* descs, const void* const* d_x, void* const* d_out,
                                  const size_t* out_cap, uint64_t* d_out_size, int* d_status, void* d_ws,

@@ -1215,7 +1215,7 @@ int lopc_set_repair_mode(int mode) {
 }
 
 size_t lopc_batch_compress_workspace_size(int n, const lopc_field_desc* descs) {
-  if (n <= 0 || !descs) return 0;
+  if (n <= 0 || n > LOPC_MAX_BATCH_FIELDS || !descs) return 0;
   for (int i = 0; i < n; ++i)
     if (!desc_valid(&descs[i])) return 0;
   CompressPlan p;
@@ -1252,7 +1252,8 @@ int lopc_compress(const lopc_field_desc* d, const void* d_x, void* d_out, size_t
 int lopc_batch_compress(int n, const lopc_field_desc* descs, const void* const* d_x, void* const* d_out,
                         const size_t* out_cap, uint64_t* d_out_size, int* d_status, void* d_ws, size_t ws_size,
                         void* stream) {
-  if (n <= 0 || !descs || !d_x || !d_out || !out_cap || !d_out_size || !d_status) return LOPC_ERR_INVALID_ARG;
+  if (n <= 0 || n > LOPC_MAX_BATCH_FIELDS || !descs || !d_x || !d_out || !out_cap || !d_out_size || !d_status)
+    return LOPC_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i)
     if (!desc_valid(&descs[i]) || !d_x[i] || !d_out[i]) return LOPC_ERR_INVALID_ARG;
   CompressPlan p;

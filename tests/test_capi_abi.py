@@ -119,3 +119,19 @@ def test_tuning_knobs_clamp_and_read_back(L):
         L.tune_set_budget(saved[1])
         L.tune_set_dense(saved[2])
         L.tune_set_pass_order(saved[3])
+
+
+def test_batch_field_limit(L):
+    """A compression batch holds at most LOPC_MAX_BATCH_FIELDS fields: the limit is
+    checked on the host, before any launch."""
+    lib = L.lib()
+    d = L.make_desc((8, 8), "f32", L.NOA, 1e-3)
+    for n, ok in ((65535, True), (65536, False)):
+        descs = (type(d) * n)(*([d] * n))
+        assert (lib.lopc_batch_compress_workspace_size(n, descs) > 0) == ok
+    n = 65536
+    descs = (type(d) * n)(*([d] * n))
+    ptrs = (C.c_void_p * n)(*([1] * n))
+    caps = (C.c_size_t * n)(*([4096] * n))
+    rc = lib.lopc_batch_compress(n, descs, ptrs, ptrs, caps, C.c_void_p(1), C.c_void_p(1), C.c_void_p(1), 1 << 40, None)
+    assert rc == -1
