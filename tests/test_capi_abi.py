@@ -135,3 +135,13 @@ def test_batch_field_limit(L):
     caps = (C.c_size_t * n)(*([4096] * n))
     rc = lib.lopc_batch_compress(n, descs, ptrs, ptrs, caps, C.c_void_p(1), C.c_void_p(1), C.c_void_p(1), 1 << 40, None)
     assert rc == -1
+
+
+def test_fixpoint_work_reports_seven_values(L):
+    """Pass and rerun evaluations and raises, rerun tiles and idle ones, and the pass
+    order taken: the count is part of the ABI, so a caller can size its array."""
+    v = (C.c_int64 * 9)(*([-7] * 9))
+    assert L.lib().lopc_last_fixpoint_work(v, 9) == 7
+    assert v[7] == v[8] == -7  # nothing past the seventh value is written
+    assert set(L.last_fixpoint_work()) == {"pass_evals", "pass_raises", "rerun_evals", "rerun_raises",
+                                           "rerun_tiles", "rerun_idle", "pass_ordered"}
