@@ -16,21 +16,28 @@ import numpy as np
 HERE = Path(__file__).resolve().parent
 SRC = HERE / "lopc_oracle.c"
 LIB = HERE / "_liboracle.so"
+LIB_OMP = HERE / "_liboracle_omp.so"
 
 OK, INVALID_ARG, NONFINITE, RANGE, CAPACITY, CORRUPT = 0, -1, -2, -3, -4, -5
 
 
 def build(force: bool = False, openmp: bool = False) -> Path:
-    """Compiles the oracle with gcc (IEEE binary64 on SSE2, no FMA contraction)."""
-    if LIB.exists() and not force and LIB.stat().st_mtime >= max(SRC.stat().st_mtime,
+    """Compiles the oracle with gcc (IEEE binary64 on SSE2, no FMA contraction).
+
+    ``openmp=True`` builds the same source a second time with -fopenmp
+    (``_liboracle_omp.so``): the quantizer's points and the coder's and decoder's
+    chunks are then split over threads; the output bytes are the same."""
+    out = LIB_OMP if openmp else LIB
+    if out.exists() and not force and out.stat().st_mtime >= max(SRC.stat().st_mtime,
                                                                (HERE / "lopc_oracle.h").stat().st_mtime):
-        return LIB
-    tmp = LIB.with_suffix(f".{os.getpid()}.tmp")
-    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
-           str(SRC), "-o", str(tmp), "-lquadmath", "-lm"]
+        return out
+    tmp = out.with_suffix(f".{os.getpid()}.tmp")
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-Wno-unknown-pragmas",
+           "-shared", "-fPIC", *(["-fopenmp"] if openmp else []), str(SRC), "-o", str(tmp),
+           "-lquadmath", "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, out)
+    return out
 
 
 class Desc(C.Structure):
@@ -38,14 +45,13 @@ class Desc(C.Structure):
                 ("mode", C.c_int32), ("pad_", C.c_int32), ("eb", C.c_double)]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        build()
-        L = C.CDLL(str(LIB))
+def lib(openmp: bool = False):
+    """The single-threaded oracle, or (openmp=True) its OpenMP build."""
+    if openmp not in _libs:
+        L = C.CDLL(str(build(openmp=openmp)))
         P = C.c_void_p
         L.orc_resolve_eps.argtypes = [C.POINTER(Desc), P, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_double)]
@@ -78,8 +84,14 @@ def lib():
         L.orc_order_violations.argtypes = [C.POINTER(Desc), P, P]
         L.orc_order_violations.restype = C.c_int64
         L.orc_critical_types.argtypes = [C.POINTER(Desc), P, P, P]
-        _lib = L
-    return _lib
+        _libs[openmp] = L
+    return _libs[openmp]
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP build uses (OMP_NUM_THREADS, else every core it sees)."""
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n and n.isdigit() and int(n) > 0 else (os.cpu_count() or 1)
 
 
 def _ptr(a: np.ndarray):
@@ -258,15 +270,16 @@ def encode_chunk(dtype_c: int, b: np.ndarray, s: np.ndarray, shape):
 
 # whole stream ------------------------------------------------------------------
 
-def compress(x: np.ndarray, mode: int = 1, eb: float = 1e-3) -> bytes:
+def compress(x: np.ndarray, mode: int = 1, eb: float = 1e-3, openmp: bool = False) -> bytes:
     x = _c(x)
+    L = lib(openmp)
     d = make_desc(x.shape, dtype_code(x), mode, eb)
-    cap = lib().orc_compress_bound(C.byref(d))
+    cap = L.orc_compress_bound(C.byref(d))
     if cap == 0:
         raise OracleError(INVALID_ARG, "compress_bound")
     out = np.zeros(cap, np.uint8)
     sz = C.c_size_t()
-    rc = lib().orc_compress(C.byref(d), _ptr(x), _ptr(out), cap, C.byref(sz))
+    rc = L.orc_compress(C.byref(d), _ptr(x), _ptr(out), cap, C.byref(sz))
     if rc:
         raise OracleError(rc, "compress")
     return out[:sz.value].tobytes()
@@ -292,12 +305,12 @@ def peek(stream: bytes) -> Desc:
     return d
 
 
-def decompress(stream: bytes) -> np.ndarray:
+def decompress(stream: bytes, openmp: bool = False) -> np.ndarray:
     a = np.frombuffer(stream, np.uint8).copy()
     d = peek(stream)
     shape = tuple(int(d.dims[k]) for k in range(d.ndim))
     out = np.empty(shape, np.float32 if d.dtype == 0 else np.float64)
-    rc = lib().orc_decompress(_ptr(a), a.size, _ptr(out), out.nbytes)
+    rc = lib(openmp).orc_decompress(_ptr(a), a.size, _ptr(out), out.nbytes)
     if rc:
         raise OracleError(rc, "decompress")
     return out

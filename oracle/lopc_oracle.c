@@ -3,6 +3,10 @@
  * TEST INFRASTRUCTURE ONLY (see lopc_oracle.h).  Every function follows a passage of
  * the paper or one of the stated readings of it; nothing here is blocked, fused or
  * reordered for speed.  Build:  gcc -O2 -ffp-contract=off -shared -fPIC ... -lquadmath
+ * A second build adds -fopenmp: the loops whose iterations are independent (points
+ * of the quantizer, chunks of the coder and decoder) are then split over threads,
+ * each iteration computing exactly what it computes alone, so both builds give the
+ * same bytes.  The repair stays one sequential pass in (value, index) order.
  *
  * Readings of the paper that this file fixes (the paper is silent or garbled there):
  *   neighbourhood   Freudenthal triangulation of the grid (Sec. II, "as in prior
@@ -93,12 +97,16 @@ int64_t orc_q1(int dtype, double v, double inv) {
 
 int orc_quantize(int dtype, const void* x, int64_t n, double inv, int64_t* b) {
   int64_t lim = bin_limit(dtype);
+  int bad = 0; /* every point is independent: the OpenMP build splits the loop */
+#pragma omp parallel for schedule(static) reduction(| : bad)
   for (int64_t i = 0; i < n; i++) {
     int64_t q = orc_q1(dtype, val_at(dtype, x, i), inv);
-    if (q == INT64_MIN || q >= lim || q <= -lim) return ORC_RANGE;
-    b[i] = q;
+    if (q == INT64_MIN || q >= lim || q <= -lim)
+      bad = 1;
+    else
+      b[i] = q;
   }
-  return ORC_OK;
+  return bad ? ORC_RANGE : ORC_OK;
 }
 
 /* Sec. III-E: subbin 0 is the lowest representable value of the bin.  The
@@ -269,6 +277,7 @@ int orc_repair_lfp(const orc_desc* d, const void* x, const int64_t* b, uint64_t*
   int64_t n = g.nx * g.ny * g.nz;
   vi_t* ord = (vi_t*)malloc(sizeof(vi_t) * (size_t)n);
   if (!ord) return ORC_CAPACITY;
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; i++) {
     ord[i].v = val_at(d->dtype, x, i);
     ord[i].i = i;
@@ -891,12 +900,14 @@ int orc_compress(const orc_desc* d, const void* x, uint8_t* out, size_t cap, siz
     return rc;
   }
   int64_t cmax = T.t[0] * T.t[1] * T.t[2];
-  int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)cmax);
-  int64_t* tb = (int64_t*)malloc(sizeof(int64_t) * (size_t)cmax);
-  uint64_t* ts = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)cmax);
   uint32_t* sizes = (uint32_t*)malloc(sizeof(uint32_t) * 2 * (size_t)T.ntiles);
   uint8_t** recs = (uint8_t**)malloc(sizeof(uint8_t*) * 2 * (size_t)T.ntiles);
+  /* chunks are coded independently (Sec. II-C): the OpenMP build splits this loop */
+#pragma omp parallel for schedule(dynamic, 16)
   for (int64_t c = 0; c < T.ntiles; c++) {
+    int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)cmax);
+    int64_t* tb = (int64_t*)malloc(sizeof(int64_t) * (size_t)cmax);
+    uint64_t* ts = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)cmax);
     int64_t dims[3];
     int64_t m = tile_points(&T, c, idx, dims);
     for (int64_t i = 0; i < m; i++) {
@@ -907,6 +918,9 @@ int orc_compress(const orc_desc* d, const void* x, uint8_t* out, size_t cap, siz
     recs[T.ntiles + c] = (uint8_t*)malloc((size_t)m * w + 64);
     sizes[c] = enc_bins(w, tb, dims, recs[c]);
     sizes[T.ntiles + c] = enc_subbins(w, ts, m, recs[T.ntiles + c]);
+    free(idx);
+    free(tb);
+    free(ts);
   }
   size_t table = pad16((size_t)T.ntiles * 8);
   size_t total = HDR + table;
@@ -928,9 +942,6 @@ int orc_compress(const orc_desc* d, const void* x, uint8_t* out, size_t cap, siz
   for (int64_t c = 0; c < 2 * T.ntiles; c++) free(recs[c]);
   free(recs);
   free(sizes);
-  free(idx);
-  free(tb);
-  free(ts);
   free(b);
   free(s);
   return rc;
@@ -1024,24 +1035,27 @@ int orc_decompress(const uint8_t* in, size_t n, void* xhat, size_t cap_bytes) {
     return ORC_CORRUPT;
   }
   int64_t cmax = T.t[0] * T.t[1] * T.t[2];
-  int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)cmax);
-  int64_t* tb = (int64_t*)malloc(sizeof(int64_t) * (size_t)cmax);
-  uint64_t* ts = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)cmax);
-  for (int64_t c = 0; c < T.ntiles && rc == ORC_OK; c++) {
+  int bad = 0; /* every decoder error is a corrupt stream */
+  /* chunks decode independently (Sec. III-E): the OpenMP build splits this loop */
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
+  for (int64_t c = 0; c < T.ntiles; c++) {
+    int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)cmax);
+    int64_t* tb = (int64_t*)malloc(sizeof(int64_t) * (size_t)cmax);
+    uint64_t* ts = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)cmax);
     int64_t dims[3];
     int64_t m = tile_points(&T, c, idx, dims);
     uint32_t sb = (uint32_t)get_word(tab + 4 * c, 4), ss = (uint32_t)get_word(tab + 4 * (T.ntiles + c), 4);
-    rc = dec_bins(w, H.version, in + off[c], sb, dims, tb);
-    if (rc == ORC_OK) rc = dec_subbins(w, in + off[T.ntiles + c], ss, m, ts);
-    for (int64_t i = 0; i < m && rc == ORC_OK; i++) {
+    int crc = dec_bins(w, H.version, in + off[c], sb, dims, tb);
+    if (crc == ORC_OK) crc = dec_subbins(w, in + off[T.ntiles + c], ss, m, ts);
+    for (int64_t i = 0; i < m && crc == ORC_OK; i++) {
       double lo;
       if (orc_lowest_in_bin(H.d.dtype, tb[i], H.inv, &lo) != ORC_OK) {
-        rc = ORC_CORRUPT;
+        crc = ORC_CORRUPT;
         break;
       }
       double v = orc_succ_k(H.d.dtype, lo, ts[i]);
       if (!isfinite(v)) {
-        rc = ORC_CORRUPT;
+        crc = ORC_CORRUPT;
         break;
       }
       if (H.d.dtype == 0)
@@ -1049,12 +1063,13 @@ int orc_decompress(const uint8_t* in, size_t n, void* xhat, size_t cap_bytes) {
       else
         ((double*)xhat)[idx[i]] = v;
     }
+    if (crc != ORC_OK) bad = 1;
+    free(idx);
+    free(tb);
+    free(ts);
   }
   free(off);
-  free(idx);
-  free(tb);
-  free(ts);
-  return rc;
+  return bad ? ORC_CORRUPT : ORC_OK;
 }
 
 /* ---------------------------------------------------------------- checkers */

@@ -1,6 +1,7 @@
 """Serving engine and request loop on the GPU: each served stream is byte-identical
-to the same field compressed alone, fields admitted while others are in repair
-join them between rounds, and a failing field fails alone."""
+to the same field compressed alone and to the oracle's stream of that field, fields
+admitted while others are in repair join them between rounds, and a failing field
+fails alone."""
 import numpy as np
 import pytest
 import torch
@@ -25,7 +26,9 @@ def _mixed_specs(n, seed, rate=3000.0):
     return specs
 
 
-def test_served_streams_equal_solo_streams(L):
+def test_served_streams_equal_solo_streams(L, orc):
+    """Each served stream equals the same field compressed alone and, byte for byte,
+    the oracle's stream of that field (copied to the host)."""
     from paper_2603_26968_b300 import serve
     specs = _mixed_specs(24, seed=5)
     assert {(len(s.shape), s.dtype) for s in specs} == {(2, "f32"), (3, "f32"), (2, "f64"), (3, "f64")}
@@ -40,9 +43,12 @@ def test_served_streams_equal_solo_streams(L):
         solo = serve.solo_stream(r.spec)
         assert r.size == solo.numel()
         assert torch.equal(r.stream, solo), r.spec
+        x = SG.make_field(r.spec).cpu().numpy()   # the field the server compressed
+        want = orc.compress(x, 1, r.spec.eb, openmp=True)
+        assert bytes(r.stream.cpu().numpy().tobytes()) == want, r.spec
 
 
-def test_tight_budget_serialises_but_still_matches(L):
+def test_tight_budget_serialises_but_still_matches(L, orc):
     from paper_2603_26968_b300 import serve
     specs = _mixed_specs(8, seed=6)
     need = max(sum(serve.request_bytes(s).values()) for s in specs)
@@ -53,9 +59,11 @@ def test_tight_budget_serialises_but_still_matches(L):
     for r in rep.served:
         assert r.status == L.OK
         assert torch.equal(r.stream, serve.solo_stream(r.spec))
+        want = orc.compress(SG.make_field(r.spec).cpu().numpy(), 1, r.spec.eb, openmp=True)
+        assert bytes(r.stream.cpu().numpy().tobytes()) == want, r.spec
 
 
-def test_several_rounds_per_step_match_solo(L):
+def test_several_rounds_per_step_match_solo(L, orc):
     from paper_2603_26968_b300 import serve
     specs = _mixed_specs(10, seed=11)
     srv = serve.Server(budget_bytes=2 << 30, max_fields=32, rounds_per_step=3)
@@ -64,6 +72,8 @@ def test_several_rounds_per_step_match_solo(L):
     for r in rep.served:
         assert r.status == L.OK
         assert torch.equal(r.stream, serve.solo_stream(r.spec))
+        want = orc.compress(SG.make_field(r.spec).cpu().numpy(), 1, r.spec.eb, openmp=True)
+        assert bytes(r.stream.cpu().numpy().tobytes()) == want, r.spec
 
 
 def _engine_submit(L, E, x, eb, tag, cap=None):
