@@ -236,13 +236,30 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool pred)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Asynchronous copy of a tile's box (the tile and a one-point halo; 2D tiles have no
-// z halo) of `src` (row-major field of nz x ny x nx elements of `Word`) into shared
-// memory at `dst` (entry layout of G).  Rows are walked as (row, column) with one
-// row base per row: the interior columns go to lanes (16-byte copies of four words
-// when the layout and the field allow it), the two halo columns are a second loop.
-// Absent points read nothing and are zero.  The caller waits.
-template <typename G, typename Word>
+// A word copy into shared memory for a box load: asynchronous through L1
+// (cp.async.ca) for data no block changes during the kernel, or else a load from L2
+// (ld.global.cg; L1 is not coherent across SMs, so a line it cached earlier in the
+// same kernel could hold a value another block has raised since) and a store.
+template <bool MUTABLE, typename Word>
+__device__ __forceinline__ void box_word(Word* dst, const Word* src, bool in) {
+  if (MUTABLE) {
+    *dst = in ? __ldcg(src) : (Word)0;
+  } else if (sizeof(Word) == 4) {
+    cp_async4(dst, src, in);
+  } else {
+    cp_async8(dst, src, in);
+  }
+}
+
+// Copy of a tile's box (the tile and a one-point halo; 2D tiles have no z halo) of
+// `src` (row-major field of nz x ny x nx elements of `Word`) into shared memory at
+// `dst` (entry layout of G).  Rows are walked as (row, column) with one row base per
+// row: the interior columns go to lanes (asynchronous 16-byte copies of four words,
+// which bypass L1, when the layout and the field allow it), the two halo columns are
+// a second loop.  Absent points read nothing and are zero.  MUTABLE: `src` may be
+// changed by other blocks during the kernel (see box_word).  The caller waits for
+// the asynchronous copies.
+template <typename G, typename Word, bool MUTABLE = false>
 __device__ __forceinline__ void load_box_async(Word* dst, const Word* __restrict__ src, const Geometry& g,
                                                const TileBox& tb) {
   static_assert(G::TX == 16 || G::TX == 64, "interior columns are whole lane groups");
@@ -278,10 +295,7 @@ __device__ __forceinline__ void load_box_async(Word* dst, const Word* __restrict
       for (int lx = c; lx < G::TX; lx += CW) {
         const int64_t gx = tb.x0 + lx;
         const bool in = row_in && gx < g.nx;
-        if (sizeof(Word) == 4)
-          cp_async4(&drow[lx], in ? row + gx : src, in);
-        else
-          cp_async8(&drow[lx], in ? row + gx : src, in);
+        box_word<MUTABLE>(&drow[lx], in ? row + gx : src, in);
       }
     }
   }
@@ -293,10 +307,7 @@ __device__ __forceinline__ void load_box_async(Word* dst, const Word* __restrict
     const int64_t gx = side ? tb.x0 + G::TX : tb.x0 - 1;
     const bool in = gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx >= 0 && gx < g.nx;
     Word* d = dst + lz * G::PP + ly * G::BXP + (side ? G::XO + G::TX : G::XO - 1);
-    if (sizeof(Word) == 4)
-      cp_async4(d, in ? src + gz * plane + gy * g.nx + gx : src, in);
-    else
-      cp_async8(d, in ? src + gz * plane + gy * g.nx + gx : src, in);
+    box_word<MUTABLE>(d, in ? src + gz * plane + gy * g.nx + gx : src, in);
   }
 }
 
@@ -345,6 +356,58 @@ __device__ __forceinline__ uint32_t out_of_box_bits(int lz, int ly, int lx) {
   uint32_t r = (ly == 0 ? yl : 0u) | (ly == G::TY - 1 ? yh : 0u) | (lx == 0 ? xl : 0u) | (lx == G::TX - 1 ? xh : 0u);
   if (G::HZ) r |= (lz == 0 ? zl : 0u) | (lz == G::TZ - 1 ? zh : 0u);
   return r;
+}
+
+// Bit (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1) of the neighbour tile (dz, dy, dx in
+// {-1, 0, 1}) that holds the box entry at local (lz, ly, lx) of a tile.
+template <typename G>
+__device__ __forceinline__ uint32_t tile_dir_bit(int lz, int ly, int lx) {
+  const int dz = lz < 0 ? -1 : lz >= G::TZ ? 1 : 0, dy = ly < 0 ? -1 : ly >= G::TY ? 1 : 0;
+  const int dx = lx < 0 ? -1 : lx >= G::TX ? 1 : 0;
+  return 1u << ((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
+}
+
+// Tile index of the neighbour in direction d (a tile_dir_bit position) of tile tid,
+// or -1 when it lies outside the field's tiles.
+__device__ __forceinline__ int64_t neighbour_tile(const Geometry& g, int64_t tid, int d) {
+  const int64_t tz = tid / (g.ntx * g.nty), ty = (tid / g.ntx) % g.nty, tx = tid % g.ntx;
+  const int64_t nz = tz + d / 9 - 1, ny = ty + (d / 3) % 3 - 1, nx = tx + d % 3 - 1;
+  if (nz < 0 || nz >= g.ntz || ny < 0 || ny >= g.nty || nx < 0 || nx >= g.ntx) return -1;
+  return (nz * g.nty + ny) * g.ntx + nx;
+}
+
+// Neighbour-tile bits of the constraints that the thread's segment points violate
+// after a rerun: a point p of the segment that rose in this run constrains each
+// out-of-tile upper same-bin neighbour q to s(q) >= s(p) + [p after q]; q's value in
+// the box is what this run loaded (a lower bound of its current value), so a tile
+// whose constraint holds there is never marked, and one whose constraint fails may
+// be marked when it need not be (its rerun then finds every constraint held).
+// `cm(o)` gives point o's lower bits 0-13 and same-bin bits 16-29; `risen(j)`
+// whether segment point j rose.
+template <typename G, typename CmFn, typename RisenFn>
+__device__ __forceinline__ uint32_t violated_tile_bits(const uint32_t* sv, const TileBox& tb, int lz, int ly0, int lx,
+                                                       int e0, int o0, CmFn cm, RisenFn risen) {
+  uint32_t bits = 0;
+  if (lz >= tb.cz || lx >= tb.cx) return 0;
+#pragma unroll 1
+  for (int j = 0; j < G::SEG; ++j) {
+    const int ly = ly0 + j;
+    if (ly >= tb.cy) break;
+    const uint32_t ob = out_of_box_bits<G>(lz, ly, lx);
+    if (!ob || !risen(j)) continue;
+    const uint32_t m = cm(o0 + j * G::TX);
+    const uint32_t upo = (m >> 16) & ~m & ob & 0x3FFFu;
+    if (!upo) continue;
+    const int e = e0 + j * G::BXP;
+    const uint32_t v = sv[e];
+#pragma unroll
+    for (int k = 0; k < 14; ++k) {
+      if (!G::HZ && dz_of(k) != 0) continue;
+      if (((upo >> k) & 1u) && sv[e + G::off(dz_of(k), dy_of(k), dx_of(k))] < v + (k < 7 ? 1u : 0u))
+        bits |= tile_dir_bit<G>(lz + dz_of(k), ly + dy_of(k), lx + dx_of(k));
+    }
+  }
+  return bits;
 }
 
 // Local coordinates of tile point o (linear order: x fastest).
@@ -998,11 +1061,6 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
     }
     __syncthreads();
     const uint32_t ebits = earlier;
-    auto tile_bit = [](int lz, int ly, int lx) {  // which neighbour tile a halo entry lies in
-      const int dz = lz < 0 ? -1 : lz >= G::TZ ? 1 : 0, dy = ly < 0 ? -1 : ly >= G::TY ? 1 : 0;
-      const int dx = lx < 0 ? -1 : lx >= G::TX ? 1 : 0;
-      return 1u << ((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
-    };
     if (ebits) {
       constexpr int NZF = G::HZ ? 2 * G::BY * G::BX : 0;  // z faces (whole planes)
       constexpr int NYF = 2 * G::TZ * G::BX;              // y faces of the tile's planes
@@ -1025,7 +1083,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
           ly = r % G::TY;
           lx = jj < G::TZ * G::TY ? -1 : G::TX;
         }
-        if (!(ebits & tile_bit(lz, ly, lx))) continue;  // a later tile: its subbins are still 0
+        if (!(ebits & tile_dir_bit<G>(lz, ly, lx))) continue;  // a later tile: its subbins are still 0
         const int64_t qz = tb.z0 + lz, qy = tb.y0 + ly, qx = tb.x0 + lx;
         if (qz >= 0 && qz < g.nz && qy >= 0 && qy < g.ny && qx >= 0 && qx < g.nx)
           sv[G::entry(lz, ly, lx)] = __ldcg(&s_glob[qz * plane + qy * g.nx + qx]);
@@ -1073,14 +1131,11 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
 template <typename T, int ND>
 struct RerunSmem {
   using G = TileGeom<T, ND, true>;
-  // boundary points of a tile: an upper bound for the queue of risen boundary points
-  static constexpr int QMAX = G::HZ ? 2 * (G::TY * G::TX + G::TZ * G::TX + G::TZ * G::TY) : 2 * (G::TX + G::TY);
   static constexpr size_t up16(size_t v) { return (v + 15) & ~(size_t)15; }
   static constexpr size_t CM = (size_t)G::E * 4;                      // subbins, then lower masks
   static constexpr size_t BITS = CM + up16((size_t)G::NP * 4);        // frontiers, risen bits, counters
   static constexpr size_t LIST = BITS + up16(FixSmem<G>::bits_bytes());
-  static constexpr size_t QUEUE = LIST + FixSmem<G>::list_bytes();
-  static constexpr size_t bytes() { return QUEUE + (size_t)QMAX * 4 + 16; }
+  static constexpr size_t bytes() { return LIST + FixSmem<G>::list_bytes(); }
 };
 
 // Rerun of a tile whose halo subbins may have risen: the stored lower-neighbour
@@ -1105,8 +1160,8 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
   uint32_t* rb = fa0 + 2 * (G::NP / 32);
   unsigned* cnt = rb + G::NP / 32;
   uint16_t* flist = reinterpret_cast<uint16_t*>(smem + RS::LIST);
-  uint32_t* queue = reinterpret_cast<uint32_t*>(smem + RS::QUEUE);
-  __shared__ uint32_t qn;
+  __shared__ uint32_t marks;
+  __shared__ uint32_t nb_rank[27];  // ranks of the neighbour tiles (~0u: none)
   __shared__ unsigned s_item, s_claimed;
   __shared__ long long s_lim, s_app_gt;
   // the first round (list == nullptr) visits every tile of the class; blocks take
@@ -1182,7 +1237,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
     long long t0 = clock64();
     // subbins of the box and lower masks of the tile's own points, by asynchronous
     // copies (absent points read nothing and are zero)
-    load_box_async<G, uint32_t>(sv, s_glob, g, tb);
+    load_box_async<G, uint32_t, true>(sv, s_glob, g, tb);  // other blocks of this round raise subbins
     if ((g.nx & 3) == 0) {  // four masks per 16-byte copy (a copy is wholly inside or outside)
       for (int i = threadIdx.x; i < G::NP / 4; i += NT) {
         const int o = 4 * i;
@@ -1203,7 +1258,11 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
       }
     }
     for (int i = threadIdx.x; i < 3 * (G::NP / 32); i += NT) fa0[i] = 0;  // frontiers, risen bits
-    if (threadIdx.x == 0) qn = 0;
+    if (threadIdx.x < 27) {  // the neighbour tiles' ranks, for marking (loaded beside the box)
+      const int64_t nt = threadIdx.x == 13 ? -1 : neighbour_tile(g, tid, threadIdx.x);
+      nb_rank[threadIdx.x] = nt >= 0 ? fi.rank[nt] : ~0u;
+    }
+    if (threadIdx.x == 0) marks = 0u;
     cp_async_wait_all();
     __syncthreads();
     const SegPos sp = seg_pos<G>();
@@ -1258,10 +1317,10 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
     }
     block_add2(evals, raises, &P->work[2]);
     phase_mark(P, 6, t0);
-    // write the subbins that rose; queue the risen boundary points.  With appended
-    // tiles two blocks can hold the same tile at once, each from its own snapshot: the
-    // write takes the larger value, and the elementwise max of two tile-local
-    // fixpoints is again one (each is a lower bound of the least fixpoint)
+    // write the subbins that rose.  With appended tiles two blocks can hold the same
+    // tile at once, each from its own snapshot: the write takes the larger value, and
+    // the elementwise max of two tile-local fixpoints is again one (each is a lower
+    // bound of the least fixpoint)
     const int64_t gz = tb.z0 + sp.lz, gx = tb.x0 + sp.lx;
     if (col_in && risen) {
 #pragma unroll 1
@@ -1269,48 +1328,31 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
         if (!((risen >> j) & 1u)) continue;
         const int ly = sp.ly0 + j;
         atomicMax(&s_glob[gz * plane + (tb.y0 + ly) * g.nx + gx], sv[sp.e0 + j * G::BXP]);
-        if (out_of_box_bits<G>(sp.lz, ly, sp.lx)) {
-          const uint32_t slot = atomicAdd(&qn, 1u);
-          if (slot < (uint32_t)RS::QMAX) queue[slot] = ((uint32_t)sp.lz << 20) | ((uint32_t)ly << 10) | (uint32_t)sp.lx;
-        }
       }
     }
-    __syncthreads();
-    // mark, in parallel over the queue: tiles holding an upper same-bin neighbour q of
-    // a risen boundary point p whose constraint s(q) >= s(p) + [p after q] no longer
+    // the neighbour tiles to mark: those holding an upper same-bin neighbour q of a
+    // risen boundary point p whose constraint s(q) >= s(p) + [p after q] no longer
     // holds.  q's subbin is read from the halo loaded at the start: it can only have
     // risen since, so a tile is sometimes marked when it need not be (its rerun then
     // finds every constraint held) but never missed.
+    const uint32_t mine = risen ? violated_tile_bits<G>(sv, tb, sp.lz, sp.ly0, sp.lx, sp.e0, sp.o0,
+                                                        [&](int o) { return cm[o]; },
+                                                        [&](int j) { return ((risen >> j) & 1u) != 0u; })
+                                : 0u;
+    if (mine) atomicOr(&marks, mine);
     __threadfence();  // the raised subbins are visible before any tile is marked
     __syncthreads();
-    const uint32_t nq = min(qn, (uint32_t)RS::QMAX);
-    for (uint32_t qi = threadIdx.x; qi < nq; qi += NT) {
-      const uint32_t v = queue[qi];
-      const int lz = (int)(v >> 20), ly = (int)((v >> 10) & 1023u), lx = (int)(v & 1023u);
-      const int e = G::entry(lz, ly, lx);
-      const uint32_t sf = sv[e];
-      const uint32_t pm = cm[G::lin(lz, ly, lx)];
-      const uint32_t up = (pm >> 16) & ~pm & out_of_box_bits<G>(lz, ly, lx);  // upper, outside the tile
-      const int64_t pz = tb.z0 + lz, py = tb.y0 + ly, px = tb.x0 + lx;
-#pragma unroll
-      for (int k = 0; k < 14; ++k) {
-        if (!G::HZ && dz_of(k) != 0) continue;
-        if (!((up >> k) & 1u)) continue;
-        if (sv[e + G::off(dz_of(k), dy_of(k), dx_of(k))] >= sf + (k < 7 ? 1u : 0u)) continue;
-        const int64_t qz = pz + dz_of(k), qy = py + dy_of(k), qx = px + dx_of(k);
-        const int64_t tq = ((qz / g.tz) * g.nty + qy / g.ty) * g.ntx + qx / g.tx;
-        const uint32_t r = fi.rank[tq];
-        if (!app_seg) {
-          // a plain byte store: every writer stores the same value
-          reinterpret_cast<volatile uint8_t*>(fi.dirty)[r] = 1;
-        } else {
-          // newly dirty: also offer the tile to this round
-          const uint32_t sh = 8u * (r & 3u);
-          const uint32_t old = atomicOr(&fi.dirty[r >> 2], 1u << sh);
-          if (!((old >> sh) & 0xFFu)) {
-            const unsigned pos = atomicAdd(&B->app[cls], 1u);
-            if ((int64_t)pos < ntile_cls) app_seg[pos] = (uint32_t)(fi.tile_base + tq);
-          }
+    if (threadIdx.x < 27 && ((marks >> threadIdx.x) & 1u) && nb_rank[threadIdx.x] != ~0u) {
+      const uint32_t r = nb_rank[threadIdx.x];
+      if (!app_seg) {
+        reinterpret_cast<volatile uint8_t*>(fi.dirty)[r] = 1;  // every writer stores the same value
+      } else {
+        // newly dirty: also offer the tile to this round
+        const uint32_t sh = 8u * (r & 3u);
+        const uint32_t old = atomicOr(&fi.dirty[r >> 2], 1u << sh);
+        if (!((old >> sh) & 0xFFu)) {
+          const unsigned pos = atomicAdd(&B->app[cls], 1u);
+          if ((int64_t)pos < ntile_cls) app_seg[pos] = (uint32_t)(fi.tile_base + fi.order[r]);
         }
       }
     }
@@ -1710,20 +1752,35 @@ __global__ void k_pack(const FieldInfo* __restrict__ F) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)(table_end - kHeaderBytes) / 4;
        i += (int64_t)gridDim.x * blockDim.x)
     reinterpret_cast<uint32_t*>(out + kHeaderBytes)[i] = i < m ? sizes[i] : 0u;
-  // records: one warp per record, 16-byte copies, two in flight per lane
+  // records: one warp per record, 16-byte copies, two in flight per lane; the bytes
+  // that pad a record to 16 are written as zeros (a slot holds stale bytes there)
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < m; c += warps) {
-    const uint64_t n16 = pad16(sizes[c] & kSizeMask) / 16;
+    const uint32_t len = sizes[c] & kSizeMask;
+    const uint64_t n16 = pad16(len) / 16;
+    const uint32_t rem = len & 15u;  // bytes of the record in its last 16-byte unit (0: all 16)
     const uint4* src = reinterpret_cast<const uint4*>(slots + (size_t)c * kSlotBytes);
     uint4* dst = reinterpret_cast<uint4*>(out + offs[c]);
+    auto put = [&](uint64_t j, uint4 v) {
+      if (rem && j + 1 == n16) {
+        uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int keep = (int)rem - 4 * q;
+          w[q] = keep >= 4 ? w[q] : keep <= 0 ? 0u : (w[q] & ((1u << (8 * keep)) - 1u));
+        }
+        v = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      dst[j] = v;
+    };
     uint64_t j = lane;
     for (; j + 32 < n16; j += 64) {
       const uint4 a = src[j], b = src[j + 32];
-      dst[j] = a;
-      dst[j + 32] = b;
+      put(j, a);
+      put(j + 32, b);
     }
-    if (j < n16) dst[j] = src[j];
+    if (j < n16) put(j, src[j]);
   }
 }
 

@@ -61,6 +61,25 @@ def test_stage_parity_bins_and_subbins(L, orc, name, make, mode, eb):
     assert (s_g.cpu().numpy().astype(np.uint64) == s_o).all()
 
 
+@pytest.mark.parametrize("shape,dtype", [((17, 17, 17), np.float32), ((33, 65), np.float64), ((65, 66), np.float32),
+                                         ((9, 18, 33), np.float64)])
+def test_stale_buffer_bytes_never_reach_the_stream(L, orc, shape, dtype):
+    """Fields whose edge chunks hold a point count that is not a multiple of 4, so a raw
+    record ends inside its last 16-byte unit: the padding must be zeros (as the oracle
+    writes them) even when the output and workspace hold stale bytes from earlier use."""
+    x = bumps(shape, dtype, seed=11)
+    xt = torch.from_numpy(x).cuda()
+    d = L.make_desc(tuple(x.shape), xt.dtype, L.NOA, 1e-3)
+    out = torch.full((L.compress_bound(d),), 0xCD, dtype=torch.uint8, device="cuda")
+    ws = torch.full((L.compress_workspace_size(d),), 0xAB, dtype=torch.uint8, device="cuda")
+    want = orc.compress(x, 1, 1e-3)
+    for _ in range(2):
+        st = L.compress(xt, 1e-3, L.NOA, out=out, workspace=ws)
+        assert bytes(st.cpu().numpy().tobytes()) == want
+        ws.fill_(0x5A)
+        out.fill_(0xFF)
+
+
 def test_decoder_reads_oracle_streams_after_gpu_compress(L, orc):
     x = bumps((90, 110), np.float32, seed=3)
     st = orc.compress(x, 1, 1e-3)
