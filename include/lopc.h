@@ -81,10 +81,16 @@ typedef struct {
   double eb;       /* error bound, > 0 and finite */
 } lopc_field_desc;
 
-/* Worst-case stream size in bytes for a field (0 for an invalid descriptor). */
+/* Worst-case stream size in bytes for a field (0 for an invalid descriptor): the
+ * 128-byte header, the size table of the bin and subbin records of every 16 KiB chunk
+ * (Sec. II-C), and each record at its raw size (Sec. III-C stores a record raw when
+ * coding would not shrink it), padded to 16 bytes. */
 LOPC_API size_t lopc_compress_bound(const lopc_field_desc* desc);
 
-/* Device scratch bytes that lopc_compress needs for this field (0 if invalid). */
+/* Device scratch bytes that lopc_compress needs for this field (0 if invalid): the
+ * per-point subbins and neighbour masks of the repair (Alg. 1-2, Sec. III-B), the
+ * repair's per-tile rounds state (Sec. III-D), and one record slot per chunk for
+ * the bin and subbin coders (Sec. III-C). */
 LOPC_API size_t lopc_compress_workspace_size(const lopc_field_desc* desc);
 
 /* Compresses a field (Sec. III): resolves eps (NOA: from the value range), quantizes
@@ -101,11 +107,14 @@ LOPC_API size_t lopc_compress_workspace_size(const lopc_field_desc* desc);
 LOPC_API int lopc_compress(const lopc_field_desc* desc, const void* d_x, void* d_out, size_t out_cap,
                   size_t* out_size, void* d_ws, size_t ws_size, void* stream);
 
-/* Reads the descriptor from the first 128 bytes of a stream held in HOST memory.
+/* Reads the descriptor from the first 128 bytes of a stream held in HOST memory: the
+ * field's dtype, dimensions, bound mode and eb (the inputs of the problem statement,
+ * Sec. III-A), which size the decompression's output and workspace.
  * Errors: INVALID_ARG (null), CORRUPT (bad header). */
 LOPC_API int lopc_peek(const void* h_stream, size_t n, lopc_field_desc* desc);
 
-/* Device scratch bytes that lopc_decompress needs for streams of this field. */
+/* Device scratch bytes that lopc_decompress needs for streams of this field: a status
+ * word and the byte offsets of every chunk's two records (Sec. II-C, III-C). */
 LOPC_API size_t lopc_decompress_workspace_size(const lopc_field_desc* desc);
 
 /* Decompresses a stream (Sec. III-D/E): decodes each chunk's bins and subbins and
@@ -128,9 +137,42 @@ LOPC_API int lopc_decompress(const void* d_in, size_t in_size, void* d_x, size_t
  * kernels): a larger n returns LOPC_ERR_INVALID_ARG, and its workspace size is 0. */
 #define LOPC_MAX_BATCH_FIELDS 65535
 LOPC_API size_t lopc_batch_compress_workspace_size(int n, const lopc_field_desc* descs);
+
+/* Launch plan of a batched compression (the paper compresses one field per call
+ * and has no counterpart).  Four entries per array, one per field class: 0 float32
+ * 2D, 1 float32 3D, 2 float64 2D, 3 float64 3D.  Output bytes never depend on it:
+ * the repair reaches the same least fixpoint under every schedule (Sec. III-E).
+ *   rerun_blocks_per_sm  persistent blocks per SM of the repair rounds, [1, 16];
+ *   pass_budget16        frontier evaluations a tile of the tile pass may spend, in
+ *                        sixteenths of its points, before it finishes in topological
+ *                        order, [1, 4096];
+ *   pass_dense16         same-bin neighbour pairs, in sixteenths of a full tile's
+ *                        pairs, above which a tile goes to topological order at
+ *                        once, [0, 17] (17 = never);
+ *   pass_order           order of the tile pass: 0 decided per field from its tiles'
+ *                        sampled bin spans, 1 tile index order, 2 ascending tile key.
+ * Out-of-range values are clamped. */
+typedef struct {
+  int32_t rerun_blocks_per_sm[4];
+  int32_t pass_budget16[4];
+  int32_t pass_dense16[4];
+  int32_t pass_order[4];
+} lopc_plan;
+
+/* The library's default plan, and this thread's current one (the lopc_tune_*
+ * settings, which the autotuner writes). */
+LOPC_API void lopc_plan_default(lopc_plan* plan);
+LOPC_API void lopc_plan_get(lopc_plan* plan);
+
+/* Compresses n fields (the per-field operation of lopc_compress, Sec. III) in one
+ * launch sequence.  d_x, d_out, out_cap: n entries each (host arrays of device
+ * pointers and capacities); d_out_size, d_status: DEVICE arrays of n.  plan: the
+ * launch plan, or NULL for this thread's current plan (lopc_plan_get).
+ * Errors (returned): INVALID_ARG, WORKSPACE, CUDA; per field (in d_status): OK,
+ * NONFINITE, RANGE, CAPACITY, NOT_CONVERGED. */
 LOPC_API int lopc_batch_compress(int n, const lopc_field_desc* descs, const void* const* d_x, void* const* d_out,
-                                 const size_t* out_cap, uint64_t* d_out_size, int* d_status, void* d_ws,
-                                 size_t ws_size, void* stream);
+                                 const size_t* out_cap, uint64_t* d_out_size, int* d_status,
+                                 const lopc_plan* plan, void* d_ws, size_t ws_size, void* stream);
 
 /* Decompresses n streams (descs from lopc_peek of each header) into d_x[i]; each
  * stream's status goes to the DEVICE array d_status.  Asynchronous. */
@@ -149,11 +191,12 @@ LOPC_API int lopc_batch_decompress(int n, const lopc_field_desc* descs, const vo
  *     every GPU that loads it, held until the process exits), so streams of at most
  *     lopc_noalloc_max_chunks() chunks (65536: 256 Mi float32 or 128 Mi float64
  *     points) are accepted; larger ones return LOPC_ERR_WORKSPACE before any work.
- *   - The first call on a device looks up the array's device address (one
- *     cudaGetSymbolAddress with that device current); make that first call before
- *     any stream capture.
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress); the first call on a device also loads the library's
+ *     device code there, so make that first call before any stream capture.
  *   - All calls share the array: calls whose work overlaps on the GPU (other streams,
- *     other host threads) race and must be serialised by the caller.
+ *     other host threads) race and must be serialised by the caller.  Every call,
+ *     failed ones included, returns with its work on the array finished.
  * Synchronising.  Errors: INVALID_ARG, CORRUPT, CAPACITY, WORKSPACE, CUDA. */
 LOPC_API int lopc_decompress_noalloc(const void* d_in, size_t in_size, void* d_x, size_t x_cap, void* stream);
 

@@ -4,7 +4,6 @@
 #include <stdint.h>
 #include <string.h>
 
-#include <mutex>
 #include <algorithm>
 #include <deque>
 #include <vector>
@@ -333,7 +332,37 @@ thread_local int g_pass_dense16[4] = {8, 8, 8, 8};
 // key (set by lopc_tune_set_pass_order).
 thread_local int g_pass_order[4] = {0, 0, 0, 0};
 
-int rerun_blocks(int c) { return sm_count() * g_rerun_per_sm[c]; }
+// Launch settings of one compression: the caller's lopc_plan (lopc_batch_compress),
+// else this thread's lopc_tune_* values.  Output bytes never depend on them.
+struct Tune {
+  int rerun_per_sm[4], budget16[4], dense16[4], order[4];
+};
+
+int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+Tune current_tune() {
+  Tune u;
+  for (int c = 0; c < 4; ++c) {
+    u.rerun_per_sm[c] = g_rerun_per_sm[c];
+    u.budget16[c] = g_pass_budget16[c];
+    u.dense16[c] = g_pass_dense16[c];
+    u.order[c] = g_pass_order[c];
+  }
+  return u;
+}
+
+Tune tune_of_plan(const lopc_plan& pl) {
+  Tune u;
+  for (int c = 0; c < 4; ++c) {
+    u.rerun_per_sm[c] = clampi(pl.rerun_blocks_per_sm[c], 1, 16);
+    u.budget16[c] = clampi(pl.pass_budget16[c], 1, 4096);
+    u.dense16[c] = clampi(pl.pass_dense16[c], 0, 17);
+    u.order[c] = clampi(pl.pass_order[c], 0, 2);
+  }
+  return u;
+}
+
+int rerun_blocks(const Tune& tu, int c) { return sm_count() * tu.rerun_per_sm[c]; }
 
 int launch_init(const Table& t, const FieldInfo* dF, cudaStream_t st) {
   const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (t.max_words + 255) / 256));
@@ -357,22 +386,22 @@ int launch_class_range(const Table& t, int c, const FieldInfo* dF, cudaStream_t 
 
 // The tile pass of one class's fields.
 template <typename T, int ND>
-int launch_class_pre(const Table& t, int c, const FieldInfo* dF, int fix, cudaStream_t st) {
+int launch_class_pre(const Table& t, int c, const FieldInfo* dF, const Tune& tu, int fix, cudaStream_t st) {
   using C = TileCfg<T, ND>;
   if (!t.cls_nf[c]) return LOPC_OK;
   LAUNCH("tile_pass", st,
          k_pass<T, ND><<<(unsigned)t.cls_nt[c], C::NT, PassSmem<T, ND>::bytes(), st>>>(
-             dF, t.cls_f0[c], t.cls_nf[c], t.cls_t0[c], (unsigned)g_pass_budget16[c], (unsigned)g_pass_dense16[c], fix));
+             dF, t.cls_f0[c], t.cls_nf[c], t.cls_t0[c], (unsigned)tu.budget16[c], (unsigned)tu.dense16[c], fix));
   CK(cudaGetLastError());
   return LOPC_OK;
 }
 
 template <typename T, int ND>
-int launch_class_rerun(const Table& t, int c, const FieldInfo* dF, BatchState* dB, const uint32_t* list,
-                       uint32_t* app, cudaStream_t st) {
+int launch_class_rerun(const Table& t, int c, const FieldInfo* dF, const Tune& tu, BatchState* dB,
+                       const uint32_t* list, uint32_t* app, cudaStream_t st) {
   using C = TileCfg<T, ND>;
   if (!t.cls_nf[c]) return LOPC_OK;
-  const unsigned grid = (unsigned)imin64(t.cls_nt[c], rerun_blocks(c));
+  const unsigned grid = (unsigned)imin64(t.cls_nt[c], rerun_blocks(tu, c));
   LAUNCH(list ? "tile_rerun" : "tile_rerun_all", st,
          k_rerun<T, ND><<<grid, C::NT, RerunSmem<T, ND>::bytes(), st>>>(dF, t.cls_f0[c], t.cls_nf[c], t.cls_t0[c],
                                                                        t.cls_nt[c], c, dB, list, app));
@@ -395,7 +424,7 @@ int launch_class_encode(const Table& t, int c, const FieldInfo* dF, cudaStream_t
 // and the tile pass of every field of the table (fix = 0: the pass leaves every subbin
 // at 0, for the worklist schedule).  The reruns visit each field's tiles in ascending
 // tile key, and so does the pass of a field whose tiles span few bins.
-int launch_pre(const Table& t, const FieldInfo* dF, cudaStream_t st, int fix = 1) {
+int launch_pre(const Table& t, const FieldInfo* dF, const Tune& tu, cudaStream_t st, int fix = 1) {
   int rc;
   if ((rc = launch_init(t, dF, st))) return rc;
   if ((rc = launch_class_range<float, 2>(t, 0, dF, st))) return rc;
@@ -403,28 +432,28 @@ int launch_pre(const Table& t, const FieldInfo* dF, cudaStream_t st, int fix = 1
   if ((rc = launch_class_range<double, 2>(t, 2, dF, st))) return rc;
   if ((rc = launch_class_range<double, 3>(t, 3, dF, st))) return rc;
   unsigned pass_order = 0;
-  for (int c = 0; c < 4; ++c) pass_order |= (unsigned)g_pass_order[c] << (2 * c);
+  for (int c = 0; c < 4; ++c) pass_order |= (unsigned)tu.order[c] << (2 * c);
   LAUNCH("order", st, k_order<1024><<<t.n(), 1024, 0, st>>>(dF, pass_order));
   LAUNCH("clear_subbins", st, k_clear_subbins<<<dim3(sm_count() * 2, t.n()), 256, 0, st>>>(dF));
   CK(cudaGetLastError());
-  if ((rc = launch_class_pre<float, 2>(t, 0, dF, fix, st))) return rc;
-  if ((rc = launch_class_pre<float, 3>(t, 1, dF, fix, st))) return rc;
-  if ((rc = launch_class_pre<double, 2>(t, 2, dF, fix, st))) return rc;
-  return launch_class_pre<double, 3>(t, 3, dF, fix, st);
+  if ((rc = launch_class_pre<float, 2>(t, 0, dF, tu, fix, st))) return rc;
+  if ((rc = launch_class_pre<float, 3>(t, 1, dF, tu, fix, st))) return rc;
+  if ((rc = launch_class_pre<double, 2>(t, 2, dF, tu, fix, st))) return rc;
+  return launch_class_pre<double, 3>(t, 3, dF, tu, fix, st);
 }
 
 // One rerun round: of every tile (list == null, the first round) or of the listed ones.
 // app (total_tiles entries, or null: no appends) receives the tiles reruns mark, for
 // the round in progress to take.
-int launch_reruns(const Table& t, const FieldInfo* dF, BatchState* dB, const uint32_t* list, uint32_t* app,
-                  cudaStream_t st) {
+int launch_reruns(const Table& t, const FieldInfo* dF, const Tune& tu, BatchState* dB, const uint32_t* list,
+                  uint32_t* app, cudaStream_t st) {
   int rc;
   if (!list) CK(cudaMemsetAsync(dB->next_all, 0, sizeof(dB->next_all), st));  // the all-tile round's counters
   if (!list && app) CK(cudaMemsetAsync(dB->app, 0, sizeof(dB->app), st));
-  if ((rc = launch_class_rerun<float, 2>(t, 0, dF, dB, list, app, st))) return rc;
-  if ((rc = launch_class_rerun<float, 3>(t, 1, dF, dB, list, app, st))) return rc;
-  if ((rc = launch_class_rerun<double, 2>(t, 2, dF, dB, list, app, st))) return rc;
-  return launch_class_rerun<double, 3>(t, 3, dF, dB, list, app, st);
+  if ((rc = launch_class_rerun<float, 2>(t, 0, dF, tu, dB, list, app, st))) return rc;
+  if ((rc = launch_class_rerun<float, 3>(t, 1, dF, tu, dB, list, app, st))) return rc;
+  if ((rc = launch_class_rerun<double, 2>(t, 2, dF, tu, dB, list, app, st))) return rc;
+  return launch_class_rerun<double, 3>(t, 3, dF, tu, dB, list, app, st);
 }
 
 int launch_compact(const Table& t, FieldInfo* dF, uint32_t* list, BatchState* dB, unsigned int* field_counts,
@@ -457,6 +486,7 @@ struct CompressPlan {
   Table t;
   std::vector<int> order;  // position in the table -> caller's index
   bool worklist = false;   // one field, repaired by the worklist schedule
+  Tune tu;                 // launch settings (lopc_plan or this thread's tuning)
   size_t off_state = 0, off_table = 0, off_results = 0, off_list = 0, off_app = 0;
   size_t off_wl_state = 0, off_stamp = 0, off_wl = 0;
   std::vector<size_t> off_field;
@@ -469,6 +499,7 @@ int plan_compress(int n, const lopc_field_desc* descs, const void* const* xs, vo
                   bool worklist = false) {
   p = CompressPlan{};  // planning twice (size, then pointers) must not accumulate
   p.worklist = worklist && n == 1;
+  p.tu = current_tune();
   p.order.resize(n);
   for (int i = 0; i < n; ++i) p.order[i] = i;
   std::stable_sort(p.order.begin(), p.order.end(), [&](int a, int b) {
@@ -534,8 +565,6 @@ Ptrs ptrs_of(const CompressPlan& p, uint8_t* ws) {
   return q;
 }
 
-// Everything before the repair loop: state reset, range, eps, tile pass, the first
-// (all-tile) rerun round and its compaction.
 // The worklist schedule: launches of one iteration and of its swap.
 int launch_wl(const CompressPlan& p, const Ptrs& q, uint8_t* ws, int all, cudaStream_t st,
               cudaGraphConditionalHandle h, int use_h) {
@@ -548,6 +577,8 @@ int launch_wl(const CompressPlan& p, const Ptrs& q, uint8_t* ws, int all, cudaSt
   return LOPC_OK;
 }
 
+// Everything before the repair loop: state reset, range, eps, tile pass, the first
+// (all-tile) rerun round and its compaction.
 int enqueue_prologue(const CompressPlan& p, const Ptrs& q, cudaStream_t st, cudaGraphConditionalHandle h, int use_h) {
   int rc;
   CK(cudaMemsetAsync(q.B, 0, sizeof(BatchState), st));
@@ -556,18 +587,18 @@ int enqueue_prologue(const CompressPlan& p, const Ptrs& q, cudaStream_t st, cuda
     const size_t npts = (size_t)(p.t.F[0].g.nz * p.t.F[0].g.ny * p.t.F[0].g.nx);
     CK(cudaMemsetAsync(ws + p.off_wl_state, 0, sizeof(WorklistState), st));
     CK(cudaMemsetAsync(ws + p.off_stamp, 0, 4 * npts, st));
-    if ((rc = launch_pre(p.t, q.F, st, 0))) return rc;
+    if ((rc = launch_pre(p.t, q.F, p.tu, st, 0))) return rc;
     return launch_wl(p, q, ws, 1, st, h, use_h);
   }
-  if ((rc = launch_pre(p.t, q.F, st))) return rc;
-  if ((rc = launch_reruns(p.t, q.F, q.B, nullptr, q.app, st))) return rc;
+  if ((rc = launch_pre(p.t, q.F, p.tu, st))) return rc;
+  if ((rc = launch_reruns(p.t, q.F, p.tu, q.B, nullptr, q.app, st))) return rc;
   return launch_compact(p.t, q.F, q.list, q.B, nullptr, h, use_h, st);
 }
 
 int enqueue_loop_body(const CompressPlan& p, const Ptrs& q, cudaStream_t st, cudaGraphConditionalHandle h, int use_h) {
   int rc;
   if (p.worklist) return launch_wl(p, q, reinterpret_cast<uint8_t*>(q.B) - p.off_state, 0, st, h, use_h);
-  if ((rc = launch_reruns(p.t, q.F, q.B, q.list, q.app, st))) return rc;
+  if ((rc = launch_reruns(p.t, q.F, p.tu, q.B, q.list, q.app, st))) return rc;
   return launch_compact(p.t, q.F, q.list, q.B, nullptr, h, use_h, st);
 }
 
@@ -687,8 +718,8 @@ std::vector<uint64_t> plan_key(const CompressPlan& p, const uint8_t* ws) {
   k.push_back((uint64_t)(uintptr_t)ws);
   k.push_back((uint64_t)p.t.n() | ((uint64_t)p.worklist << 32));
   for (int c = 0; c < 4; ++c)
-    k.push_back((uint64_t)rerun_blocks(c) | ((uint64_t)g_pass_budget16[c] << 20) | ((uint64_t)g_pass_dense16[c] << 40) |
-                ((uint64_t)g_pass_order[c] << 56));
+    k.push_back((uint64_t)rerun_blocks(p.tu, c) | ((uint64_t)p.tu.budget16[c] << 20) |
+                ((uint64_t)p.tu.dense16[c] << 40) | ((uint64_t)p.tu.order[c] << 56));
   for (const FieldInfo& f : p.t.F) {
     const uint64_t* w = reinterpret_cast<const uint64_t*>(&f);
     for (size_t i = 0; i < sizeof(FieldInfo) / 8; ++i) k.push_back(w[i]);
@@ -912,8 +943,8 @@ int decompress_one(const void* d_in, size_t in_size, void* d_x, size_t x_cap, ui
   int rc = parse_header(hb, in_size, &H);
   if (rc) return rc;
   const Geometry g = geometry_of(&H.d);
+  if (H.total > in_size) return LOPC_ERR_CORRUPT;  // a truncated stream is corrupt, whatever it declares
   if (max_chunks && (size_t)g.ntiles > max_chunks) return LOPC_ERR_WORKSPACE;  // beyond a fixed scratch
-  if (H.total > in_size) return LOPC_ERR_CORRUPT;
   const size_t need = (size_t)(g.nz * g.ny * g.nx) * word_bytes(H.d.dtype);
   if (x_cap < need) return LOPC_ERR_CAPACITY;
   DecompressPlan p;
@@ -1051,6 +1082,7 @@ int engine_upload(lopc_engine* e, int which, const Table& t, cudaStream_t st) {
 
 int engine_step(lopc_engine* e, int rounds, int* active) {
   int rc;
+  const Tune tu = current_tune();
   const bool round = !e->running.empty();
   Table tr;
   if (round) {
@@ -1067,17 +1099,17 @@ int engine_step(lopc_engine* e, int rounds, int* active) {
         CK(cudaMemcpyAsync(e->hcounts, e->dcounts, 4 * (size_t)tr.n(), cudaMemcpyDeviceToHost, e->sm));
         CK(cudaEventRecord(e->ev_counts, e->sm));
       }
-      if ((rc = launch_reruns(tr, e->dT[0], e->dB, e->dlist, e->dapp, e->sm))) return rc;
+      if ((rc = launch_reruns(tr, e->dT[0], tu, e->dB, e->dlist, e->dapp, e->sm))) return rc;
     }
   }
   if (!e->fresh.empty()) {
     Table ta;
     engine_table(e->fresh, ta);
     if ((rc = engine_upload(e, 1, ta, e->sa))) return rc;
-    if ((rc = launch_pre(ta, e->dT[1], e->sa))) return rc;
+    if ((rc = launch_pre(ta, e->dT[1], tu, e->sa))) return rc;
     // no appends here: this round runs beside the running fields' round, which owns
     // the append counters
-    if ((rc = launch_reruns(ta, e->dT[1], e->dB, nullptr, nullptr, e->sa))) return rc;
+    if ((rc = launch_reruns(ta, e->dT[1], tu, e->dB, nullptr, nullptr, e->sa))) return rc;
     CK(cudaEventRecord(e->ev_pro, e->sa));
     e->pro_pending = true;
   }
@@ -1250,8 +1282,8 @@ int lopc_compress(const lopc_field_desc* d, const void* d_x, void* d_out, size_t
 }
 
 int lopc_batch_compress(int n, const lopc_field_desc* descs, const void* const* d_x, void* const* d_out,
-                        const size_t* out_cap, uint64_t* d_out_size, int* d_status, void* d_ws, size_t ws_size,
-                        void* stream) {
+                        const size_t* out_cap, uint64_t* d_out_size, int* d_status, const lopc_plan* plan,
+                        void* d_ws, size_t ws_size, void* stream) {
   if (n <= 0 || n > LOPC_MAX_BATCH_FIELDS || !descs || !d_x || !d_out || !out_cap || !d_out_size || !d_status)
     return LOPC_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i)
@@ -1260,6 +1292,7 @@ int lopc_batch_compress(int n, const lopc_field_desc* descs, const void* const* 
   plan_compress(n, descs, d_x, d_out, out_cap, d_out_size, d_status, nullptr, nullptr, p);
   if (!d_ws || ws_size < p.ws_total) return LOPC_ERR_WORKSPACE;
   plan_compress(n, descs, d_x, d_out, out_cap, d_out_size, d_status, nullptr, reinterpret_cast<uint8_t*>(d_ws), p);
+  if (plan) p.tu = tune_of_plan(*plan);
   const int rc = run_compress(p, reinterpret_cast<uint8_t*>(d_ws), reinterpret_cast<cudaStream_t>(stream));
   if (g_prof.on) {
     (void)cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
@@ -1328,35 +1361,30 @@ constexpr size_t kNoAllocScratchBytes = 256 + 16 * (size_t)kNoAllocMaxChunks;  /
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
 
 namespace {
-constexpr int kNoAllocMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kNoAllocMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once per
-// device.  In host code the array's name is only a stand-in, so the address must
-// come from cudaGetSymbolAddress with that device current.
+// Device address of the scratch array on the current device.  In host code the
+// array's name is only a stand-in, so the address comes from cudaGetSymbolAddress
+// with that device current.  It is looked up on every call (cheap next to the
+// synchronous header read), so a device reset between calls cannot leave a stale
+// address behind.
 int noalloc_scratch(uint8_t** out) {
-  int dev = -1;
-  CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kNoAllocMaxDevices) return LOPC_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_addr[dev] = p;
-  }
-  *out = reinterpret_cast<uint8_t*>(g_noalloc_addr[dev]);
+  void* p = nullptr;
+  CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  *out = reinterpret_cast<uint8_t*>(p);
   return LOPC_OK;
 }
 }  // namespace
 
 int lopc_decompress_noalloc(const void* d_in, size_t in_size, void* d_x, size_t x_cap, void* stream) {
   uint8_t* ws = nullptr;
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int rc = noalloc_scratch(&ws);
   // every offset the decoder reads is rewritten and its status word zeroed first
-  if (!rc)
-    rc = decompress_one(d_in, in_size, d_x, x_cap, ws, kNoAllocScratchBytes, reinterpret_cast<cudaStream_t>(stream),
-                        (size_t)kNoAllocMaxChunks);
+  if (!rc) {
+    rc = decompress_one(d_in, in_size, d_x, x_cap, ws, kNoAllocScratchBytes, st, (size_t)kNoAllocMaxChunks);
+    // an error can come after work was queued on the shared scratch: wait for it, so
+    // that every call returns with the scratch idle
+    if (rc) (void)cudaStreamSynchronize(st);
+  }
   g_prof.resolve();
   return rc;
 }
@@ -1458,6 +1486,29 @@ const char* lopc_strerror(int s) {
   }
 }
 
+
+void lopc_plan_get(lopc_plan* pl) {
+  if (!pl) return;
+  memset(pl, 0, sizeof(*pl));
+  const Tune u = current_tune();
+  for (int c = 0; c < 4; ++c) {
+    pl->rerun_blocks_per_sm[c] = u.rerun_per_sm[c];
+    pl->pass_budget16[c] = u.budget16[c];
+    pl->pass_dense16[c] = u.dense16[c];
+    pl->pass_order[c] = u.order[c];
+  }
+}
+
+void lopc_plan_default(lopc_plan* pl) {
+  if (!pl) return;
+  memset(pl, 0, sizeof(*pl));
+  for (int c = 0; c < 4; ++c) {
+    pl->rerun_blocks_per_sm[c] = c < 2 ? 3 : 6;
+    pl->pass_budget16[c] = 64;
+    pl->pass_dense16[c] = 8;
+    pl->pass_order[c] = 0;
+  }
+}
 
 void lopc_tune_set(const int* v) {
   if (!v) return;

@@ -57,6 +57,36 @@ class VerifyReport(C.Structure):
                 ("psnr", C.c_double), ("eps", C.c_double), ("bound_ok", C.c_int32), ("reserved", C.c_int32)]
 
 
+class Plan(C.Structure):
+    """lopc_plan: launch settings of a batched compression, per field class (0 f32 2D,
+    1 f32 3D, 2 f64 2D, 3 f64 3D).  Output bytes never depend on them."""
+    _fields_ = [("rerun_blocks_per_sm", C.c_int32 * 4), ("pass_budget16", C.c_int32 * 4),
+                ("pass_dense16", C.c_int32 * 4), ("pass_order", C.c_int32 * 4)]
+
+    def as_dict(self) -> dict:
+        return {k: list(getattr(self, k)) for k, _ in self._fields_}
+
+    @classmethod
+    def of(cls, d: dict) -> "Plan":
+        p = cls()
+        for k, _ in cls._fields_:
+            setattr(p, k, (C.c_int32 * 4)(*[int(v) for v in d[k]]))
+        return p
+
+
+def plan_default() -> Plan:
+    p = Plan()
+    lib().lopc_plan_default(C.byref(p))
+    return p
+
+
+def plan_get() -> Plan:
+    """This thread's current plan (the lopc_tune_* settings)."""
+    p = Plan()
+    lib().lopc_plan_get(C.byref(p))
+    return p
+
+
 def lib():
     """Loads ``liblopc.so`` (raises if it has not been built)."""
     global _lib
@@ -78,7 +108,11 @@ def lib():
         L.lopc_noalloc_max_chunks.restype = C.c_int64
         L.lopc_batch_compress_workspace_size.argtypes = [C.c_int, D]
         L.lopc_batch_compress_workspace_size.restype = C.c_size_t
-        L.lopc_batch_compress.argtypes = [C.c_int, D, P, P, P, P, P, P, C.c_size_t, P]
+        L.lopc_batch_compress.argtypes = [C.c_int, D, P, P, P, P, P, C.POINTER(Plan), P, C.c_size_t, P]
+        L.lopc_plan_default.argtypes = [C.POINTER(Plan)]
+        L.lopc_plan_default.restype = None
+        L.lopc_plan_get.argtypes = [C.POINTER(Plan)]
+        L.lopc_plan_get.restype = None
         L.lopc_batch_decompress_workspace_size.argtypes = [C.c_int, D]
         L.lopc_batch_decompress_workspace_size.restype = C.c_size_t
         L.lopc_batch_decompress.argtypes = [C.c_int, D, P, P, P, P, P, C.c_size_t, P]
@@ -414,7 +448,8 @@ class BatchCompress:
     """A reusable batched compression of fixed fields (inputs, outputs, workspace
     and result arrays stay allocated, so repeated launches replay one cached graph)."""
 
-    def __init__(self, fields, ebs, modes=None, device=None):
+    def __init__(self, fields, ebs, modes=None, device=None, plan: Optional[Plan] = None):
+        self.plan = plan
         self.fields = [f.contiguous() for f in fields]
         n = len(self.fields)
         modes = modes if modes is not None else [NOA] * n
@@ -430,10 +465,13 @@ class BatchCompress:
         self._o = (C.c_void_p * n)(*[o.data_ptr() for o in self.outs])
         self._c = (C.c_size_t * n)(*self.caps)
 
-    def launch(self, stream=None) -> None:
-        """Enqueues the batch on the stream (asynchronous)."""
+    def launch(self, stream=None, plan: Optional[Plan] = None) -> None:
+        """Enqueues the batch on the stream (asynchronous).  ``plan`` (else the one
+        given at construction, else this thread's current plan) sets the launches."""
+        pl = plan if plan is not None else self.plan
         rc = lib().lopc_batch_compress(len(self.fields), self._d, self._x, self._o, self._c,
                                        C.c_void_p(self.sizes.data_ptr()), C.c_void_p(self.status.data_ptr()),
+                                       C.byref(pl) if pl is not None else None,
                                        C.c_void_p(self.ws.data_ptr()), self.ws.numel(), C.c_void_p(_stream(stream)))
         _check(rc, "lopc_batch_compress")
 
@@ -444,8 +482,8 @@ class BatchCompress:
         return [o[:n] for o, n in zip(self.outs, sizes)], st
 
 
-def batch_compress(fields, ebs, modes=None, stream=None):
-    b = BatchCompress(fields, ebs, modes)
+def batch_compress(fields, ebs, modes=None, stream=None, plan: Optional[Plan] = None):
+    b = BatchCompress(fields, ebs, modes, plan=plan)
     b.launch(stream)
     torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
     return b.results()

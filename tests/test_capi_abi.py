@@ -133,8 +133,25 @@ def test_batch_field_limit(L):
     descs = (type(d) * n)(*([d] * n))
     ptrs = (C.c_void_p * n)(*([1] * n))
     caps = (C.c_size_t * n)(*([4096] * n))
-    rc = lib.lopc_batch_compress(n, descs, ptrs, ptrs, caps, C.c_void_p(1), C.c_void_p(1), C.c_void_p(1), 1 << 40, None)
-    assert rc == -1
+    plan = L.plan_default()
+    for pl in (None, C.byref(plan)):
+        rc = lib.lopc_batch_compress(n, descs, ptrs, ptrs, caps, C.c_void_p(1), C.c_void_p(1), pl, C.c_void_p(1),
+                                     1 << 40, None)
+        assert rc == -1
+
+
+def test_plan_default_and_current(L):
+    """lopc_plan: the defaults, and the thread's current plan following lopc_tune_*."""
+    d = L.plan_default().as_dict()
+    assert d == {"rerun_blocks_per_sm": [3, 3, 6, 6], "pass_budget16": [64] * 4, "pass_dense16": [8] * 4,
+                 "pass_order": [0] * 4}
+    saved = L.tune_get()
+    try:
+        L.tune_set([2, 5, 7, 9])
+        assert L.plan_get().as_dict()["rerun_blocks_per_sm"] == [2, 5, 7, 9]
+        assert L.Plan.of(d).as_dict() == d
+    finally:
+        L.tune_set(saved)
 
 
 def test_fixpoint_work_reports_seven_values(L):

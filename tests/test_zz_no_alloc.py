@@ -51,6 +51,16 @@ def test_noalloc_rejects_streams_beyond_its_scratch(L):
     nx = 64 * (max_chunks + 1)                      # one chunk more than the scratch holds
     hdr[16:24] = nx.to_bytes(8, "little")
     hdr[80:88] = (max_chunks + 1).to_bytes(8, "little")
-    dev = torch.frombuffer(hdr, dtype=torch.uint8).cuda()
     out = torch.empty(16, dtype=torch.float32, device="cuda")
+    # the header declares more bytes than the 128 passed: a truncated stream is
+    # reported as corrupt before its chunk count is looked at
+    dev = torch.frombuffer(bytearray(hdr), dtype=torch.uint8).cuda()
+    assert L.decompress_noalloc(dev, out) == -5     # LOPC_ERR_CORRUPT
+    hdr[88:96] = (128).to_bytes(8, "little")        # a stream that claims to be whole
+    dev = torch.frombuffer(hdr, dtype=torch.uint8).cuda()
     assert L.decompress_noalloc(dev, out) == -8     # LOPC_ERR_WORKSPACE
+    # the scratch is idle after a failed call: a good stream decodes right after
+    ok = torch.empty_like(x)
+    assert L.decompress_noalloc(st, ok) == 0
+    torch.cuda.synchronize()
+    assert ok.cpu().numpy().tobytes() == L.decompress(st).cpu().numpy().tobytes()
