@@ -35,11 +35,35 @@ sys.path.insert(0, ROOT)
 
 METRIC = "compress/decompress GB/s (1 B300, bit-exact) & % HBM peak; batched vs per-field; p50/p99"
 
-# DRAM bytes (read + write) of one tile-pass launch on the headline workload (512^3
-# f32, NOA 1e-3, the pass in tile index order), from the ncu capture in
-# profiles/launches_3d_f32_512_noa1e-3.md; None whenever k_pass has changed since it
-# was captured, and reported only for that workload and order.
-PASS_TRAFFIC = 542665216 + 1064044288
+# Per-launch DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# library's kernels on the headline workload, from an ncu capture, with the hash of
+# the library sources that capture ran.  The roofline's `traffic` is taken from it
+# only while the sources still hash the same (else null: the counters are stale).
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "dram_traffic_3d_f32_512_noa1e-3.json")
+
+
+def library_source_sha256() -> str:
+    """SHA-256 over the CUDA library's sources (kernels, C ABI and header)."""
+    import hashlib
+    from paper_2603_26968_b300 import build
+    h = hashlib.sha256()
+    for p in build.sources():
+        h.update(p.name.encode())
+        h.update(p.read_bytes())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str, workload: str):
+    """Captured DRAM bytes per launch of `kernel` on `workload`, or None."""
+    try:
+        with open(TRAFFIC_JSON) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_sha256") != library_source_sha256() or d.get("workload") != workload:
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return int(k["dram_bytes_read"]) + int(k["dram_bytes_write"]) if k else None
 
 
 def peaks():
@@ -126,16 +150,47 @@ def make_batch_field(spec):
     return S.make_field(spec)
 
 
-def cpu_oracle_sample(x: np.ndarray, eb: float, sub: int):
-    """Oracle compress + decompress of the central sub^3 block (bounded CPU work)."""
+def cpu_oracle_sample(x: np.ndarray, eb: float, sub: int, openmp: bool = False):
+    """Oracle compress + decompress of the central sub^3 block (bounded CPU work):
+    the single-threaded build, or its OpenMP build on every host core.  Returns the
+    block's bytes, the seconds and the stream."""
     import oracle
     c = [(s - sub) // 2 for s in x.shape]
     blk = np.ascontiguousarray(x[c[0]:c[0] + sub, c[1]:c[1] + sub, c[2]:c[2] + sub])
     t0 = time.perf_counter()
-    st = oracle.compress(blk, 1, eb)
-    oracle.decompress(st)
+    st = oracle.compress(blk, 1, eb, openmp=openmp)
+    oracle.decompress(st, openmp=openmp)
     dt = time.perf_counter() - t0
-    return blk.nbytes, dt, len(st)
+    return blk.nbytes, dt, st
+
+
+def host_cpu() -> dict:
+    """The host's CPU model and core count, for the baselines."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count() or 1}
+
+
+def cpu_baselines(x: np.ndarray, eb: float, sub: int) -> dict:
+    """The oracle on the machine's host cores: its OpenMP build on every core (the
+    reported value) and its single-threaded build, on the same block; both must give
+    the same bytes."""
+    import oracle
+    nb, dt1, st1 = cpu_oracle_sample(x, eb, sub, openmp=False)
+    _, dtn, stn = cpu_oracle_sample(x, eb, sub, openmp=True)
+    hc = host_cpu()
+    return {"value": nb / dtn / 1e9, "unit": "GB/s", "cores": oracle.omp_threads(), "kind": "oracle",
+            "sample": f"central {sub}^3 block of the field, compress+decompress, OpenMP build (chunks and "
+                      f"points split over threads; the repair's sort and pass sequential)",
+            "single_thread": {"value": nb / dt1 / 1e9, "unit": "GB/s", "cores": 1},
+            "identical_bytes": st1 == stn, **hc}
 
 
 def workload_config(args, nbytes: int, world: int) -> dict:
@@ -149,13 +204,14 @@ def workload_config(args, nbytes: int, world: int) -> dict:
 def run_reference(args, rank):
     if rank != 0:
         return
+    import oracle
     x = make_headline(args.size, seed=1)
     sub = args.cpu_sample
     for _ in range(args.warmup):
-        cpu_oracle_sample(x, args.eb, sub)
+        cpu_oracle_sample(x, args.eb, sub, openmp=True)
     tot_b, tot_t = 0, 0.0
     for _ in range(args.steps):
-        nb, dt, _ = cpu_oracle_sample(x, args.eb, sub)
+        nb, dt, _ = cpu_oracle_sample(x, args.eb, sub, openmp=True)
         tot_b += nb
         tot_t += dt
     gbs = tot_b / tot_t / 1e9
@@ -164,8 +220,9 @@ def run_reference(args, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(args, x.nbytes, 1),
-        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"central {sub}^3 block of the field, compress+decompress, single thread"},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": oracle.omp_threads(), "kind": "oracle",
+                         "sample": f"central {sub}^3 block of the field, compress+decompress, OpenMP build "
+                                   f"on every host core", **host_cpu()},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -180,7 +237,6 @@ def batch_leg(torch, lopc, fields_np, specs, flush, args):
     xs = [torch.from_numpy(a).to(dev) for a in fields_np]
     ebs = [float(s.eb) for s in specs]
     nbytes = sum(a.nbytes for a in fields_np)
-    default = lopc.tune_get()
     singles = [lopc.BatchCompress([x], [e]) for x, e in zip(xs, ebs)]
     batch = lopc.BatchCompress(xs, ebs)
     st = torch.cuda.current_stream()
@@ -201,41 +257,52 @@ def batch_leg(torch, lopc, fields_np, specs, flush, args):
             out.append(a.elapsed_time(b))
         return float(np.median(out))
 
+    default_plan = lopc.plan_default()
     run_singles()
-    batch.launch()
+    batch.launch(plan=default_plan)
     torch.cuda.synchronize()
     per_field_ms = timed(run_singles, args.batch_reps)
-    batch_default_ms = timed(batch.launch, args.batch_reps)
+    batch_default_ms = timed(lambda: batch.launch(plan=default_plan), args.batch_reps)
     key = autotune.device_key(batch.descs)
     tuned = autotune.load(key) if not args.retune else None
+    trials = None
     if tuned is None:
-        tuned = autotune.tune(batch.launch, autotune.classes_of(batch.descs), reps=args.batch_reps)
+        tuned = autotune.tune(lambda pl: batch.launch(plan=pl), autotune.classes_of(batch.descs),
+                              reps=args.batch_reps, flush=flush)
+        trials = tuned["trials"]
         try:
             autotune.save(key, {k: v for k, v in tuned.items() if k != "trials"})
         except OSError:
             pass
-    lopc.tune_set(tuned["rerun_blocks_per_sm"])
-    batch.launch()
+    tuned_plan = lopc.Plan.of(tuned["plan"])
+    batch.launch(plan=tuned_plan)
     torch.cuda.synchronize()
-    batch_ms = timed(batch.launch, args.batch_reps)
+    batch_ms = timed(lambda: batch.launch(plan=tuned_plan), args.batch_reps)
     # identical output: every field's batched stream equals its own launch's stream
     bs, bst = batch.results()
     identical = all(s == 0 for s in bst)
     for b, s in zip(singles, bs):
         o, ss = b.results()
         identical = identical and ss[0] == 0 and torch.equal(o[0], s)
-    lopc.tune_set(default)
     del singles, batch, xs
     torch.cuda.empty_cache()
     classes = autotune.signature([lopc.make_desc(s.shape, s.dtype, lopc.NOA, s.eb) for s in specs])
-    return {"fields": len(specs), "bytes": int(nbytes), "class_signature": classes,
-            "per_field_ms": per_field_ms, "per_field_gbs": nbytes / (per_field_ms * 1e-3) / 1e9,
-            "batched_default_ms": batch_default_ms, "batched_ms": batch_ms,
-            "batched_gbs": nbytes / (batch_ms * 1e-3) / 1e9, "speedup": per_field_ms / batch_ms,
-            "tuned_rerun_blocks_per_sm": tuned["rerun_blocks_per_sm"], "default_rerun_blocks_per_sm": list(default),
-            "identical_output": bool(identical),
-            "timing": f"median of {args.batch_reps}, L2 flushed before each; per-field = one async launch "
-                      f"sequence (cached graph) per field back to back on one stream"}
+    out = {"fields": len(specs), "bytes": int(nbytes), "class_signature": classes,
+           "per_field_ms": per_field_ms, "per_field_gbs": nbytes / (per_field_ms * 1e-3) / 1e9,
+           "batched_default_ms": batch_default_ms, "batched_ms": batch_ms,
+           "batched_gbs": nbytes / (batch_ms * 1e-3) / 1e9, "speedup": per_field_ms / batch_ms,
+           "tuned_vs_default": batch_default_ms / batch_ms,
+           "tuned_plan": tuned["plan"], "default_plan": default_plan.as_dict(),
+           "tuner_default_spread_ms": tuned.get("default_spread_ms"),
+           "identical_output": bool(identical),
+           "timing": f"median of {args.batch_reps}, L2 flushed before each; per-field = one async launch "
+                     f"sequence (cached graph) per field back to back on one stream"}
+    if trials is not None:
+        out["tuner_trials"] = len(trials)
+        out["tuner_best_by_knob"] = {
+            k: min((t["ms"], t["cls"], t["value"]) for t in trials if t.get("knob") == k)
+            for k in autotune.KNOBS if any(t.get("knob") == k for t in trials)}
+    return out
 
 
 def configs_leg(torch, lopc, fields, flush, steps, warmup):
@@ -633,8 +700,7 @@ def main():
         achieved = bytes_per_launch / (kern[dom]["ms_per_launch"] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm,
-                "traffic": PASS_TRAFFIC if dom == "tile_pass" and args.size == 512 and args.eb == 1e-3
-                and not work.get("pass_ordered") else None,
+                "traffic": measured_traffic(dom, f"3d_f32_{args.size} NOA {args.eb:g}"),
                 "peak_kind": f"{peak_kind} (copy)", "algorithmic_bytes_per_launch": bytes_per_launch,
                 "timing": "CUDA events around each launch on its stream, in a second pass of the same workload"}
     launches_per_step = sum(v["launches_per_step"] for v in kern.values())
@@ -681,9 +747,7 @@ def main():
     value = replicas.whole_job_gbs(nbytes, world, ms_step)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        nb, dt, _ = cpu_oracle_sample(x_np, args.eb, args.cpu_sample)
-        cpu = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": f"central {args.cpu_sample}^3 block of the field, compress+decompress, single thread"}
+        cpu = cpu_baselines(x_np, args.eb, args.cpu_sample)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,

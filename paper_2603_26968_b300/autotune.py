@@ -1,14 +1,22 @@
 """Launch autotuner for batched compression.
 
-The tunable is the number of persistent rerun blocks per SM for each field class
-(f32 2D, f32 3D, f64 2D, f64 3D): it sets how a repair round's tile list is spread
-over the GPU, the round schedule of a batch.  The chunk geometry (the tile that is
-also the stream's chunk) is part of the format and never tuned.  Output bytes do not
-depend on the tunables, so the tuner only times.
+It searches the launch plan (``lopc_plan``) of a batch, per field class (f32 2D, f32
+3D, f64 2D, f64 3D):
+  - rerun_blocks_per_sm: how a repair round's tile list is spread over the GPU;
+  - pass_order: the order in which the tile pass takes a field's tiles (by the
+    field's sampled bin span, tile index, or ascending tile key), which decides how
+    much chain work the pass does and how many repair rounds follow;
+  - pass_budget16 and pass_dense16: when a tile's fixpoint leaves its frontier
+    sweeps for the topological order.
+The chunk geometry (the tile that is also the stream's chunk) is part of the format
+and never tuned.  Output bytes do not depend on the plan (the repair's result is the
+unique least fixpoint, Sec. III-E), so the tuner only times.
 
-Search: coordinate descent over the classes present in the workload, each trial
-timed with CUDA events (median of `reps`); results are cached in a JSON file keyed
-by device name and workload signature.
+Search: coordinate descent over (knob, class) for the classes present, starting
+from the library's default plan.  Each trial passes its plan to the batch
+explicitly, runs once untimed (graph capture), then is timed with CUDA events
+(median of ``reps``, L2 flushed before each).  Results are cached in a JSON file
+keyed by device name and workload signature.
 """
 from __future__ import annotations
 
@@ -22,7 +30,12 @@ import torch
 
 from . import lopc
 
-CANDIDATES = (1, 2, 3, 4, 6, 8)
+KNOBS = {
+    "pass_order": (0, 1, 2),
+    "rerun_blocks_per_sm": (1, 2, 3, 4, 6, 8),
+    "pass_dense16": (4, 8, 12, 17),
+    "pass_budget16": (16, 64, 256, 4096),
+}
 DEFAULT_CACHE = Path(__file__).resolve().parent / "tuned.json"
 
 
@@ -41,42 +54,61 @@ def classes_of(descs: Iterable) -> List[int]:
     return sorted({(2 if d.dtype == lopc.F64 else 0) + (1 if d.ndim == 3 else 0) for d in descs})
 
 
-def time_ms(run: Callable[[], None], reps: int = 3) -> float:
+def time_ms(run: Callable[[], None], reps: int = 3, flush: Optional[torch.Tensor] = None) -> List[float]:
+    """CUDA-event times of `reps` runs on the current stream, L2 flushed before each
+    (a write of `flush`, a buffer larger than L2) when given."""
     st = torch.cuda.current_stream()
     out = []
     for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(st)
         run()
         b.record(st)
         b.synchronize()
         out.append(a.elapsed_time(b))
-    return float(np.median(out))
+    return out
 
 
-def tune(run: Callable[[], None], classes: Sequence[int], candidates: Sequence[int] = CANDIDATES,
-         reps: int = 3) -> Dict:
-    """Coordinate descent over the rerun blocks per SM of the given classes; leaves
-    the best setting active and returns it with the trial log."""
-    best = list(lopc.tune_get())
-    lopc.tune_set(best)
-    run()                                          # warm: graphs captured, clocks up
-    best_ms = time_ms(run, reps)
-    trials = [{"setting": list(best), "ms": best_ms}]
-    for c in classes:
-        for v in candidates:
-            if v == best[c]:
-                continue
-            cand = list(best)
-            cand[c] = v
-            lopc.tune_set(cand)
-            run()
-            ms = time_ms(run, reps)
-            trials.append({"setting": cand, "ms": ms})
-            if ms < best_ms:
-                best, best_ms = cand, ms
-    lopc.tune_set(best)
-    return {"rerun_blocks_per_sm": best, "ms": best_ms, "trials": trials}
+def tune(run: Callable[[lopc.Plan], None], classes: Sequence[int], reps: int = 3,
+         flush: Optional[torch.Tensor] = None, knobs: Dict[str, Sequence[int]] = KNOBS) -> Dict:
+    """Coordinate descent over the plan's knobs for the given classes.  `run(plan)`
+    enqueues one batch with that plan.  Returns the best plan (as a dict), its time,
+    the default plan's time and spread, and the trial log."""
+    def trial(d: dict) -> List[float]:
+        pl = lopc.Plan.of(d)
+        run(pl)                                     # graph capture, clocks up
+        return time_ms(lambda: run(pl), reps, flush)
+
+    best = lopc.plan_default().as_dict()
+    t0 = trial(best)
+    default_ms, best_ms = float(np.median(t0)), float(np.median(t0))
+    trials = [{"plan": json.loads(json.dumps(best)), "ms": best_ms}]
+    for knob, values in knobs.items():
+        for c in classes:
+            for v in values:
+                if v == best[knob][c]:
+                    continue
+                cand = json.loads(json.dumps(best))
+                cand[knob][c] = v
+                ms = float(np.median(trial(cand)))
+                trials.append({"knob": knob, "cls": c, "value": v, "ms": ms})
+                if ms < best_ms:
+                    best, best_ms = cand, ms
+    # the default timed again beside the winner, for the noise level
+    t1 = trial(lopc.plan_default().as_dict())
+    return {"plan": best, "ms": best_ms, "default_ms": default_ms,
+            "default_spread_ms": float(max(t0 + t1) - min(t0 + t1)), "trials": trials}
+
+
+def apply(plan: dict) -> None:
+    """Makes `plan` this thread's current plan (lopc_tune_*), which single-field calls
+    and batches launched without a plan use."""
+    lopc.tune_set(plan["rerun_blocks_per_sm"])
+    lopc.tune_set_budget(plan["pass_budget16"])
+    lopc.tune_set_dense(plan["pass_dense16"])
+    lopc.tune_set_pass_order(plan["pass_order"])
 
 
 def load(key: str, path: Optional[Path] = None) -> Optional[Dict]:
@@ -84,9 +116,10 @@ def load(key: str, path: Optional[Path] = None) -> Optional[Dict]:
     if not p.exists():
         return None
     try:
-        return json.loads(p.read_text()).get(key)
+        v = json.loads(p.read_text()).get(key)
     except (OSError, ValueError):
         return None
+    return v if isinstance(v, dict) and "plan" in v else None
 
 
 def save(key: str, value: Dict, path: Optional[Path] = None) -> None:
