@@ -321,7 +321,7 @@ int sm_count() {
 }
 
 // Persistent rerun blocks per SM, per class (set by lopc_tune_set).
-thread_local int g_rerun_per_sm[4] = {3, 3, 6, 6};
+thread_local int g_rerun_per_sm[4] = {4, 4, 6, 6};
 // Frontier evaluations of a tile pass before it switches to the topological order,
 // in sixteenths of the tile's points, per class (set by lopc_tune_set_budget).
 thread_local int g_pass_budget16[4] = {64, 64, 64, 64};
@@ -1503,7 +1503,7 @@ void lopc_plan_default(lopc_plan* pl) {
   if (!pl) return;
   memset(pl, 0, sizeof(*pl));
   for (int c = 0; c < 4; ++c) {
-    pl->rerun_blocks_per_sm[c] = c < 2 ? 3 : 6;
+    pl->rerun_blocks_per_sm[c] = c < 2 ? 4 : 6;
     pl->pass_budget16[c] = 64;
     pl->pass_dense16[c] = 8;
     pl->pass_order[c] = 0;

@@ -14,7 +14,7 @@ struct TileCfg;
 // blocks per SM those kernels are built for; NTC: threads of the chunk codecs.
 template <>
 struct TileCfg<float, 3> {
-  static constexpr int TZ = 16, TY = 16, TX = 16, HZ = 1, NT = 256, SEG = 16, MINB = 3, MINB_RERUN = 3, NTC = 256;
+  static constexpr int TZ = 16, TY = 16, TX = 16, HZ = 1, NT = 256, SEG = 16, MINB = 3, MINB_RERUN = 4, NTC = 256;
 };
 template <>
 struct TileCfg<double, 3> {
@@ -22,7 +22,7 @@ struct TileCfg<double, 3> {
 };
 template <>
 struct TileCfg<float, 2> {
-  static constexpr int TZ = 1, TY = 64, TX = 64, HZ = 0, NT = 256, SEG = 16, MINB = 3, MINB_RERUN = 3, NTC = 256;
+  static constexpr int TZ = 1, TY = 64, TX = 64, HZ = 0, NT = 256, SEG = 16, MINB = 3, MINB_RERUN = 4, NTC = 256;
 };
 template <>
 struct TileCfg<double, 2> {
@@ -1161,9 +1161,8 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
   unsigned* cnt = rb + G::NP / 32;
   uint16_t* flist = reinterpret_cast<uint16_t*>(smem + RS::LIST);
   __shared__ uint32_t marks;
-  __shared__ uint32_t nb_rank[27];  // ranks of the neighbour tiles (~0u: none)
-  __shared__ unsigned s_item, s_claimed;
-  __shared__ long long s_lim, s_app_gt;
+  __shared__ unsigned s_item, s_claimed, s_lim;
+  __shared__ long long s_app_gt;
   // the first round (list == nullptr) visits every tile of the class; blocks take
   // items from a counter, so a slow tile holds up only its own block.  Items past the
   // list are tiles that reruns of this round marked (app, the class's segment of a
@@ -1190,7 +1189,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
         if ((long long)ahead >= count) agt = (long long)reinterpret_cast<volatile uint32_t*>(app_seg)[ahead - count];
       }
       s_item = ahead;
-      s_lim = lim;
+      s_lim = (unsigned)lim;  // count + appended <= 2 * the class's tiles < 2^32
       s_app_gt = agt;
       if ((long long)ahead < lim) ahead = atomicAdd(next, 1u);
     }
@@ -1258,9 +1257,10 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
       }
     }
     for (int i = threadIdx.x; i < 3 * (G::NP / 32); i += NT) fa0[i] = 0;  // frontiers, risen bits
-    if (threadIdx.x < 27) {  // the neighbour tiles' ranks, for marking (loaded beside the box)
+    uint32_t nb_rank = ~0u;  // thread d < 27: rank of neighbour tile d (~0u: none), for marking
+    if (threadIdx.x < 27) {
       const int64_t nt = threadIdx.x == 13 ? -1 : neighbour_tile(g, tid, threadIdx.x);
-      nb_rank[threadIdx.x] = nt >= 0 ? fi.rank[nt] : ~0u;
+      if (nt >= 0) nb_rank = fi.rank[nt];
     }
     if (threadIdx.x == 0) marks = 0u;
     cp_async_wait_all();
@@ -1342,8 +1342,8 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB_RERUN
     if (mine) atomicOr(&marks, mine);
     __threadfence();  // the raised subbins are visible before any tile is marked
     __syncthreads();
-    if (threadIdx.x < 27 && ((marks >> threadIdx.x) & 1u) && nb_rank[threadIdx.x] != ~0u) {
-      const uint32_t r = nb_rank[threadIdx.x];
+    if (threadIdx.x < 27 && ((marks >> threadIdx.x) & 1u) && nb_rank != ~0u) {
+      const uint32_t r = nb_rank;
       if (!app_seg) {
         reinterpret_cast<volatile uint8_t*>(fi.dirty)[r] = 1;  // every writer stores the same value
       } else {

@@ -143,7 +143,7 @@ def test_batch_field_limit(L):
 def test_plan_default_and_current(L):
     """lopc_plan: the defaults, and the thread's current plan following lopc_tune_*."""
     d = L.plan_default().as_dict()
-    assert d == {"rerun_blocks_per_sm": [3, 3, 6, 6], "pass_budget16": [64] * 4, "pass_dense16": [8] * 4,
+    assert d == {"rerun_blocks_per_sm": [4, 4, 6, 6], "pass_budget16": [64] * 4, "pass_dense16": [8] * 4,
                  "pass_order": [0] * 4}
     saved = L.tune_get()
     try:

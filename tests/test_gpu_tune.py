@@ -31,7 +31,7 @@ def restore(L):
 
 
 SETTINGS = [  # (rerun blocks per SM, frontier budget in 16ths, dense threshold in 16ths, pass order)
-    ([3, 3, 6, 6], [64] * 4, [8] * 4, [0] * 4),      # defaults
+    ([4, 4, 6, 6], [64] * 4, [8] * 4, [0] * 4),      # defaults
     ([1, 1, 1, 1], [1] * 4, [17] * 4, [2] * 4),      # tiny grid; topological at once; tile-key order
     ([8, 8, 8, 8], [4096] * 4, [17] * 4, [1] * 4),   # frontier sweeps only, index order
     ([2, 5, 3, 7], [16] * 4, [0] * 4, [2, 1, 2, 1]), # every tile in topological order
