@@ -23,35 +23,70 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
   return x;
 }
 
+// Bytes of a plane buffer (n32 / 32 words per plane, L bytes in all) that hold its
+// first P planes, rounded up to 64 bytes (whole level-0 bitmap bytes of every RZE
+// unit size used here) and clipped to L: where the coder can stop reading when the
+// planes above P are zero.
+__device__ __forceinline__ uint32_t plane_bytes_of(int n32, int P, uint32_t L) {
+  const uint32_t b = ((uint32_t)P * (uint32_t)n32 / 8u + 63u) & ~63u;  // P planes of n32/32 words
+  return b < L ? b : L;
+}
+
+// Planes a word OR-reduction `orw` reaches (the planes above are zero).
+__device__ __forceinline__ int planes_of(uint64_t orw) { return orw ? 64 - __clzll((long long)orw) : 0; }
+
+// After a partial rze_decode into `buf` (L bytes; the first lw, a multiple of 16,
+// written): zeroes the rest, 16 bytes a store (all threads; ends with a barrier).
+template <int NT>
+__device__ __forceinline__ void zero_after_decode(uint8_t* buf, uint32_t lw, uint32_t L) {
+  uint4* b = reinterpret_cast<uint4*>(buf);
+  for (uint32_t i = lw / 16u + threadIdx.x; i < L / 16u; i += NT) b[i] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+}
+
 // Bit-plane transpose of n32 words (a multiple of 32): plane k (k = 0 least
 // significant) is n32/32 u32 words, bit j of word g being bit k of word 32g+j.
 // `word(i)` supplies input word i (zero for padding).  One warp per group of 32
 // words; with a plane length that is a multiple of 4 a warp takes four groups at a
 // time and each lane stores its four plane words in one 16-byte access (the lanes'
 // words lie a plane apart, on the same banks, so this cuts the conflicts by four).
+// Returns the OR of the words this thread transposed (the block-wide OR tells how
+// many planes can be non-zero).
 template <int NT, int W, typename WordFn>
-__device__ __forceinline__ void bit_transpose(int n32, WordFn word, uint32_t* planes) {
+__device__ __forceinline__ uint64_t bit_transpose(int n32, WordFn word, uint32_t* planes) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int G = n32 >> 5;
+  uint64_t orw = 0;
   if ((G & 3) == 0) {
     for (int g = 4 * wid; g < G; g += 4 * (NT / 32)) {
       uint32_t lo[4], hi[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const uint64_t v = word(32 * (g + u) + lane);
+        orw |= v;
         lo[u] = warp_transpose32((uint32_t)v);
         hi[u] = W == 8 ? warp_transpose32((uint32_t)(v >> 32)) : 0u;
       }
       *reinterpret_cast<uint4*>(&planes[lane * G + g]) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
       if (W == 8) *reinterpret_cast<uint4*>(&planes[(32 + lane) * G + g]) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
     }
-    return;
+    return orw;
   }
   for (int g = wid; g < G; g += NT / 32) {
     const uint64_t v = word(32 * g + lane);
+    orw |= v;
     planes[lane * G + g] = warp_transpose32((uint32_t)v);
     if (W == 8) planes[(32 + lane) * G + g] = warp_transpose32((uint32_t)(v >> 32));
   }
+  return orw;
+}
+
+// Block-wide OR of each thread's `v` into *dst (zeroed beforehand and read after the
+// caller's next barrier).
+__device__ __forceinline__ void block_or_into(uint64_t v, unsigned long long* dst) {
+  const uint64_t o = ((uint64_t)__reduce_or_sync(0xffffffffu, (unsigned)(v >> 32)) << 32) |
+                     __reduce_or_sync(0xffffffffu, (unsigned)v);
+  if ((threadIdx.x & 31) == 0 && o) atomicOr(dst, (unsigned long long)o);
 }
 
 // Inverse of bit_transpose: `emit(i, word)` receives word i of the n32.
@@ -208,13 +243,18 @@ __device__ __forceinline__ void block_exclusive_scan3(const uint32_t v[3], uint3
 // RZE_g encode of `in` (L bytes, shared memory, 16-byte aligned) into `out` (shared
 // memory): [level-2 bitmap][level-1 kept][level-0 kept][non-zero units].  Nothing is
 // written when the result would not be shorter than `limit`.  Returns its length.
+// Bytes of `in` from Lnz on are taken as zero and not read (Lnz: a multiple of 8 G
+// bytes, or >= L); the record is the same as for the whole input.
 // Needs ceil(L/G/512) <= NT (true for the chunk sizes used here).
 template <int NT, int G>
-__device__ uint32_t rze_encode(const uint8_t* in, uint32_t L, uint8_t* out, uint32_t limit, const RzeWork& w) {
+__device__ uint32_t rze_encode(const uint8_t* in, uint32_t L, uint8_t* out, uint32_t limit, const RzeWork& w,
+                               uint32_t Lnz = 0xffffffffu) {
   const uint32_t U = L / G;
   const uint32_t l0 = ceil8(U), l1 = ceil8(l0), l2 = ceil8(l1);
+  const uint32_t l0nz = Lnz >= L ? l0 : Lnz / (8u * G);  // level-0 bytes that can be non-zero
   const int t = threadIdx.x, lane = t & 31;
-  const WarpRange<NT> wr(l0);
+  const WarpRange<NT> wr(l0nz);
+  auto m0at = [&](uint32_t j) -> uint32_t { return j < l0nz ? (uint32_t)w.m0[j] : 0u; };
   // level 0, warp-strided
   uint32_t c0 = 0;
   for (uint32_t j = wr.a + lane; j < wr.b; j += 32) {
@@ -222,7 +262,6 @@ __device__ uint32_t rze_encode(const uint8_t* in, uint32_t L, uint8_t* out, uint
     w.m0[j] = (uint8_t)byte;
     c0 += __popc(byte);
   }
-  for (uint32_t j = l0 + t; j < ((l0 + 3) & ~3u); j += NT) w.m0[j] = 0;
   __syncthreads();
   // level 1: contiguous level-1 bytes per thread (few)
   const uint32_t per1 = (l1 + NT - 1) / NT;
@@ -230,11 +269,13 @@ __device__ uint32_t rze_encode(const uint8_t* in, uint32_t L, uint8_t* out, uint
   uint32_t c1 = 0;
   for (uint32_t jj = a1; jj < b1; ++jj) {
     uint32_t byte = 0;
-    for (uint32_t b = 0; b < 8; ++b) {
-      const uint32_t j = 8 * jj + b;
-      if (j >= l0) break;
-      const uint8_t prev = j ? w.m0[j - 1] : 0;
-      if (w.m0[j] != prev) byte |= 1u << b;
+    if (8 * jj <= l0nz) {  // past the non-zero level-0 bytes nothing changes
+      for (uint32_t b = 0; b < 8; ++b) {
+        const uint32_t j = 8 * jj + b;
+        if (j >= l0) break;
+        const uint32_t prev = j ? m0at(j - 1) : 0u;
+        if (m0at(j) != prev) byte |= 1u << b;
+      }
     }
     w.m1[jj] = (uint8_t)byte;
     c1 += __popc(byte);
@@ -278,7 +319,7 @@ __device__ uint32_t rze_encode(const uint8_t* in, uint32_t L, uint8_t* out, uint
       while (bits) {
         const uint32_t j = 8 * jj + (__ffs(bits) - 1);
         bits &= bits - 1;
-        k0[r++] = w.m0[j];
+        k0[r++] = (uint8_t)m0at(j);
       }
     }
   }
@@ -311,9 +352,13 @@ __device__ __forceinline__ bool tail_clear(const uint8_t* bm, uint32_t nbits) {
 }
 
 // RZE_g decode: `in` (in_len bytes, shared memory) -> `out` (L bytes, shared
-// memory, 16-byte aligned).  Returns false for an inconsistent record.
+// memory, 16-byte aligned).  Returns false for an inconsistent record.  With
+// `written` null the whole output is written; otherwise only its first *written
+// bytes (the bytes up to the last non-zero unit, rounded up to 64 and clipped to L),
+// and every later byte of the output is zero.
 template <int NT, int G>
-__device__ bool rze_decode(const uint8_t* in, uint32_t in_len, uint32_t L, uint8_t* out, const RzeWork& w) {
+__device__ bool rze_decode(const uint8_t* in, uint32_t in_len, uint32_t L, uint8_t* out, const RzeWork& w,
+                           uint32_t* written = nullptr) {
   const uint32_t U = L / G;
   const uint32_t l0 = ceil8(U), l1 = ceil8(l0), l2 = ceil8(l1);
   const int t = threadIdx.x, lane = t & 31;
@@ -345,37 +390,51 @@ __device__ bool rze_decode(const uint8_t* in, uint32_t in_len, uint32_t L, uint8
     w.m1[j] = v;
   }
   __syncthreads();
-  // prefix counts of level-1 words (warp 0)
+  // prefix counts of level-1 words (warp 0); for a partial decode also the level-0
+  // bytes that can be non-zero: m0 changes last at the last set bit jl of m1, to the
+  // last kept level-0 byte, so m0 is zero from jl on when that byte is 0
   const uint32_t nw1 = (l1 + 3) >> 2;
   const uint32_t* m1w = reinterpret_cast<const uint32_t*>(w.m1);
   if (t < 32) {
-    uint32_t carry = 0;
+    uint32_t carry = 0, last = 0;  // last: 1 + the highest set bit of m1 seen so far
     for (uint32_t base = 0; base < nw1; base += 32) {
       const uint32_t wi = base + t;
-      const uint32_t c = wi < nw1 ? __popc(m1w[wi]) : 0u;
+      const uint32_t mw = wi < nw1 ? m1w[wi] : 0u;
+      const uint32_t c = __popc(mw);
       uint32_t tot;
       const uint32_t ex = warp_exclusive_scan(c, &tot);
       if (wi < nw1) w.pre[wi] = carry + ex;
       carry += tot;
+      const uint32_t hi = __ballot_sync(0xffffffffu, mw != 0u);
+      if (hi) {
+        const int hl = 31 - __clz(hi);
+        const uint32_t hw = __shfl_sync(0xffffffffu, mw, hl);
+        last = 32 * (base + hl) + (32 - __clz(hw));
+      }
     }
-    if (t == 0) w.pre[nw1] = carry;
+    if (t == 0) {
+      w.pre[nw1] = carry;
+      w.tmp[39] = last;
+    }
   }
   __syncthreads();
   const uint32_t nk0 = w.pre[nw1];
   if (!tail_clear(w.m1, l0) || l2 + nk1 + nk0 > in_len) return false;  // uniform
   const uint8_t* k0 = in + l2 + nk1;
-  for (uint32_t j = t; j < ((l0 + 3) & ~3u); j += NT) {
+  uint32_t l0nz = l0;  // level-0 bytes that can be non-zero
+  if (written) l0nz = nk0 == 0 ? 0u : (k0[nk0 - 1] != 0 ? l0 : min(l0, w.tmp[39] - 1u));
+  for (uint32_t j = t; j < ((l0nz + 3) & ~3u); j += NT) {
     uint8_t v = 0;
-    if (j < l0) {
+    if (j < l0nz) {
       const uint32_t r = w.pre[j >> 5] + __popc(m1w[j >> 5] << (31 - (j & 31)));
       v = r ? k0[r - 1] : 0;
     }
     w.m0[j] = v;
   }
   __syncthreads();
-  if (!tail_clear(w.m0, U)) return false;  // uniform
+  if (l0nz == l0 && !tail_clear(w.m0, U)) return false;  // uniform (a shorter m0 ends in zeros)
   // payload, warp-strided over the level-0 bytes
-  const WarpRange<NT> wr(l0);
+  const WarpRange<NT> wr(l0nz);
   uint32_t c0 = 0;
   for (uint32_t j = wr.a + lane; j < wr.b; j += 32) c0 += __popc((uint32_t)w.m0[j]);
   uint32_t wtot;
@@ -419,6 +478,11 @@ __device__ bool rze_decode(const uint8_t* in, uint32_t in_len, uint32_t L, uint8
         }
       }
     }
+  }
+  if (written) {
+    const uint32_t done = min(L, 8u * G * l0nz), lw = min(L, (done + 63u) & ~63u);
+    for (uint32_t i = done + t; i < lw; i += NT) out[i] = 0;
+    *written = lw;
   }
   __syncthreads();
   return true;

@@ -889,6 +889,8 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   // 1D differences of the thread's points (the Lorenzo stencil's seven lower-octant
   // points are the neighbours -D[0..6] the flags load anyway)
   unsigned cost_l = 0, cost_d = 0;
+  __shared__ unsigned long long s_or;  // OR of the bin record's mapped words (its non-zero planes)
+  if (threadIdx.x == 0) s_or = 0ull;
   constexpr WordT NBM = (WordT)0xAAAAAAAAAAAAAAAAULL;
 #pragma unroll 1
   for (int j = 0; j < G::SEG; ++j) {
@@ -957,6 +959,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   {
     const unsigned wsum = __reduce_add_sync(0xffffffffu, same_pairs);
     const unsigned wl = __reduce_add_sync(0xffffffffu, cost_l), wd = __reduce_add_sync(0xffffffffu, cost_d);
+
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(&cnt[0], wsum);
       atomicAdd(&cnt[2], wl);
@@ -1019,14 +1022,16 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
     const bool use_diff = cnt[3] < cnt[2];  // the costs summed during the flags
     uint32_t* planes = reinterpret_cast<uint32_t*>(smem);
     const RzeWork w = rze_work_at(smem + PS::L, PS::L);
-    bit_transpose<NT, W>(n32, [&](int i) -> uint64_t {
+    block_or_into(bit_transpose<NT, W>(n32, [&](int i) -> uint64_t {
       if (i >= n) return 0;
       return nb(use_diff ? diff_of(i) : lorenzo_of(i));
-    }, planes);
+    }, planes), &s_or);
     __syncthreads();
     uint8_t* slot = slots + (size_t)tid * kSlotBytes;
     uint8_t* stage = reinterpret_cast<uint8_t*>(bin);  // bins are dead once the record is written
-    const uint32_t len = rze_encode<NT, 1>(reinterpret_cast<const uint8_t*>(planes), W * n32, stage, raw, w);
+    // planes above those the mapped words reach are zero: the coder does not read them
+    const uint32_t Lnz = plane_bytes_of(n32, planes_of(s_or), (uint32_t)W * n32);
+    const uint32_t len = rze_encode<NT, 1>(reinterpret_cast<const uint8_t*>(planes), W * n32, stage, raw, w, Lnz);
     if (len >= raw) {  // nothing was staged: bins are intact
       for (int i = threadIdx.x; i < n; i += NT) reinterpret_cast<WordT*>(slot)[i] = bin_of(i);
       if (threadIdx.x == 0) sizes[tid] = raw | kRawFlag;
@@ -1664,12 +1669,17 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC) k_encode_sub(const FieldI
       ws[i] = (W_t)s_glob[(tb.z0 + lz) * plane + (tb.y0 + ly) * g.nx + tb.x0 + lx];
     }
   }
-  __syncthreads();
   const uint32_t raw = (uint32_t)n * W;
   uint8_t* slot = slots + ((size_t)g.ntiles + tid) * kSlotBytes;
-  bit_transpose<NT, W>(n32, [&](int i) -> uint64_t { return i < n ? (uint64_t)ws[i] : 0ULL; }, planes);
+  __shared__ unsigned long long s_or;  // OR of the subbins: the planes they reach
+  if (threadIdx.x == 0) s_or = 0ull;
   __syncthreads();
-  const uint32_t l2 = rze_encode<NT, W>(reinterpret_cast<const uint8_t*>(planes), W * n32, rzw, 0xffffffffu, w);
+  block_or_into(bit_transpose<NT, W>(n32, [&](int i) -> uint64_t { return i < n ? (uint64_t)ws[i] : 0ULL; }, planes),
+                &s_or);
+  __syncthreads();
+  // planes above those the subbins reach are zero: the coder does not read them
+  const uint32_t Lnz = plane_bytes_of(n32, planes_of(s_or), (uint32_t)W * n32);
+  const uint32_t l2 = rze_encode<NT, W>(reinterpret_cast<const uint8_t*>(planes), W * n32, rzw, 0xffffffffu, w, Lnz);
   // the words in A are still intact: only B and C were written so far
   uint32_t len = 0xffffffffu;
   if (raw > 4) len = rze_encode<NT, 1>(rzw, l2, stage + 4, raw - 4, w);

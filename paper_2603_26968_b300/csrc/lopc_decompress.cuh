@@ -283,16 +283,18 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC, 4) k_decode(const DecFiel
   } else {
     if (sb_len >= raw) bad = 1;  // an encoded record is shorter than the raw chunk
     __syncthreads();
+    uint32_t lw = 0;  // bytes of the bins' planes the decode wrote (the rest is zero)
     if (!bad) {
       copy16<NT>(A, rb, sb_len);
       __syncthreads();
-      if (!rze_decode<NT, 1>(A, sb_len, (uint32_t)W * n32, Bf, w)) bad = 1;
+      if (!rze_decode<NT, 1>(A, sb_len, (uint32_t)W * n32, Bf, w, &lw)) bad = 1;
       __syncthreads();
     }
     dec_mark(0, t0);
     prefetch_sub();  // A is free from here on
     if (!bad) {
       constexpr W_t M = (W_t)0xAAAAAAAAAAAAAAAAULL;
+      zero_after_decode<NT>(Bf, lw, (uint32_t)W * n32);
       bit_untranspose<NT, W>(n32, reinterpret_cast<const uint32_t*>(Bf), [&](int i, uint64_t u) {
         if (i < n)
           wb[i] = (W_t)(((W_t)u ^ M) - M);
@@ -425,10 +427,12 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC, 4) k_decode(const DecFiel
     if (!bad && !rze_decode<NT, 1>(A + 4, ss - 4, l2, Bf, w)) bad = 1;
     __syncthreads();
     dec_mark(3, t0);
-    if (!bad && !rze_decode<NT, W>(Bf, l2, (uint32_t)W * n32, A, w)) bad = 1;
+    uint32_t lws = 0;  // bytes of the subbins' planes the decode wrote (the rest is zero)
+    if (!bad && !rze_decode<NT, W>(Bf, l2, (uint32_t)W * n32, A, w, &lws)) bad = 1;
     __syncthreads();
     dec_mark(4, t0);
     if (!bad) {
+      zero_after_decode<NT>(A, lws, (uint32_t)W * n32);
       bit_untranspose<NT, W>(n32, reinterpret_cast<const uint32_t*>(A), [&](int i, uint64_t u) {
         if (i < n)
           put(i, (uint64_t)(W_t)u);
