@@ -89,16 +89,93 @@ __device__ __forceinline__ void block_or_into(uint64_t v, unsigned long long* ds
   if ((threadIdx.x & 31) == 0 && o) atomicOr(dst, (unsigned long long)o);
 }
 
-// Inverse of bit_transpose: `emit(i, word)` receives word i of the n32.
+// Packed transposes for words whose bits from P on are zero (P <= P2 = 2^LG <= 32).
+// One 32 x 32 warp transpose then carries Q = 32 / P2 groups of 32 words: row
+// j * P2 + k is plane k of group j, and column c holds the low P2 bits of word c of
+// group j in bits [j P2, (j + 1) P2).  The planes are the same as bit_transpose's;
+// planes [P2, W*8) are not written (they are zero), planes [P, P2) are written as zero.
+template <int LG, int NT, typename WordFn>
+__device__ __forceinline__ void transpose_packed(int G, WordFn word, uint32_t* planes) {
+  constexpr int P2 = 1 << LG, Q = 32 >> LG;
+  constexpr uint32_t MASK = P2 == 32 ? 0xffffffffu : (1u << P2) - 1u;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int j = lane >> LG, k = lane & (P2 - 1);
+  for (int go = wid * Q; go < G; go += (NT / 32) * Q) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int jj = 0; jj < Q; ++jj)
+      if (go + jj < G) v |= ((uint32_t)word(32 * (go + jj) + lane) & MASK) << (jj * P2);
+    const uint32_t r = warp_transpose32(v);
+    if (go + j < G) planes[k * G + go + j] = r;
+  }
+}
+
+// Inverse of transpose_packed: reads planes [0, P) only.
+template <int LG, int NT, typename EmitFn>
+__device__ __forceinline__ void untranspose_packed(int G, const uint32_t* planes, int P, EmitFn emit) {
+  constexpr int P2 = 1 << LG, Q = 32 >> LG;
+  constexpr uint32_t MASK = P2 == 32 ? 0xffffffffu : (1u << P2) - 1u;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int j = lane >> LG, k = lane & (P2 - 1);
+  for (int go = wid * Q; go < G; go += (NT / 32) * Q) {
+    const int g = go + j;
+    const uint32_t r = warp_transpose32(k < P && g < G ? planes[k * G + g] : 0u);
+#pragma unroll
+    for (int jj = 0; jj < Q; ++jj)
+      if (go + jj < G) emit(32 * (go + jj) + lane, (uint64_t)((r >> (jj * P2)) & MASK));
+  }
+}
+
+// Whether the packed transposes serve a chunk of n32 words whose planes from P on are
+// zero: P <= 16 (at least two groups per transpose), or P <= 32 for 64-bit words
+// (one transpose instead of two), and whole 64-byte planes, so that the coder's
+// plane_bytes_of(n32, P) ends on a plane the transpose wrote.
+template <int W>
+__device__ __forceinline__ bool packed_ok(int n32, int P) {
+  return (n32 & 511) == 0 && (P <= 16 || (W == 8 && P <= 32));
+}
+
+// log2 of the packing width for P planes: 4 planes at least (eight groups).
+__device__ __forceinline__ int packed_lg(int P) { return P <= 4 ? 2 : 32 - __clz(P - 1); }
+
+// bit_transpose of words whose planes from P on are zero (the caller knows P, e.g.
+// from an OR of the words): packed when packed_ok, else the plain transpose.
+template <int NT, int W, typename WordFn>
+__device__ __forceinline__ void bit_transpose_planes(int n32, int P, WordFn word, uint32_t* planes) {
+  if (!packed_ok<W>(n32, P)) {
+    (void)bit_transpose<NT, W>(n32, word, planes);
+    return;
+  }
+  const int G = n32 >> 5;
+  switch (packed_lg(P)) {
+    case 2: transpose_packed<2, NT>(G, word, planes); break;
+    case 3: transpose_packed<3, NT>(G, word, planes); break;
+    case 4: transpose_packed<4, NT>(G, word, planes); break;
+    default: transpose_packed<5, NT>(G, word, planes); break;
+  }
+}
+
+// Inverse of bit_transpose: `emit(i, word)` receives word i of the n32.  Only planes
+// [0, P) are read; the others are taken as zero.
 template <int NT, int W, typename EmitFn>
-__device__ __forceinline__ void bit_untranspose(int n32, const uint32_t* planes, EmitFn emit) {
+__device__ __forceinline__ void bit_untranspose(int n32, const uint32_t* planes, EmitFn emit, int P = 8 * W) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int G = n32 >> 5;
+  if (packed_ok<W>(n32, P)) {
+    switch (packed_lg(P)) {
+      case 2: untranspose_packed<2, NT>(G, planes, P, emit); break;
+      case 3: untranspose_packed<3, NT>(G, planes, P, emit); break;
+      case 4: untranspose_packed<4, NT>(G, planes, P, emit); break;
+      default: untranspose_packed<5, NT>(G, planes, P, emit); break;
+    }
+    return;
+  }
+  const uint4 z = make_uint4(0u, 0u, 0u, 0u);
   if ((G & 3) == 0) {
     for (int g = 4 * wid; g < G; g += 4 * (NT / 32)) {
-      const uint4 a = *reinterpret_cast<const uint4*>(&planes[lane * G + g]);
-      uint4 b = make_uint4(0u, 0u, 0u, 0u);
-      if (W == 8) b = *reinterpret_cast<const uint4*>(&planes[(32 + lane) * G + g]);
+      const uint4 a = lane < P ? *reinterpret_cast<const uint4*>(&planes[lane * G + g]) : z;
+      uint4 b = z;
+      if (W == 8 && 32 + lane < P) b = *reinterpret_cast<const uint4*>(&planes[(32 + lane) * G + g]);
       const uint32_t la[4] = {a.x, a.y, a.z, a.w}, lb[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -110,10 +187,23 @@ __device__ __forceinline__ void bit_untranspose(int n32, const uint32_t* planes,
     return;
   }
   for (int g = wid; g < G; g += NT / 32) {
-    const uint32_t lo = warp_transpose32(planes[lane * G + g]);
-    const uint32_t hi = W == 8 ? warp_transpose32(planes[(32 + lane) * G + g]) : 0u;
+    const uint32_t lo = warp_transpose32(lane < P ? planes[lane * G + g] : 0u);
+    const uint32_t hi = W == 8 ? warp_transpose32(32 + lane < P ? planes[(32 + lane) * G + g] : 0u) : 0u;
     emit(32 * g + lane, (uint64_t)lo | ((uint64_t)hi << 32));
   }
+}
+
+// Planes of a buffer of n32-word planes that a partial RZE decode of lw bytes can have
+// made non-zero (all planes from there on are zero), and the end of the bytes that must
+// be zeroed after the decode for bit_untranspose(..., P): the rest of plane P - 1,
+// rounded up to 16 and clipped to L.
+__device__ __forceinline__ int planes_in(uint32_t lw, int n32) {
+  const uint32_t pb = (uint32_t)n32 / 8u;  // bytes of a plane
+  return (int)((lw + pb - 1u) / pb);
+}
+__device__ __forceinline__ uint32_t planes_zero_end(int P, int n32, uint32_t L) {
+  const uint32_t e = ((uint32_t)P * ((uint32_t)n32 / 8u) + 15u) & ~15u;
+  return e < L ? e : L;
 }
 
 // ------------------------------------------------------------- RZE_g stage

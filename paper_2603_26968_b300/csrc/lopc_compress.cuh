@@ -840,7 +840,12 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   constexpr int NBOX = G::BZ * G::BY * G::BX;  // entries of the box (the rare error path walks them)
   load_box_async<G, Raw>(raw, reinterpret_cast<const Raw*>(x), g, tb);
   for (int i = threadIdx.x; i < 3 * (G::NP / 32); i += NT) fa[i] = 0;  // both frontiers, risen bits
-  if (threadIdx.x == 0) cnt[0] = cnt[2] = cnt[3] = 0;  // same-bin pairs; the bin predictors' costs
+  // ORs of the two predictors' mapped words: the bit planes each can reach
+  __shared__ unsigned long long s_orl, s_ord;
+  if (threadIdx.x == 0) {
+    cnt[0] = cnt[2] = cnt[3] = 0;  // same-bin pairs; the bin predictors' costs
+    s_orl = s_ord = 0ull;
+  }
   cp_async_wait_all();
   __syncthreads();
   bool bad = false;
@@ -889,8 +894,7 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
   // 1D differences of the thread's points (the Lorenzo stencil's seven lower-octant
   // points are the neighbours -D[0..6] the flags load anyway)
   unsigned cost_l = 0, cost_d = 0;
-  __shared__ unsigned long long s_or;  // OR of the bin record's mapped words (its non-zero planes)
-  if (threadIdx.x == 0) s_or = 0ull;
+  uint64_t or_l = 0, or_d = 0;
   constexpr WordT NBM = (WordT)0xAAAAAAAAAAAAAAAAULL;
 #pragma unroll 1
   for (int j = 0; j < G::SEG; ++j) {
@@ -930,8 +934,11 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
         prev = (WordT)bin[G::entry(sp.lz, ly - 1, tb.cx - 1)];
       else if (hz)
         prev = (WordT)bin[G::entry(sp.lz - 1, tb.cy - 1, tb.cx - 1)];
-      cost_l += __popcll((uint64_t)((WordT)(r + NBM) ^ NBM));
-      cost_d += __popcll((uint64_t)((WordT)((WordT)bp - prev + NBM) ^ NBM));
+      const uint64_t ml = (uint64_t)((WordT)(r + NBM) ^ NBM), md = (uint64_t)((WordT)((WordT)bp - prev + NBM) ^ NBM);
+      cost_l += __popcll(ml);
+      cost_d += __popcll(md);
+      or_l |= ml;
+      or_d |= md;
     }
     const uint32_t up = same & ~lo & ~out_of_box_bits<G>(sp.lz, ly, sp.lx);
     const int o = sp.o0 + j * G::TX;
@@ -965,6 +972,8 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
       atomicAdd(&cnt[2], wl);
       atomicAdd(&cnt[3], wd);
     }
+    block_or_into(or_l, &s_orl);
+    block_or_into(or_d, &s_ord);
   }
   __syncthreads();  // keys are dead from here on
   // same-bin pairs over the tile's points, against 16ths of the neighbour pairs a full
@@ -1022,15 +1031,18 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
     const bool use_diff = cnt[3] < cnt[2];  // the costs summed during the flags
     uint32_t* planes = reinterpret_cast<uint32_t*>(smem);
     const RzeWork w = rze_work_at(smem + PS::L, PS::L);
-    block_or_into(bit_transpose<NT, W>(n32, [&](int i) -> uint64_t {
+    // planes above those the chosen predictor's mapped words reach (their OR, taken
+    // during the flags) are zero: the transpose packs the planes below, and the coder
+    // does not read the rest
+    const int Pnz = planes_of(use_diff ? s_ord : s_orl);
+    bit_transpose_planes<NT, W>(n32, Pnz, [&](int i) -> uint64_t {
       if (i >= n) return 0;
       return nb(use_diff ? diff_of(i) : lorenzo_of(i));
-    }, planes), &s_or);
+    }, planes);
     __syncthreads();
     uint8_t* slot = slots + (size_t)tid * kSlotBytes;
     uint8_t* stage = reinterpret_cast<uint8_t*>(bin);  // bins are dead once the record is written
-    // planes above those the mapped words reach are zero: the coder does not read them
-    const uint32_t Lnz = plane_bytes_of(n32, planes_of(s_or), (uint32_t)W * n32);
+    const uint32_t Lnz = plane_bytes_of(n32, Pnz, (uint32_t)W * n32);
     const uint32_t len = rze_encode<NT, 1>(reinterpret_cast<const uint8_t*>(planes), W * n32, stage, raw, w, Lnz);
     if (len >= raw) {  // nothing was staged: bins are intact
       for (int i = threadIdx.x; i < n; i += NT) reinterpret_cast<WordT*>(slot)[i] = bin_of(i);
@@ -1674,11 +1686,18 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC) k_encode_sub(const FieldI
   __shared__ unsigned long long s_or;  // OR of the subbins: the planes they reach
   if (threadIdx.x == 0) s_or = 0ull;
   __syncthreads();
-  block_or_into(bit_transpose<NT, W>(n32, [&](int i) -> uint64_t { return i < n ? (uint64_t)ws[i] : 0ULL; }, planes),
-                &s_or);
+  {
+    uint64_t o = 0;
+    for (int i = threadIdx.x; i < n; i += NT) o |= (uint64_t)ws[i];
+    block_or_into(o, &s_or);
+  }
   __syncthreads();
-  // planes above those the subbins reach are zero: the coder does not read them
-  const uint32_t Lnz = plane_bytes_of(n32, planes_of(s_or), (uint32_t)W * n32);
+  // planes above those the subbins reach are zero: the transpose packs the planes
+  // below, and the coder does not read the rest
+  const int Pnz = planes_of(s_or);
+  bit_transpose_planes<NT, W>(n32, Pnz, [&](int i) -> uint64_t { return i < n ? (uint64_t)ws[i] : 0ULL; }, planes);
+  __syncthreads();
+  const uint32_t Lnz = plane_bytes_of(n32, Pnz, (uint32_t)W * n32);
   const uint32_t l2 = rze_encode<NT, W>(reinterpret_cast<const uint8_t*>(planes), W * n32, rzw, 0xffffffffu, w, Lnz);
   // the words in A are still intact: only B and C were written so far
   uint32_t len = 0xffffffffu;

@@ -294,13 +294,18 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC, 4) k_decode(const DecFiel
     prefetch_sub();  // A is free from here on
     if (!bad) {
       constexpr W_t M = (W_t)0xAAAAAAAAAAAAAAAAULL;
-      zero_after_decode<NT>(Bf, lw, (uint32_t)W * n32);
-      bit_untranspose<NT, W>(n32, reinterpret_cast<const uint32_t*>(Bf), [&](int i, uint64_t u) {
-        if (i < n)
-          wb[i] = (W_t)(((W_t)u ^ M) - M);
-        else if (u != 0)
-          bad = 1;
-      });
+      // planes from P on are zero and not read; the rest of plane P - 1 is zeroed
+      const int P = planes_in(lw, n32);
+      zero_after_decode<NT>(Bf, lw, planes_zero_end(P, n32, (uint32_t)W * n32));
+      bit_untranspose<NT, W>(
+          n32, reinterpret_cast<const uint32_t*>(Bf),
+          [&](int i, uint64_t u) {
+            if (i < n)
+              wb[i] = (W_t)(((W_t)u ^ M) - M);
+            else if (u != 0)
+              bad = 1;
+          },
+          P);
       __syncthreads();
     }
     if (!bad && !use_diff) undo_lorenzo<NT, ND>(wb, tb.cz, tb.cy, tb.cx);
@@ -432,13 +437,17 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC, 4) k_decode(const DecFiel
     __syncthreads();
     dec_mark(4, t0);
     if (!bad) {
-      zero_after_decode<NT>(A, lws, (uint32_t)W * n32);
-      bit_untranspose<NT, W>(n32, reinterpret_cast<const uint32_t*>(A), [&](int i, uint64_t u) {
-        if (i < n)
-          put(i, (uint64_t)(W_t)u);
-        else if (u != 0)
-          fail = true;
-      });
+      const int P = planes_in(lws, n32);
+      zero_after_decode<NT>(A, lws, planes_zero_end(P, n32, (uint32_t)W * n32));
+      bit_untranspose<NT, W>(
+          n32, reinterpret_cast<const uint32_t*>(A),
+          [&](int i, uint64_t u) {
+            if (i < n)
+              put(i, (uint64_t)(W_t)u);
+            else if (u != 0)
+              fail = true;
+          },
+          P);
     }
   }
   cp_async_wait_all();  // no copy may outlive the block (a no-op once the record was consumed)
