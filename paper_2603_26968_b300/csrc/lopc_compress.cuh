@@ -1610,6 +1610,17 @@ __global__ void __launch_bounds__(256) k_clear_subbins(const FieldInfo* __restri
 
 // ----------------------------------------------------------------- subbin encoder
 
+// A raw subbin record: the tile's subbins as words, in the chunk's point order (kept
+// out of line: the encoder's registers are budgeted for five blocks per SM).
+template <typename W_t>
+__device__ __noinline__ void store_raw_subbins(W_t* slot, const uint32_t* s_glob, TileBox tb, int64_t nx,
+                                               int64_t plane) {
+  for (int i = threadIdx.x; i < tb.n; i += blockDim.x) {
+    const int lx = i % tb.cx, ly = (i / tb.cx) % tb.cy, lz = i / (tb.cx * tb.cy);
+    slot[i] = (W_t)s_glob[(tb.z0 + lz) * plane + (tb.y0 + ly) * nx + tb.x0 + lx];
+  }
+}
+
 template <typename T, int ND>
 struct EncSmem {
   using G = TileGeom<T, ND>;
@@ -1617,14 +1628,15 @@ struct EncSmem {
   static constexpr int W = Traits<T>::W;
   static constexpr uint32_t L = (uint32_t)NP * W;                    // BIT output bytes of a full tile
   static constexpr uint32_t LR = (L + L / 8 + L / 64 + L / 512 + 16 + 15) & ~15u;  // RZE_w output bound
-  // A: words -> staged record; B: planes; C: RZE_w output; work
-  static constexpr size_t bytes() { return (size_t)L + L + LR + RzeWork::bytes(LR) + 16; }
+  // A: words -> RZE_w output; B: planes -> staged record; work (five blocks per SM for
+  // float32 tiles)
+  static constexpr size_t bytes() { return (size_t)LR + L + RzeWork::bytes(LR) + 16; }
 };
 
 // Subbin record of each chunk (Sec. III-C, LC-generated pipeline): BIT_w, RZE_w,
 // RZE_1, prefixed by the u32 length of the RZE_w output; raw if not shorter.
 template <typename T, int ND>
-__global__ void __launch_bounds__(TileCfg<T, ND>::NTC) k_encode_sub(const FieldInfo* __restrict__ F, int f0, int nf,
+__global__ void __launch_bounds__(TileCfg<T, ND>::NTC, 5) k_encode_sub(const FieldInfo* __restrict__ F, int f0, int nf,
                                                                    int64_t tile0) {
   using G = TileGeom<T, ND>;
   using ES = EncSmem<T, ND>;
@@ -1641,10 +1653,10 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC) k_encode_sub(const FieldI
   uint32_t* __restrict__ sizes = fi.sizes;
   extern __shared__ __align__(16) unsigned char smem[];
   W_t* ws = reinterpret_cast<W_t*>(smem);
-  uint8_t* stage = smem;
-  uint32_t* planes = reinterpret_cast<uint32_t*>(smem + ES::L);
-  uint8_t* rzw = smem + 2 * ES::L;
-  const RzeWork w = rze_work_at(rzw + ES::LR, ES::LR);
+  uint8_t* rzw = smem;  // the words are dead once transposed
+  uint32_t* planes = reinterpret_cast<uint32_t*>(smem + ES::LR);
+  uint8_t* stage = smem + ES::LR;  // the planes are dead once RZE_w has read them
+  const RzeWork w = rze_work_at(smem + ES::LR + ES::L, ES::LR);
 
   const int64_t tid = gt - fi.tile_base;
   if (tid < 0 || tid >= g.ntiles) return;  // never for a consistent plan
@@ -1699,11 +1711,10 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NTC) k_encode_sub(const FieldI
   __syncthreads();
   const uint32_t Lnz = plane_bytes_of(n32, Pnz, (uint32_t)W * n32);
   const uint32_t l2 = rze_encode<NT, W>(reinterpret_cast<const uint8_t*>(planes), W * n32, rzw, 0xffffffffu, w, Lnz);
-  // the words in A are still intact: only B and C were written so far
   uint32_t len = 0xffffffffu;
   if (raw > 4) len = rze_encode<NT, 1>(rzw, l2, stage + 4, raw - 4, w);
-  if (raw <= 4 || len + 4 >= raw) {  // nothing was staged
-    for (int i = threadIdx.x; i < n; i += NT) reinterpret_cast<W_t*>(slot)[i] = ws[i];
+  if (raw <= 4 || len + 4 >= raw) {  // nothing was staged; the words are read again
+    store_raw_subbins<W_t>(reinterpret_cast<W_t*>(slot), s_glob, tb, g.nx, plane);
     if (threadIdx.x == 0) sizes[g.ntiles + tid] = raw | kRawFlag;
     return;
   }
