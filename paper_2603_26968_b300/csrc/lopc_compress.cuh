@@ -251,6 +251,30 @@ __device__ __forceinline__ void box_word(Word* dst, const Word* src, bool in) {
   }
 }
 
+// Loads of words other blocks may change (ld.global.cg, from L2) into dst[], B per
+// thread issued together before their shared-memory stores, so that a thread waits for
+// one round trip per B loads rather than per load.  at(i, e, src) gives item i's entry
+// of dst (-1: none) and source (null: outside the field, stored as 0); i runs over
+// [0, n).
+template <int NT, int B, typename Word, typename At>
+__device__ __forceinline__ void gather_l2(Word* dst, int n, At at) {
+  for (int i0 = threadIdx.x; i0 < n; i0 += B * NT) {
+    Word v[B];
+    int e[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int i = i0 + u * NT;
+      const Word* sp = nullptr;
+      e[u] = -1;
+      if (i < n) at(i, e[u], sp);
+      v[u] = sp ? __ldcg(sp) : (Word)0;
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (e[u] >= 0) dst[e[u]] = v[u];
+  }
+}
+
 // Copy of a tile's box (the tile and a one-point halo; 2D tiles have no z halo) of
 // `src` (row-major field of nz x ny x nx elements of `Word`) into shared memory at
 // `dst` (entry layout of G).  Rows are walked as (row, column) with one row base per
@@ -281,7 +305,7 @@ __device__ __forceinline__ void load_box_async(Word* dst, const Word* __restrict
       const Word* sp = in ? src + gz * plane + gy * g.nx + gx : src;
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(sp), "r"(in ? 16 : 0) : "memory");
     }
-  } else {
+  } else if (!MUTABLE) {
     constexpr int CW = G::TX < 32 ? G::TX : 32;  // lanes per row
     constexpr int RPP = NT / CW;                 // rows per pass
     const int c = threadIdx.x % CW;
@@ -298,16 +322,35 @@ __device__ __forceinline__ void load_box_async(Word* dst, const Word* __restrict
         box_word<MUTABLE>(&drow[lx], in ? row + gx : src, in);
       }
     }
+  } else {
+    // loads from L2, four per thread in flight before their stores
+    gather_l2<NT, 4, Word>(dst, ROWS * G::TX, [&](int i, int& d, const Word*& sp) {
+      const int r = i / G::TX, lx = i - r * G::TX;
+      const int ly = r % G::BY, lz = r / G::BY;
+      const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1, gx = tb.x0 + lx;
+      d = lz * G::PP + ly * G::BXP + G::XO + lx;
+      sp = gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx < g.nx ? src + gz * plane + gy * g.nx + gx : nullptr;
+    });
   }
   // the halo columns x0 - 1 and x0 + TX
-  for (int i = threadIdx.x; i < 2 * ROWS; i += NT) {
+  auto halo = [&](int i, int& d, const Word*& sp) {
     const int r = i >> 1, side = i & 1;
     const int ly = r % G::BY, lz = r / G::BY;
     const int64_t gz = tb.z0 + lz - G::HZ, gy = tb.y0 + ly - 1;
     const int64_t gx = side ? tb.x0 + G::TX : tb.x0 - 1;
     const bool in = gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx >= 0 && gx < g.nx;
-    Word* d = dst + lz * G::PP + ly * G::BXP + (side ? G::XO + G::TX : G::XO - 1);
-    box_word<MUTABLE>(d, in ? src + gz * plane + gy * g.nx + gx : src, in);
+    d = lz * G::PP + ly * G::BXP + (side ? G::XO + G::TX : G::XO - 1);
+    sp = in ? src + gz * plane + gy * g.nx + gx : nullptr;
+  };
+  if (MUTABLE) {
+    gather_l2<NT, (2 * ROWS + NT - 1) / NT, Word>(dst, 2 * ROWS, halo);  // every load in flight at once
+  } else {
+    for (int i = threadIdx.x; i < 2 * ROWS; i += NT) {
+      int d;
+      const Word* sp;
+      halo(i, d, sp);
+      box_word<false>(dst + d, sp ? sp : src, sp != nullptr);
+    }
   }
 }
 
@@ -1082,7 +1125,8 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
       constexpr int NZF = G::HZ ? 2 * G::BY * G::BX : 0;  // z faces (whole planes)
       constexpr int NYF = 2 * G::TZ * G::BX;              // y faces of the tile's planes
       constexpr int NXF = 2 * G::TZ * G::TY;              // x faces of the tile's rows
-      for (int i = threadIdx.x; i < NZF + NYF + NXF; i += NT) {
+      // from L2 (other blocks write them during the pass), several loads in flight
+      gather_l2<NT, 4, uint32_t>(sv, NZF + NYF + NXF, [&](int i, int& d, const uint32_t*& sp) {
         int lz, ly, lx;
         if (i < NZF) {
           const int r = i % (G::BY * G::BX);
@@ -1100,11 +1144,14 @@ __global__ void __launch_bounds__(TileCfg<T, ND>::NT, TileCfg<T, ND>::MINB)
           ly = r % G::TY;
           lx = jj < G::TZ * G::TY ? -1 : G::TX;
         }
-        if (!(ebits & tile_dir_bit<G>(lz, ly, lx))) continue;  // a later tile: its subbins are still 0
+        // a later tile's subbins are still 0, as the entry is: neither is read
         const int64_t qz = tb.z0 + lz, qy = tb.y0 + ly, qx = tb.x0 + lx;
-        if (qz >= 0 && qz < g.nz && qy >= 0 && qy < g.ny && qx >= 0 && qx < g.nx)
-          sv[G::entry(lz, ly, lx)] = __ldcg(&s_glob[qz * plane + qy * g.nx + qx]);
-      }
+        if ((ebits & tile_dir_bit<G>(lz, ly, lx)) && qz >= 0 && qz < g.nz && qy >= 0 && qy < g.ny && qx >= 0 &&
+            qx < g.nx) {
+          d = G::entry(lz, ly, lx);
+          sp = &s_glob[qz * plane + qy * g.nx + qx];
+        }
+      });
     }
     __syncthreads();
   }

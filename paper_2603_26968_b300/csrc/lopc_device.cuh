@@ -300,15 +300,33 @@ __device__ __forceinline__ bool bin_at_least(T v, long long b, unsigned long lon
 }
 
 // Lowest value of the dtype whose bin is b (Sec. III-E: subbin 0 decodes to the
-// lowest representable value within the bin), as an order key.  A guess from
-// (b - 1/2) eps_q, a few exact steps, and bisection over all keys if that fails.
-// Returns false if bin b holds no value.
+// lowest representable value within the bin), as an order key.  For float64 the bin's
+// lower boundary is the real t = (b - 1/2) / inv, and the division rounded up gives the
+// smallest float64 at or above t, which is in bin b unless it equals t and b is odd (a
+// tie goes to the even bin b - 1); then the next value is.  Otherwise (float32, where
+// the float64 division costs more than the steps it saves, or an infinite boundary) a
+// guess from (b - 1/2) eps_q, a few exact steps, and bisection over all keys if that
+// fails.  Returns false if bin b holds no value.
 template <typename T>
 __device__ bool lowest_key_in_bin(long long b, double eps_q, unsigned long long inv_m, int inv_e,
                                   typename Traits<T>::Key& out) {
   using K = typename Traits<T>::Key;
   const K kmax = Traits<T>::kMaxKey;
   K k;
+  if (sizeof(T) == 8) {
+    const double t = __ddiv_ru((double)b - 0.5, scalbn((double)inv_m, inv_e));  // |b| < 2^52: b - 1/2 is exact
+    const bool fin = is_finite_bits<double>(t);
+    k = fin ? (K)order_key<double>(t) : kmax;
+    if (fin) {
+      bool here = bin_at_least<T>(value_of_key<T>(k), b, inv_m, inv_e);
+      if (!here && k < kmax) here = bin_at_least<T>(value_of_key<T>(++k), b, inv_m, inv_e);
+      if (here) {
+        if (bin_at_least<T>(value_of_key<T>(k), b + 1, inv_m, inv_e)) return false;  // bin b is empty
+        out = k;
+        return true;
+      }
+    }
+  }
   if (sizeof(T) == 4) {
     const float g = __fmul_rn(__fsub_rn((float)b, 0.5f), (float)eps_q);
     k = is_finite_bits<float>(g) ? (K)order_key<float>(g) : (g > 0.f ? kmax : -kmax);
