@@ -525,7 +525,7 @@ def repair_modes_leg(torch, lopc, x, eb, flush, steps, warmup):
 
 def serve_leg(torch, lopc, args):
     """Poisson serving at the configured rate (labelled saturated when the engine does
-    not sustain the offered load), then at lower rates, from 3/4 of it down, until
+    not sustain the offered load), then at lower rates, from 7/8 of it down, until
     one is sustained with p99 below one second: the highest such rate tried is
     reported with its latencies, and half the configured rate always is."""
     from paper_2603_26968_b300 import serve, synth_gpu as SG
@@ -543,7 +543,7 @@ def serve_leg(torch, lopc, args):
 
     res = one(args.serve_rate)
     best = None
-    for f in (0.75, 0.6):
+    for f in (0.875, 0.75, 0.6):
         r = one(args.serve_rate * f)
         if not r["saturated"] and r["p99_ms"] < 1000.0:
             best = r
