@@ -1455,34 +1455,67 @@ __global__ void __launch_bounds__(NT) k_compact(const FieldInfo* __restrict__ F,
   auto bits_of = [](uint32_t v) {  // four byte flags -> four bits
     return (v & 0xffu ? 1u : 0u) | (v & 0xff00u ? 2u : 0u) | (v & 0xff0000u ? 4u : 0u) | (v & 0xff000000u ? 8u : 0u);
   };
-  unsigned int n = 0;
+  // the thread's words are read KW at a time, every load of a batch in flight before
+  // any is used, with the field of each; a thread with at most KW words keeps them in
+  // registers for the listing pass
+  constexpr int KW = 8;
+  uint32_t v[KW];
+  int fk[KW];
   int k = a < b ? field_of_word(F, nf, a) : 0;
-  for (int64_t w = a; w < b; ++w) {
-    while (k + 1 < nf && F[k + 1].word_base <= w) ++k;
-    const uint32_t v = F[k].dirty[w - F[k].word_base];
-    if (v && (long long)F[k].P->rounds <= F[k].round_cap) n += __popc(bits_of(v));
+  auto batch = [&](int64_t w0) {
+#pragma unroll
+    for (int u = 0; u < KW; ++u) {
+      const int64_t w = w0 + u;
+      v[u] = 0u;
+      fk[u] = k;
+      if (w < b) {
+        while (k + 1 < nf && F[k + 1].word_base <= w) ++k;
+        fk[u] = k;
+        v[u] = F[k].dirty[w - F[k].word_base];
+      }
+    }
+  };
+  int lf = -1;  // the field whose round-cap verdict `live` holds
+  bool live = false;
+  auto live_of = [&](int f) {
+    if (f != lf) {
+      lf = f;
+      live = (long long)F[f].P->rounds <= F[f].round_cap;
+    }
+    return live;
+  };
+  unsigned int n = 0;
+  for (int64_t w0 = a; w0 < b; w0 += KW) {
+    batch(w0);
+#pragma unroll
+    for (int u = 0; u < KW; ++u)
+      if (v[u] && live_of(fk[u])) n += __popc(bits_of(v[u]));
   }
+  const bool kept = b - a <= KW;
   unsigned int tot;
   unsigned int pos = block_exclusive_scan<NT, unsigned int>(n, tmp, &tot);
   k = a < b ? field_of_word(F, nf, a) : 0;
-  for (int64_t w = a; w < b; ++w) {
-    while (k + 1 < nf && F[k + 1].word_base <= w) ++k;
-    uint32_t* dw = F[k].dirty + (w - F[k].word_base);
-    const uint32_t v = *dw;
-    if (!v) continue;
-    *dw = 0u;
-    if ((long long)F[k].P->rounds > F[k].round_cap) {  // past the cap: drop the tiles, fail the field
-      atomicOr(&F[k].P->status, kErrNotConverged);
-      capped = 1;
-      continue;
+  for (int64_t w0 = a; w0 < b; w0 += KW) {
+    if (!kept) batch(w0);
+#pragma unroll
+    for (int u = 0; u < KW; ++u) {
+      if (!v[u]) continue;
+      const int f = fk[u];
+      const int64_t wl = w0 + u - F[f].word_base;  // the word within its field
+      F[f].dirty[wl] = 0u;
+      if (!live_of(f)) {  // past the cap: drop the tiles, fail the field
+        atomicOr(&F[f].P->status, kErrNotConverged);
+        capped = 1;
+        continue;
+      }
+      const uint32_t bits = bits_of(v[u]);
+      const uint32_t* ord = F[f].order + 4 * wl;  // the word's first rank
+      const int64_t base = F[f].tile_base;
+      for (uint32_t bb = bits; bb; bb &= bb - 1) list[pos++] = (uint32_t)(base + ord[__ffs(bb) - 1]);
+      const unsigned int c = __popc(bits);
+      atomicAdd(&cnt[class_of_geometry(F[f].g)], c);
+      if (field_counts) atomicAdd(&field_counts[f], c);
     }
-    const uint32_t bits = bits_of(v);
-    const int64_t r0 = 4 * (w - F[k].word_base);  // the word's first rank
-    for (uint32_t bb = bits; bb; bb &= bb - 1)
-      list[pos++] = (uint32_t)(F[k].tile_base + F[k].order[r0 + __ffs(bb) - 1]);
-    const unsigned int c = __popc(bits);
-    atomicAdd(&cnt[class_of_geometry(F[k].g)], c);
-    if (field_counts) atomicAdd(&field_counts[k], c);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1583,13 +1616,25 @@ __global__ void __launch_bounds__(NT) k_order(const FieldInfo* __restrict__ F, u
     if (threadIdx.x == 0) fi.P->pass_ordered = 0u;
     return;
   }
+  // every pass over the tiles reads KB keys per thread at a time, all in flight together
+  constexpr int KB = 8;
   uint32_t lo = 0xFFFFFFFFu, hi = 0u;
   unsigned long long span16 = 0;  // sum of the tiles' sample spans (sixteenths of a bin)
-  for (int64_t t = threadIdx.x; t < n; t += NT) {
-    const uint32_t k = tkey[t];
-    lo = k < lo ? k : lo;
-    hi = k > hi ? k : hi;
-    span16 += rank[t];
+  for (int64_t t0 = threadIdx.x; t0 < n; t0 += (int64_t)KB * NT) {
+    uint32_t k[KB], sp[KB];
+#pragma unroll
+    for (int u = 0; u < KB; ++u) {
+      const int64_t t = t0 + (int64_t)u * NT;
+      k[u] = t < n ? tkey[t] : lo;
+      sp[u] = t < n ? rank[t] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < KB; ++u) {
+      if (t0 + (int64_t)u * NT >= n) break;
+      lo = k[u] < lo ? k[u] : lo;
+      hi = k[u] > hi ? k[u] : hi;
+      span16 += sp[u];
+    }
   }
   {
     __shared__ unsigned long long tmp64[NT / 32 + 1];
@@ -1617,7 +1662,17 @@ __global__ void __launch_bounds__(NT) k_order(const FieldInfo* __restrict__ F, u
   }
   const uint64_t span = (uint64_t)(hi - lo) + 1u;
   auto bucket = [&](uint32_t k) { return (unsigned int)(((uint64_t)(k - lo) * NB) / span); };
-  for (int64_t t = threadIdx.x; t < n; t += NT) atomicAdd(&hist[bucket(tkey[t])], 1u);
+  for (int64_t t0 = threadIdx.x; t0 < n; t0 += (int64_t)KB * NT) {
+    uint32_t k[KB];
+#pragma unroll
+    for (int u = 0; u < KB; ++u) {
+      const int64_t t = t0 + (int64_t)u * NT;
+      k[u] = t < n ? tkey[t] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < KB; ++u)
+      if (t0 + (int64_t)u * NT < n) atomicAdd(&hist[bucket(k[u])], 1u);
+  }
   __syncthreads();
   unsigned int v[PER], sum = 0;
 #pragma unroll
@@ -1633,10 +1688,21 @@ __global__ void __launch_bounds__(NT) k_order(const FieldInfo* __restrict__ F, u
     start += v[u];
   }
   __syncthreads();
-  for (int64_t t = threadIdx.x; t < n; t += NT) {
-    const unsigned int r = atomicAdd(&hist[bucket(tkey[t])], 1u);
-    order[r] = (uint32_t)t;
-    rank[t] = r;
+  for (int64_t t0 = threadIdx.x; t0 < n; t0 += (int64_t)KB * NT) {
+    uint32_t k[KB];
+#pragma unroll
+    for (int u = 0; u < KB; ++u) {
+      const int64_t t = t0 + (int64_t)u * NT;
+      k[u] = t < n ? tkey[t] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < KB; ++u) {
+      const int64_t t = t0 + (int64_t)u * NT;
+      if (t >= n) break;
+      const unsigned int r = atomicAdd(&hist[bucket(k[u])], 1u);
+      order[r] = (uint32_t)t;
+      rank[t] = r;
+    }
   }
 }
 

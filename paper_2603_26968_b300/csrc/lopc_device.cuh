@@ -522,27 +522,38 @@ __device__ __forceinline__ V block_exclusive_scan(V v, V* tmp, V* total) {
 
 // Stream offsets of m records placed back to back from `base`, each taking its size
 // (kSizeMask bits of sizes[i]) padded to 16 bytes: offs[i] = base + the padded sizes
-// before i.  The block walks the table in chunks of 4 NT sizes, four consecutive ones
-// per thread, with one block scan per chunk and a running carry.  Returns base + the
+// before i.  The block walks the table in chunks of 8 NT sizes, eight consecutive ones
+// per thread (coalesced), with one block scan per chunk and a running carry; the next
+// chunk's sizes are loaded before this chunk's scan, so their latency overlaps it.
+// Sums are 64-bit: a corrupt table's sizes cannot wrap around.  Returns base + the
 // padded total (in every thread).
 __host__ __device__ constexpr uint64_t pad16_u(uint64_t v) { return (v + 15) & ~(uint64_t)15; }
 
 template <int NT>
 __device__ __forceinline__ uint64_t record_offsets(const uint32_t* __restrict__ sizes, int64_t m, uint64_t base,
                                                    uint64_t* __restrict__ offs, uint64_t* tmp) {
+  constexpr int PT = 8;
   uint64_t carry = base;
-  for (int64_t c0 = 0; c0 < m; c0 += 4 * NT) {
-    const int64_t i0 = c0 + 4 * (int64_t)threadIdx.x;
-    uint64_t p[4], sum = 0;
+  uint32_t nx[PT];
+  auto load = [&](int64_t c0) {
+    const int64_t i0 = c0 + PT * (int64_t)threadIdx.x;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < PT; ++u) nx[u] = i0 + u < m ? (uint32_t)pad16_u(sizes[i0 + u] & kSizeMask) : 0u;
+  };
+  if (m > 0) load(0);
+  for (int64_t c0 = 0; c0 < m; c0 += PT * NT) {
+    uint64_t p[PT], sum = 0;
+#pragma unroll
+    for (int u = 0; u < PT; ++u) {
       p[u] = sum;
-      sum += i0 + u < m ? pad16_u(sizes[i0 + u] & kSizeMask) : 0;
+      sum += nx[u];
     }
+    if (c0 + PT * NT < m) load(c0 + PT * NT);  // in flight during the scan
     uint64_t tot;
-    const uint64_t ex = block_exclusive_scan<NT, uint64_t>(sum, tmp, &tot) + carry;
+    const uint64_t ex = carry + block_exclusive_scan<NT, uint64_t>(sum, tmp, &tot);
+    const int64_t i0 = c0 + PT * (int64_t)threadIdx.x;
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < PT; ++u)
       if (i0 + u < m) offs[i0 + u] = ex + p[u];
     carry += tot;
   }
