@@ -1,5 +1,5 @@
-"""Seeded fields shared by the GPU test files: several tiles with ragged edges,
-degenerate shapes, heavy ties, deep repair chains, signed zeros and denormals."""
+"""Seeded fields shared by the GPU test files: several tiles with ragged edges, very tight
+bounds, degenerate shapes, heavy ties, deep repair chains, signed zeros and denormals."""
 import numpy as np
 
 from paper_2603_26968_b300 import synth as S
@@ -26,6 +26,12 @@ CASES = [
     ("3d_f64_ties", lambda: S.make_field(S.spec_3d_f64_ties(shape=(24, 36, 36))), 1, 5e-4),
     ("3d_f64_ties_ragged", lambda: S.make_field(S.spec_3d_f64_ties(shape=(24, 36, 36)))[:19, :35, :33].copy(), 1, 5e-4),
     ("3d_f64_abs", lambda: bumps((17, 20, 23), np.float64), 0, 1e-3),
+    # very tight bounds: bin residuals reach 14-40 bit planes (the transposes' packed,
+    # 32-plane and 64-bit paths)
+    ("3d_f32_eb1e-6", lambda: S.make_field(S.spec_3d_f32(n=40)), 1, 1e-6),
+    ("2d_f32_eb1e-6", lambda: bumps((130, 200), np.float32), 1, 1e-6),
+    ("2d_f64_eb1e-10", lambda: bumps((100, 150), np.float64), 1, 1e-10),
+    ("3d_f64_eb1e-12", lambda: bumps((17, 20, 23), np.float64, noise=0), 1, 1e-12),
     ("row_1xN", lambda: bumps((1, 777), np.float32), 1, 1e-2),
     ("col_Nx1", lambda: bumps((300, 1), np.float64), 1, 1e-2),
     ("3d_thin_z", lambda: bumps((1, 40, 50), np.float32), 1, 1e-2),
