@@ -120,7 +120,9 @@ __device__ __forceinline__ void untranspose_packed(int G, const uint32_t* planes
   for (int go = wid * Q; go < G; go += (NT / 32) * Q) {
     const int g = go + j;
     const uint32_t r = warp_transpose32(k < P && g < G ? planes[k * G + g] : 0u);
-#pragma unroll
+    // one copy of emit per variant: it is inlined, and unrolled copies of every packing
+    // width overflow the instruction cache
+#pragma unroll 1
     for (int jj = 0; jj < Q; ++jj)
       if (go + jj < G) emit(32 * (go + jj) + lane, (uint64_t)((r >> (jj * P2)) & MASK));
   }
