@@ -746,6 +746,40 @@ int run_compress(const CompressPlan& p, uint8_t* ws, cudaStream_t st) {
   return LOPC_OK;
 }
 
+// Host staging of the small read-backs of a single-field call: pinned, one per host
+// thread, so that the copies are plain DMA behind one synchronisation (pageable ones are
+// staged by the driver one at a time).  Null when pinned memory cannot be had; the
+// callers then use their stack.
+struct Readback {
+  struct {
+    uint64_t size;
+    int status;
+    int pad;
+  } res;
+  Params hp;
+  BatchState hb;
+  uint8_t header[kHeaderBytes];
+  unsigned status;
+};
+struct ReadbackHolder {
+  Readback* p = nullptr;
+  bool tried = false;
+  ~ReadbackHolder() {
+    if (p) (void)cudaFreeHost(p);
+  }
+};
+Readback* readback() {
+  thread_local ReadbackHolder h;
+  if (!h.tried) {
+    h.tried = true;
+    if (cudaMallocHost(&h.p, sizeof(Readback)) != cudaSuccess) {
+      h.p = nullptr;
+      (void)cudaGetLastError();
+    }
+  }
+  return h.p;
+}
+
 // Single field: plan, run, read back the size and status.
 int compress_one(const lopc_field_desc* d, const void* d_x, void* d_out, size_t out_cap, size_t* out_size,
                  int64_t* bins_out, uint64_t* subbins_out, void* d_ws, size_t ws_size, cudaStream_t st) {
@@ -766,16 +800,15 @@ int compress_one(const lopc_field_desc* d, const void* d_x, void* d_out, size_t 
   if (subbins_out)
     LAUNCH("export", st,
            k_export_subbins<<<148 * 8, 256, 0, st>>>(f.g.nz * f.g.ny * f.g.nx, f.s, subbins_out));
-  struct {
-    uint64_t size;
-    int status;
-    int pad;
-  } res;
-  Params hp;
-  BatchState hb;
-  CK(cudaMemcpyAsync(&res, dsize, 16, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(&hp, f.P, sizeof(Params), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(&hb, ptrs_of(p, ws).B, sizeof(BatchState), cudaMemcpyDeviceToHost, st));
+  Readback local;
+  Readback* rbk = readback();
+  if (!rbk) rbk = &local;
+  auto& res = rbk->res;
+  const Params& hp = rbk->hp;
+  const BatchState& hb = rbk->hb;
+  CK(cudaMemcpyAsync(&rbk->res, dsize, 16, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&rbk->hp, f.P, sizeof(Params), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&rbk->hb, ptrs_of(p, ws).B, sizeof(BatchState), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   g_last_rounds = (int64_t)hb.rounds;
   g_last_tile_runs = p.worklist ? f.g.ntiles : (int64_t)(2 * f.g.ntiles + hb.runs);
@@ -936,7 +969,11 @@ int decompress_one(const void* d_in, size_t in_size, void* d_x, size_t x_cap, ui
                    cudaStream_t st, size_t max_chunks) {
   if (!d_in || !d_x) return LOPC_ERR_INVALID_ARG;
   if (in_size < (size_t)kHeaderBytes) return LOPC_ERR_CORRUPT;
-  uint8_t hb[kHeaderBytes];
+  // the pinned staging, except for the entry point that must allocate nothing
+  Readback local;
+  Readback* rbk = max_chunks ? nullptr : readback();
+  if (!rbk) rbk = &local;
+  uint8_t* hb = rbk->header;
   CK(cudaMemcpyAsync(hb, d_in, kHeaderBytes, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   Header H;
@@ -955,10 +992,10 @@ int decompress_one(const void* d_in, size_t in_size, void* d_x, size_t x_cap, ui
   void* xs[1] = {d_x};
   plan_decompress(1, &H.d, ins, sizes, xs, nullptr, ws, p);
   if ((rc = run_decompress(p, ws, st))) return rc;
-  unsigned hs = 0;
-  CK(cudaMemcpyAsync(&hs, ws + p.off_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  rbk->status = 0;
+  CK(cudaMemcpyAsync(&rbk->status, ws + p.off_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  return hs ? LOPC_ERR_CORRUPT : LOPC_OK;
+  return rbk->status ? LOPC_ERR_CORRUPT : LOPC_OK;
 }
 
 // ------------------------------------------------------------ serving engine
