@@ -22,7 +22,11 @@
  * Conventions for every entry point:
  *   - Device pointers ("d_" prefix) point to memory of the current CUDA device;
  *     host pointers ("h_" prefix, or plain) to host memory.  The caller owns every
- *     buffer; the library never allocates device memory on these paths.
+ *     buffer; the library never allocates device memory on these paths.  A
+ *     synchronising single-field call reads its few result bytes back through a
+ *     small pinned host buffer that the library allocates once per host thread
+ *     (cudaMallocHost; on failure it uses the stack instead).
+ *     lopc_decompress_noalloc never does.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
  *     Work is stream-ordered.  Calls documented as "synchronising" wait for the
  *     stream once before returning, to report a size or a status.
