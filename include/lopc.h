@@ -179,7 +179,9 @@ LOPC_API int lopc_batch_compress(int n, const lopc_field_desc* descs, const void
                                  const lopc_plan* plan, void* d_ws, size_t ws_size, void* stream);
 
 /* Decompresses n streams (descs from lopc_peek of each header) into d_x[i]; each
- * stream's status goes to the DEVICE array d_status.  Asynchronous. */
+ * stream's status goes to the DEVICE array d_status.  Asynchronous.  A stream whose
+ * header does not match its descriptor (dtype, ndim, dims or chunk count) is reported
+ * as CORRUPT and leaves d_x[i] unwritten. */
 LOPC_API size_t lopc_batch_decompress_workspace_size(int n, const lopc_field_desc* descs);
 LOPC_API int lopc_batch_decompress(int n, const lopc_field_desc* descs, const void* const* d_in,
                                    const size_t* in_size, void* const* d_x, int* d_status, void* d_ws,

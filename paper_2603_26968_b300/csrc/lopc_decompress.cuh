@@ -39,7 +39,8 @@ __device__ __forceinline__ void dec_mark(int k, long long& t0) {
 }
 
 // Reads each stream's header on the device: the decoder's parameters, and a check
-// that the header matches the descriptor the launch was planned for.
+// that the header (dtype, ndim, dims, chunk count) matches the descriptor the launch
+// was planned for.
 __global__ void k_dec_setup(DecField* F, int nf) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= nf) return;
@@ -53,6 +54,11 @@ __global__ void k_dec_setup(DecField* F, int nf) {
   };
   bool ok = d.in_size >= (uint64_t)kHeaderBytes && rd(0, 4) == kMagic && rd(4, 2) >= 1 && rd(4, 2) <= LOPC_VERSION &&
             h[6] == (uint8_t)d.g.dtype && h[7] == (uint8_t)d.g.ndim;
+  // the dims too: a descriptor with other dims but as many tiles would decode garbage
+  if (d.g.ndim == 3)
+    ok = ok && rd(8, 8) == (uint64_t)d.g.nz && rd(16, 8) == (uint64_t)d.g.ny && rd(24, 8) == (uint64_t)d.g.nx;
+  else
+    ok = ok && rd(8, 8) == (uint64_t)d.g.ny && rd(16, 8) == (uint64_t)d.g.nx && rd(24, 8) == 0;
   const uint64_t total = ok ? rd(88, 8) : 0;
   ok = ok && total <= d.in_size && total >= (uint64_t)kHeaderBytes;
   d.constant = ok ? h[33] : 0;

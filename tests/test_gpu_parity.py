@@ -318,3 +318,30 @@ def test_full_size_sampled_parity(L, orc, name, make, mode, eb, tile, ordered):
     ys = y.view(-1)[torch.from_numpy(idx[:2000]).cuda()].cpu().numpy()
     want = orc.reconstruct(dc, bf[:2000], sn[idx[:2000]], e["inv"])
     assert ys.tobytes() == want.tobytes()
+
+
+@pytest.mark.parametrize("shape,dtype,other", [
+    ((32, 16, 48), np.float32, (16, 32, 48)),   # 2 x 1 x 3 and 1 x 2 x 3 tiles
+    ((128, 64), np.float32, (64, 128)),         # 2 x 1 and 1 x 2 tiles
+    ((16, 32, 40), np.float64, (8, 64, 40)),    # 2 x 2 x 3 and 1 x 4 x 3 tiles
+])
+def test_decompress_with_descriptor(L, orc, shape, dtype, other):
+    """lopc.decompress with the field's descriptor (one batch call checked on the
+    device) gives the oracle's reconstruction; a descriptor with other dims but as many
+    tiles is CORRUPT, and an output too small is CAPACITY, both before any write."""
+    x = bumps(shape, dtype, seed=4)
+    st = orc.compress(x, 1, 1e-3)
+    t = torch.frombuffer(bytearray(st), dtype=torch.uint8).cuda()
+    d = L.peek(t)
+    assert tuple(d.shape) == shape
+    y = L.decompress(t, desc=d)
+    assert y.cpu().numpy().tobytes() == orc.decompress(st).tobytes()
+    assert torch.equal(y, L.decompress(t))
+    bad = L.make_desc(other, "f32" if dtype == np.float32 else "f64", L.NOA, 1e-3)
+    with pytest.raises(L.LopcError) as e:
+        L.decompress(t, desc=bad)
+    assert e.value.code == -5
+    small = torch.empty(int(np.prod(shape)) - 1, dtype=y.dtype, device="cuda")
+    with pytest.raises(L.LopcError) as e:
+        L.decompress(t, out=small, desc=d)
+    assert e.value.code == -4
