@@ -1,7 +1,8 @@
 // lopc_codec.cuh -- block-cooperative lossless stages on shared memory (Sec. III-C):
-// BIT_w bit-plane transposes with warp ballots, and RZE_g (repeated zero
-// elimination with a twice repeat-eliminated bitmap) as word-level encode/decode,
-// plus 16-byte copies between a staged record and global memory.
+// BIT_w bit-plane transposes by warp butterflies (several groups of words per
+// butterfly when the words reach few planes), and RZE_g (repeated zero elimination
+// with a twice repeat-eliminated bitmap) as word-level encode/decode, plus 16-byte
+// copies between a staged record and global memory.
 #pragma once
 #include "lopc_device.cuh"
 
@@ -35,12 +36,13 @@ __device__ __forceinline__ uint32_t plane_bytes_of(int n32, int P, uint32_t L) {
 // Planes a word OR-reduction `orw` reaches (the planes above are zero).
 __device__ __forceinline__ int planes_of(uint64_t orw) { return orw ? 64 - __clzll((long long)orw) : 0; }
 
-// After a partial rze_decode into `buf` (L bytes; the first lw, a multiple of 16,
-// written): zeroes the rest, 16 bytes a store (all threads; ends with a barrier).
+// After a partial rze_decode into `buf` (its first lw bytes, a multiple of 16,
+// written): zeroes bytes [lw, end), 16 bytes a store (all threads; ends with a
+// barrier).  `end` is a multiple of 16: the end of the planes a transpose will read.
 template <int NT>
-__device__ __forceinline__ void zero_after_decode(uint8_t* buf, uint32_t lw, uint32_t L) {
+__device__ __forceinline__ void zero_after_decode(uint8_t* buf, uint32_t lw, uint32_t end) {
   uint4* b = reinterpret_cast<uint4*>(buf);
-  for (uint32_t i = lw / 16u + threadIdx.x; i < L / 16u; i += NT) b[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (uint32_t i = lw / 16u + threadIdx.x; i < end / 16u; i += NT) b[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
 }
 
