@@ -72,14 +72,19 @@ def time_ms(run: Callable[[], None], reps: int = 3, flush: Optional[torch.Tensor
 
 
 def tune(run: Callable[[lopc.Plan], None], classes: Sequence[int], reps: int = 3,
-         flush: Optional[torch.Tensor] = None, knobs: Dict[str, Sequence[int]] = KNOBS) -> Dict:
+         flush: Optional[torch.Tensor] = None, knobs: Dict[str, Sequence[int]] = KNOBS,
+         timer: Optional[Callable[[Callable[[], None]], List[float]]] = None) -> Dict:
     """Coordinate descent over the plan's knobs for the given classes.  `run(plan)`
-    enqueues one batch with that plan.  Returns the best plan (as a dict), its time,
-    the default plan's time and spread, and the trial log."""
+    enqueues one batch with that plan; `timer(fn)` gives the times of `reps` runs of
+    fn (CUDA events with L2 flushed by default).  Returns the best plan (as a dict),
+    its time, the default plan's time and spread, and the trial log."""
+    if timer is None:
+        timer = lambda fn: time_ms(fn, reps, flush)  # noqa: E731
+
     def trial(d: dict) -> List[float]:
         pl = lopc.Plan.of(d)
         run(pl)                                     # graph capture, clocks up
-        return time_ms(lambda: run(pl), reps, flush)
+        return timer(lambda: run(pl))
 
     best = lopc.plan_default().as_dict()
     t0 = trial(best)
@@ -87,8 +92,9 @@ def tune(run: Callable[[lopc.Plan], None], classes: Sequence[int], reps: int = 3
     trials = [{"plan": json.loads(json.dumps(best)), "ms": best_ms}]
     for knob, values in knobs.items():
         for c in classes:
+            start = best[knob][c]  # measured already, with the other knobs as they are
             for v in values:
-                if v == best[knob][c]:
+                if v == start or v == best[knob][c]:
                     continue
                 cand = json.loads(json.dumps(best))
                 cand[knob][c] = v
